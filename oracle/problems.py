@@ -1,0 +1,235 @@
+"""Self-similar profile problems: ansatz, network and residual operators (FP64).
+
+Paper, Methods, "Self-similar Solutions": phi_A(x, t) = (1-t)^{k_A(lambda)} Phi_A(y),
+y = x / (1-t)^{1+lambda}; substituting into each PDE and factoring out the
+power of (1-t) gives the static equations E_k(Phi, lambda) = 0 (Eq.
+self-similar-static).  With tau = 1 - t, a time derivative of tau^k Phi(y)
+is tau^{k-1} [-k Phi + (1+lambda) y . grad Phi]; velocities scale as
+tau^lambda.  V = (1+lambda) y + U denotes the self-similar transport velocity.
+The resulting residual operators (this project's derivation; the paper's own
+are in its Supplementary Information):
+
+  Burgers      u_t + u u_x = 0            k_u = lambda
+               R = -lambda U + ((1+lambda) y + U) U'
+  CCF          theta_t + (H theta) theta_x = 0     k = lambda, U = H Theta
+               R = -lambda Theta + ((1+lambda) y + U) Theta'
+  IPM          rho_t + u . grad rho = 0, Delta psi = d1 rho, u = (d2 psi, -d1 psi)
+               k_rho = lambda, k_psi = 1 + 2 lambda
+               R1 = -lambda P + V . grad P,   R2 = Delta Psi - d1 P
+  Boussinesq   omega_t + u . grad omega = d1 theta, theta_t + u . grad theta = 0,
+               -Delta psi = omega, u = (d2 psi, -d1 psi)
+               k_omega = -1, k_theta = lambda - 1, k_psi = 1 + 2 lambda
+               R_Omega = Omega + V . grad Omega - d1 Theta
+               R_Theta = (1 - lambda) Theta + V . grad Theta
+               R_Psi   = Delta Psi + Omega
+In the Boussinesq case d11 R_Theta at the origin reproduces the paper's printed
+lambda-inference rule lambda = -3 - 2 d1 U1(0, 0) (Methods, "Identifying
+admissible lambda values", item 2); a test checks this symbolically.
+
+Ansatz (Methods, "Solution Modeling", Eq. ansatz_vorticity and its stated
+generalisation to every field): Phi_A(y) = s_A(y) * NN_A(z(y)) * q^{-k_A},
+with q = (1 + |y|^2)^{-1/(2(1+lambda))}, beta = y2 / sqrt(1 + |y|^2),
+z = q (1D) or (q, beta) (2D), s_A = y1 / sqrt(1+|y|^2) for odd fields and
+1 for even fields (CCF Theta: y^2 / (1+y^2), which removes the forced zero
+at the origin).  For Omega (k = -1) this is exactly Eq. ansatz_vorticity.
+NN is a tanh MLP with a linear output layer; theta stores, per layer, W
+(out x in, row-major) then b.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import hilbert
+from .jets import Jet
+
+BURGERS, CCF, IPM, BOUSSINESQ = 0, 1, 2, 3
+DIM = {BURGERS: 1, CCF: 1, IPM: 2, BOUSSINESQ: 2}
+N_EQ = {BURGERS: 1, CCF: 1, IPM: 2, BOUSSINESQ: 3}
+N_FIELDS = {BURGERS: 1, CCF: 1, IPM: 2, BOUSSINESQ: 3}
+HAS_WALL = {BURGERS: False, CCF: False, IPM: True, BOUSSINESQ: True}
+
+
+# ---------------------------------------------------------------------------
+# residual operators on field values and derivatives (plain arithmetic, so
+# they also accept sympy expressions)
+# ---------------------------------------------------------------------------
+
+def residual_burgers(lam, y, U, U_y):
+    return [-lam * U + ((1 + lam) * y + U) * U_y]
+
+
+def residual_ccf(lam, y, Th, Th_y, Uvel):
+    return [-lam * Th + ((1 + lam) * y + Uvel) * Th_y]
+
+
+def residual_ipm(lam, y1, y2, P, P_1, P_2, Psi_1, Psi_2, Psi_11, Psi_22):
+    U1, U2 = Psi_2, -Psi_1
+    V1, V2 = (1 + lam) * y1 + U1, (1 + lam) * y2 + U2
+    return [-lam * P + V1 * P_1 + V2 * P_2,
+            Psi_11 + Psi_22 - P_1]
+
+
+def residual_boussinesq(lam, y1, y2, Om, Om_1, Om_2, Th, Th_1, Th_2, Psi_1, Psi_2, Psi_11, Psi_22):
+    U1, U2 = Psi_2, -Psi_1
+    V1, V2 = (1 + lam) * y1 + U1, (1 + lam) * y2 + U2
+    return [Om + V1 * Om_1 + V2 * Om_2 - Th_1,
+            (1 - lam) * Th + V1 * Th_1 + V2 * Th_2,
+            Psi_11 + Psi_22 + Om]
+
+
+# Exponent k_A(lambda) and prefactor kind of every field, in network-output order.
+# prefactor: "odd" = y1/sqrt(u), "even" = 1, "ccf" = y^2/u, "g" = y/u.
+def field_specs(eq, lam):
+    if eq == BURGERS:
+        return [("odd", lam)]
+    if eq == CCF:
+        return [("ccf", lam)]
+    if eq == IPM:
+        return [("even", lam), ("odd", 1 + 2 * lam)]
+    if eq == BOUSSINESQ:
+        return [("odd", -1.0 + 0 * lam), ("even", lam - 1), ("odd", 1 + 2 * lam)]
+    raise ValueError(eq)
+
+
+def _prefactor(kind, ys, u):
+    y1 = ys[0]
+    if kind == "odd":
+        return y1 / u.sqrt()
+    if kind == "even":
+        return Jet.const(np.ones_like(y1.v), y1.d)
+    if kind == "ccf":
+        return (y1 * y1) / u
+    if kind == "g":
+        return y1 / u
+    raise ValueError(kind)
+
+
+class Problem:
+    """One profile fit: equation, MLP widths, collocation and wall points, loss weights."""
+
+    def __init__(self, equation, widths, y, y_bnd=None, rho=None, c_bnd=1.0,
+                 y_norm=(1.0, 0.0), c_norm=1.0, c_norm_w=1.0, hilbert_m=1024):
+        self.eq = int(equation)
+        self.widths = list(widths)
+        self.d = DIM[self.eq]
+        assert self.widths[0] == self.d and self.widths[-1] == N_FIELDS[self.eq]
+        self.y = np.asarray(y, dtype=np.float64).reshape(self.d, -1)
+        self.n = self.y.shape[1]
+        if y_bnd is None or not HAS_WALL[self.eq]:
+            self.y_bnd = np.zeros((self.d, 0))
+        else:
+            self.y_bnd = np.asarray(y_bnd, dtype=np.float64).reshape(self.d, -1)
+        self.nb = self.y_bnd.shape[1]
+        self.rho = np.ones(self.n) if rho is None else np.asarray(rho, dtype=np.float64)
+        self.c_bnd = float(c_bnd)
+        self.y_norm = tuple(float(v) for v in y_norm)
+        self.c_norm = float(c_norm)
+        self.c_norm_w = float(c_norm_w)
+        self.M = int(hilbert_m)
+        self.ne = N_EQ[self.eq]
+        self.P = sum(self.widths[i] * self.widths[i + 1] + self.widths[i + 1]
+                     for i in range(len(self.widths) - 1))
+        self.n_rows = self.n * self.ne + self.nb + 1
+
+    # -- network ----------------------------------------------------------
+    def layers(self, theta):
+        out, off = [], 0
+        for i in range(len(self.widths) - 1):
+            fi, fo = self.widths[i], self.widths[i + 1]
+            W = theta[off:off + fi * fo].reshape(fo, fi)
+            off += fi * fo
+            b = theta[off:off + fo]
+            off += fo
+            out.append((W, b))
+        assert off == self.P
+        return out
+
+    def mlp(self, theta, z):
+        """tanh MLP with linear last layer applied to the input jet z (components (d_in, n))."""
+        h = z
+        L = self.layers(theta)
+        for i, (W, b) in enumerate(L):
+            a = h.matvec(W, b)
+            h = a if i == len(L) - 1 else a.tanh()
+        return h
+
+    # -- ansatz -------------------------------------------------------------
+    def fields(self, theta, lam, ys, extra_g=False):
+        """Field jets Phi_A at points ys (d, n); for CCF optionally also g = Theta / y."""
+        d = self.d
+        yj = [Jet.variable(ys[i], i, d) for i in range(d)]
+        u = Jet.const(np.ones(ys.shape[1]), d)
+        for i in range(d):
+            u = u + yj[i] * yj[i]
+        q = u.pow(-1.0 / (2.0 * (1.0 + lam)))
+        if d == 1:
+            z = Jet.stack([q])
+        else:
+            beta = yj[1] / u.sqrt()
+            z = Jet.stack([q, beta])
+        nn = self.mlp(theta, z)
+        out = []
+        for a, (kind, k) in enumerate(field_specs(self.eq, lam)):
+            out.append(_prefactor(kind, yj, u) * nn[a] * q.pow(-k))
+        if extra_g:
+            k = field_specs(self.eq, lam)[0][1]
+            out.append(_prefactor("g", yj, u) * nn[0] * q.pow(-k))
+        return out
+
+    def interior_residuals(self, theta, lam, ys=None):
+        ys = self.y if ys is None else ys
+        if self.eq == BURGERS:
+            (U,) = self.fields(theta, lam, ys)
+            return residual_burgers(lam, ys[0], U.v, U.g[0])
+        if self.eq == CCF:
+            Th, g = self.fields(theta, lam, ys, extra_g=True)
+            _, s = hilbert.nodes(self.M)
+            g_nodes = self.fields(theta, lam, s.reshape(1, -1), extra_g=True)[1].v
+            Uvel = hilbert.velocity(ys[0], g.v, g_nodes, self.M)
+            return residual_ccf(lam, ys[0], Th.v, Th.g[0], Uvel)
+        if self.eq == IPM:
+            P, Psi = self.fields(theta, lam, ys)
+            return residual_ipm(lam, ys[0], ys[1], P.v, P.g[0], P.g[1],
+                                Psi.g[0], Psi.g[1], Psi.h[0][0], Psi.h[1][1])
+        if self.eq == BOUSSINESQ:
+            Om, Th, Psi = self.fields(theta, lam, ys)
+            return residual_boussinesq(lam, ys[0], ys[1], Om.v, Om.g[0], Om.g[1],
+                                       Th.v, Th.g[0], Th.g[1], Psi.g[0], Psi.g[1],
+                                       Psi.h[0][0], Psi.h[1][1])
+        raise ValueError(self.eq)
+
+    def wall_values(self, theta, lam):
+        """No-penetration on the wall y2 = 0: the stream function vanishes there."""
+        if self.nb == 0:
+            return np.zeros(0)
+        return self.fields(theta, lam, self.y_bnd)[-1].v
+
+    def norm_value(self, theta, lam):
+        """Normalisation constraint value Phi_{A0}(y_norm) (Boussinesq: d1 Omega there)."""
+        ys = np.array(self.y_norm[:self.d], dtype=np.float64).reshape(self.d, 1)
+        F = self.fields(theta, lam, ys)[0]
+        if self.eq == BOUSSINESQ:
+            return F.g[0][0]
+        return F.v[0]
+
+    # -- weighted rows ------------------------------------------------------
+    def rows(self, theta, lam):
+        """r~ such that h = 1/2 |r~|^2 is the paper's d0 loss plus data loss:
+        h = (1/(N N_E)) sum rho R^2 + (c_bnd/N_b) sum R_b^2 + c_norm_w (Phi(y_norm) - C)^2."""
+        R = self.interior_residuals(theta, lam)
+        w = np.sqrt(2.0 * self.rho / (self.n * self.ne))
+        inner = np.stack([w * Rk for Rk in R], axis=1).reshape(-1)   # point-major
+        parts = [inner]
+        if self.nb:
+            parts.append(np.sqrt(2.0 * self.c_bnd / self.nb) * self.wall_values(theta, lam))
+        parts.append(np.array([np.sqrt(2.0 * self.c_norm_w) * (self.norm_value(theta, lam) - self.c_norm)]))
+        return np.concatenate(parts)
+
+    def loss(self, theta, lam):
+        r = self.rows(theta, lam)
+        return 0.5 * float(np.dot(r, r))
+
+    def max_abs_residual(self, theta, lam, ys=None):
+        """Max d0 residual over a grid (Methods, "Validation Metrics", max d0 residual)."""
+        R = self.interior_residuals(theta, lam, ys)
+        return float(max(np.max(np.abs(Rk)) for Rk in R))
