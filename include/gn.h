@@ -1,0 +1,216 @@
+/*
+ * gn.h -- C ABI of the GB300 Gauss-Newton profile-fit library (libgn.so).
+ *
+ * The library evaluates, on one GPU, the hot path of the method of
+ * "Discovery of Unstable Singularities" (arXiv 2509.14185): a small tanh MLP
+ * models a self-similar blow-up profile (Methods, Eq. self-similar and Eq.
+ * ansatz_vorticity), each collocation point contributes the residuals R_k of
+ * the static self-similar equations (Eq. self-similar-static, "Training
+ * Loss"), and one damped Gauss-Newton step (Methods, "Second-order
+ * Optimizer") updates the network parameters theta and the blow-up rate
+ * lambda together (lambda as a trainable unknown, "Identifying Admissible
+ * lambda Values", item 1).
+ *
+ * Conventions used by every call:
+ *   - All floating point is IEEE binary64 ("FP64") unless a call says otherwise.
+ *   - "device" pointers are CUDA global-memory addresses on the GPU that was
+ *     current when gn_init ran; "host" pointers are ordinary CPU memory.
+ *   - Every call is asynchronous with respect to the host only where stated;
+ *     calls that return scalars to the host synchronise the handle's stream.
+ *   - Functions never abort and never print.  They return GN_OK (0), a
+ *     positive warning, or a negative GN_ERR_* code; gn_error_string maps a
+ *     code to a static message.
+ *   - Parameters: theta holds, for each linear layer l in order, the weight
+ *     matrix W_l (out_l x in_l, row-major) followed by the bias b_l (out_l).
+ *     P = sum_l (in_l*out_l + out_l).  lambda is passed separately; the
+ *     Jacobian has P' = P + 1 columns and column P is d/d lambda.
+ *   - Rows: r~ has n_rows = n_pts * N_E + n_bnd + 1 entries, in the order
+ *     (interior point i, equation k) at row i*N_E + k, then the wall rows,
+ *     then the normalisation row.  Rows are weighted so that
+ *     h = 1/2 |r~|^2 = (1/(n_pts N_E)) sum_i rho_i sum_k R_k(y_i)^2
+ *                      + (c_bnd/n_bnd) sum_b Psi(y_b)^2
+ *                      + c_norm_w (Phi_A0(y_norm) - c_norm)^2,
+ *     i.e. the paper's d0 equation loss plus its data loss ("Training Loss").
+ *     Then grad h = J~^T r~ and the Gauss-Newton matrix is G = J~^T J~.
+ */
+#ifndef GN_H_
+#define GN_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define GN_OK                 0
+#define GN_WARN_NO_DECREASE   1   /* line search found no decrease: theta, lambda kept, damping *= 10 */
+#define GN_ERR_INVALID       -1   /* bad argument (null pointer, size, unsupported shape) */
+#define GN_ERR_CUDA          -2   /* a CUDA runtime call failed */
+#define GN_ERR_OOM           -3   /* device allocation failed */
+#define GN_ERR_NONFINITE     -4   /* a residual or loss was NaN or infinite */
+#define GN_ERR_NOT_SPD       -5   /* G + gamma I not positive definite after 5 damping escalations */
+#define GN_ERR_TIMEOUT       -6   /* a bounded device-side wait gave up */
+#define GN_ERR_UNSUPPORTED   -7   /* requested precision/path not available on this device */
+
+/* ---- problem description ----------------------------------------------- */
+/* Equations (Results and Methods; residual operators as derived from the
+ * paper's ansatz, see R_k below). */
+enum gn_equation {
+  GN_BURGERS = 0,     /* 1D Burgers, the paper's worked example (research flowchart figure):
+                         R = -lambda U + ((1+lambda) y + U) U'                           */
+  GN_CCF = 1,         /* 1D Cordoba-Cordoba-Fontelos, theta_t + (H theta) theta_x = 0:
+                         R = -lambda Theta + ((1+lambda) y + H Theta) Theta'              */
+  GN_IPM = 2,         /* 2D incompressible porous media with wall y2 = 0, fields (P, Psi):
+                         R1 = -lambda P + V.grad P, R2 = Laplace Psi - d1 P               */
+  GN_BOUSSINESQ = 3   /* 2D Boussinesq with wall y2 = 0, fields (Omega, Theta, Psi):
+                         R1 = Omega + V.grad Omega - d1 Theta,
+                         R2 = (1-lambda) Theta + V.grad Theta, R3 = Laplace Psi + Omega
+                         (V = (1+lambda) y + U, U = (d2 Psi, -d1 Psi))                    */
+};
+
+/* Precision of the Gram product G = J~^T J~ (Methods, "Second-order Optimizer";
+ * everything else is always FP64). */
+enum gn_precision {
+  GN_PREC_FP64 = 0,        /* native FP64 (DFMA) Gram */
+  GN_PREC_SPLIT_BF16 = 1   /* Ozaki split: each FP64 column of J~ scaled by a power of two and
+                              split into n_slices BF16 slices; slice products on the tcgen05
+                              tensor cores with exactly representable FP32 partial sums,
+                              combined in double-FP32 and returned as FP64 */
+};
+
+#define GN_MAX_LAYERS 8
+
+typedef struct gn_problem {
+  int equation;              /* enum gn_equation */
+  int n_layers;              /* number of linear layers L (hidden layers + output layer), 1..GN_MAX_LAYERS */
+  int widths[GN_MAX_LAYERS + 1]; /* widths[0] = d (1 or 2), widths[L] = number of fields
+                                   (1 Burgers/CCF, 2 IPM, 3 Boussinesq); hidden widths 1..256 */
+  int64_t n_pts;             /* interior collocation points (>= 0) */
+  const double* y;           /* device, SoA [d][n_pts]: y[k*n_pts + i] is coordinate k of point i.
+                                Borrowed: must stay valid until gn_destroy. */
+  const double* rho;         /* device [n_pts] per-point loss weights, or NULL for all ones. Borrowed. */
+  int64_t n_bnd;             /* wall points (2D problems only; must be 0 for 1D) */
+  const double* y_bnd;       /* device, SoA [2][n_bnd], points on the wall y2 = 0. Borrowed. */
+  double c_bnd;              /* weight of the wall loss (mean over wall points); 1.0 by default */
+  double y_norm[2];          /* normalisation point (Methods, "Training Loss", data loss) */
+  double c_norm;             /* target value C_norm */
+  double c_norm_w;           /* weight c_norm of the normalisation row */
+  int hilbert_m;             /* CCF only: nodes M of the discrete Hilbert operator (even, 8..16384) */
+  int precision;             /* enum gn_precision used by gn_step for the Gram */
+  int n_slices;              /* split precision only: BF16 slices per FP64 value (1..8) */
+} gn_problem;
+
+/* Normalisation row (data loss) per equation, fixed by the library:
+ *   Burgers U(y_norm), CCF Theta(y_norm), IPM P(y_norm), Boussinesq d Omega/d y1 (y_norm). */
+
+typedef struct gn_step_info {
+  double loss_before;        /* h(theta, lambda) */
+  double loss_after;         /* h at the accepted point (== loss_before if none) */
+  double alpha;              /* accepted step length (0 if none) */
+  double rho;                /* Levenberg-Marquardt ratio actual/predicted decrease */
+  double gamma_used;         /* damping that the accepted factorisation used */
+  int chol_retries;          /* damping escalations needed to factorise */
+  int n_trials;              /* residual-only line-search evaluations */
+  int status;                /* same value as the return code */
+  double ms_phase[8];        /* device time per phase: jacobian, gram, gradient, factor,
+                                solve, line search, total, unused */
+} gn_step_info;
+
+typedef struct gn_handle gn_handle;
+
+/* ---- lifecycle ------------------------------------------------------------ */
+
+/* Create a handle for one profile fit.  Copies *p (the point arrays stay
+ * borrowed), allocates all device workspace (J~, G, factor, vectors, the CCF
+ * Hilbert matrix) on the current device, and binds the handle to
+ * cuda_stream (a cudaStream_t; NULL = legacy default stream).
+ * Cites: problem statement in Methods ("Self-similar Solutions", "Solution
+ * Modeling", "Training Loss").  Errors: GN_ERR_INVALID, GN_ERR_OOM, GN_ERR_CUDA. */
+int gn_init(const gn_problem* p, void* cuda_stream, gn_handle** out);
+
+/* Release all device workspace owned by the handle.  Safe on NULL. */
+int gn_destroy(gn_handle* h);
+
+/* P (network parameters, excluding lambda) and the number of rows of r~. */
+int gn_param_count(const gn_handle* h, int64_t* P);
+int gn_row_count(const gn_handle* h, int64_t* n_rows);
+
+/* Change the Gram precision used by gn_step and gn_gram. */
+int gn_set_precision(gn_handle* h, int precision, int n_slices);
+
+/* ---- evaluation --------------------------------------------------------- */
+
+/* r_out[0..n_rows) = r~(theta, lambda); *loss_out (host, may be NULL) = h = |r~|^2/2.
+ * theta: device [P].  r_out: device [n_rows], caller-owned (may be NULL when
+ * only the loss is wanted).  Synchronises the stream when loss_out != NULL.
+ * Returns GN_ERR_NONFINITE if the loss is not finite.
+ * Cites: residual factorisation E_k = F_k R_k and the d0 loss (Methods,
+ * "Solution Modeling" and "Training Loss"). */
+int gn_residual(gn_handle* h, const double* theta, double lambda, double* r_out, double* loss_out);
+
+/* Rows [row0, row0+nrows) of J~ = d r~ / d(theta, lambda) into J_out (device,
+ * row-major, leading dimension ld >= P+1; column P is d/d lambda, the total
+ * derivative through the coordinates q(y; lambda), the envelopes and the
+ * explicit lambda terms).  Caller owns J_out.  Asynchronous.
+ * Cites: Gauss-Newton matrix built from Jacobian products (Methods,
+ * "Second-order Optimizer"). */
+int gn_jacobian(gn_handle* h, const double* theta, double lambda, double* J_out, int64_t ld,
+                int64_t row0, int64_t nrows);
+
+/* grad_out[0..P] = J~^T seed without forming J~ (reverse pass through the
+ * jets, one per collocation point).  seed: device [n_rows], or NULL for
+ * seed = r~ (then grad_out = grad h).  grad_out: device [P+1], caller-owned.
+ * Asynchronous.  This is the adjoint that backs torch.autograd. */
+int gn_gradient(gn_handle* h, const double* theta, double lambda, const double* seed, double* grad_out);
+
+/* ---- Gauss-Newton pieces -------------------------------------------------- */
+
+/* G_out = J^T J (lower triangle; the strict upper triangle is also written
+ * for precision FP64, left untouched for SPLIT) and g_out = J^T r for a
+ * caller-given row block.  J: device [nrows x ld] row-major with P+1 used
+ * columns; r: device [nrows] (may be NULL, then g_out is not written);
+ * G_out: device [(P+1) x (P+1)] row-major; g_out: device [P+1].
+ * accumulate != 0 adds into G_out/g_out instead of overwriting (row-block
+ * streaming).  precision: enum gn_precision.  Asynchronous. */
+int gn_gram(gn_handle* h, const double* J, int64_t ld, int64_t nrows, const double* r,
+            double* G_out, double* g_out, int precision, int accumulate);
+
+/* delta_out = (G + gamma I)^{-1} g by a blocked FP64 Cholesky factorisation,
+ * escalating gamma *= 10 (at most 5 times) when a pivot is not positive.
+ * G: device [(P+1)^2] row-major (lower triangle read, not modified);
+ * g, delta_out: device [P+1]; *gamma in/out (host); *retries_out (host, may
+ * be NULL).  Synchronises.  Returns GN_ERR_NOT_SPD when all retries fail. */
+int gn_damped_solve(gn_handle* h, const double* G, const double* g, double* gamma,
+                    double* delta_out, int* retries_out);
+
+/* One damped Gauss-Newton step, in place:
+ *   r~, J~ at (theta, lambda); G = J~^T J~ (precision of the handle);
+ *   g = J~^T r~; delta = (G + gamma I)^{-1} g; Armijo backtracking on
+ *   alpha = 1, 1/2, ... (<= 8 residual-only evaluations, c1 = 1e-4);
+ *   theta -= alpha delta[0..P), lambda -= alpha delta[P];
+ *   Levenberg-Marquardt update of gamma (x1.5 if rho < 1/4, x2/3 if rho > 3/4).
+ * theta: device [P] in/out; lambda, damping: host in/out; info: host (may be NULL).
+ * Returns GN_OK, GN_WARN_NO_DECREASE (theta and lambda unchanged, damping
+ * x10), GN_ERR_NOT_SPD or GN_ERR_NONFINITE.  Synchronises.
+ * Cites: Methods, "Second-order Optimizer" (damped Gauss-Newton update and
+ * Levenberg-Marquardt damping); the line-search and LM constants are this
+ * library's choice because the paper gives none. */
+int gn_step(gn_handle* h, double* theta, double* lambda, double* damping, gn_step_info* info);
+
+/* Max |R_k| over the interior points (Methods, "Validation Metrics", max d0
+ * residual) at (theta, lambda), unweighted.  *out: host.  Synchronises. */
+int gn_max_residual(gn_handle* h, const double* theta, double lambda, double* out);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (a diagnostic counter; read it before and after a region to count its launches). */
+int64_t gn_kernel_launches(void);
+
+/* Static message for a status code. */
+const char* gn_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GN_H_ */

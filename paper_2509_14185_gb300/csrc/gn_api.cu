@@ -1,0 +1,597 @@
+// Host side of the C ABI (include/gn.h): handle lifecycle, the evaluation
+// passes over the point kinds, and the damped Gauss-Newton step driver
+// (Methods, "Second-order Optimizer"; constants of the line search and of the
+// Levenberg-Marquardt rule are this library's, the paper gives none).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "gn_internal.cuh"
+
+using namespace gn;
+
+std::atomic<long long> gn::g_launches{0};
+
+namespace {
+
+#define GN_TRY_CUDA(x)                          \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return GN_ERR_CUDA;  \
+  } while (0)
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+int dim_of(int eq) { return (eq == GN_IPM || eq == GN_BOUSSINESQ) ? 2 : 1; }
+int fields_of(int eq) { return eq == GN_IPM ? 2 : (eq == GN_BOUSSINESQ ? 3 : 1); }
+int neq_of(int eq) { return eq == GN_IPM ? 2 : (eq == GN_BOUSSINESQ ? 3 : 1); }
+
+int validate(const gn_problem* p) {
+  if (!p) return GN_ERR_INVALID;
+  if (p->equation < GN_BURGERS || p->equation > GN_BOUSSINESQ) return GN_ERR_INVALID;
+  if (p->n_layers < 1 || p->n_layers > GN_MAX_LAYERS) return GN_ERR_INVALID;
+  const int d = dim_of(p->equation);
+  if (p->widths[0] != d || p->widths[p->n_layers] != fields_of(p->equation)) return GN_ERR_INVALID;
+  for (int l = 1; l < p->n_layers; l++)
+    if (p->widths[l] < 1 || p->widths[l] > 256) return GN_ERR_INVALID;
+  if (p->n_pts < 0 || (p->n_pts > 0 && !p->y)) return GN_ERR_INVALID;
+  if (d == 1 && p->n_bnd != 0) return GN_ERR_INVALID;
+  if (p->n_bnd < 0 || (p->n_bnd > 0 && !p->y_bnd)) return GN_ERR_INVALID;
+  if (p->equation == GN_CCF) {
+    if (p->hilbert_m < 8 || p->hilbert_m > 16384 || (p->hilbert_m & 1)) return GN_ERR_INVALID;
+  }
+  if (p->precision != GN_PREC_FP64 && p->precision != GN_PREC_SPLIT_BF16) return GN_ERR_INVALID;
+  if (p->precision == GN_PREC_SPLIT_BF16 && (p->n_slices < 1 || p->n_slices > 8)) return GN_ERR_INVALID;
+  return GN_OK;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+void free_all(gn_handle* h) {
+  void* ptrs[] = {h->wt, h->theta_t, h->r, h->J, h->G, h->A, h->Linv, h->g, h->delta, h->vtmp, h->red,
+                  h->flag, h->gpart, h->kf, h->dcoef, h->snode, h->gnode, h->Jg, h->ug, h->sU, h->tnode,
+                  h->split_ws};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->hpin) cudaFreeHost(h->hpin);
+}
+
+// Device copies of the normalisation point live at the end of vtmp's header.
+struct Pass {
+  int mode;
+  double* r;        // r~ destination (may be null)
+  double* J;        // Jacobian block destination
+  int64_t ldJ, jlo, jhi;
+  const double* seed;
+};
+
+double* norm_point(gn_handle* h) { return h->red + 512; }
+
+// Evaluate rows (all kinds) at (theta, lambda) in one mode.  In gradient mode
+// the per-warp partials are reduced into grad (P+1 entries).
+int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, double* grad) {
+  cudaStream_t st = h->st;
+  GN_TRY_CUDA(launch_transpose_weights(h->net, theta, h->wt, st));
+  JetArgs a;
+  memset(&a, 0, sizeof(a));
+  a.net = h->net;
+  a.eq = h->eq;
+  a.theta = theta;
+  a.wt = h->wt;
+  a.lam = lam;
+  a.flag = h->flag;
+  a.ldg = round_up(h->Pp, 16);
+  a.gpart = h->gpart;
+  const int64_t n = h->p.n_pts;
+  if (ps.mode == MODE_GRADIENT) GN_TRY_CUDA(cudaMemsetAsync(h->gpart, 0, h->gpart_warps * a.ldg * 8, st));
+
+  // CCF: g at the positive Hilbert nodes (and their Jacobian rows), then U's K part.
+  if (h->eq == GN_CCF) {
+    JetArgs b = a;
+    b.kind = KIND_NODE;
+    b.mode = (ps.mode == MODE_JACOBIAN) ? MODE_JACOBIAN : MODE_RESIDUAL;
+    b.n = h->Mh;
+    b.y = h->snode;
+    b.ystride = h->Mh;
+    b.wscale = 1.0;
+    b.row0 = 0;
+    b.r = h->gnode;
+    b.J = h->Jg;
+    b.ldJ = h->ldJ;
+    b.jrow_lo = 0;
+    b.jrow_hi = h->Mh;
+    GN_TRY_CUDA(launch_jet(b, st, nullptr));
+    GN_TRY_CUDA(dgemv_n(h->kf, h->Mh, n, h->Mh, h->gnode, h->ug, 0.0, st));
+  }
+  // interior points
+  {
+    JetArgs b = a;
+    b.kind = KIND_INTERIOR;
+    b.mode = ps.mode;
+    b.n = n;
+    b.y = h->p.y;
+    b.ystride = n;
+    b.rho = h->p.rho;
+    b.wscale = n > 0 ? sqrt(2.0 / ((double)n * h->ne)) : 0.0;
+    b.row0 = 0;
+    b.r = ps.r;
+    b.J = ps.J;
+    b.ldJ = ps.ldJ;
+    b.jrow_lo = ps.jlo;
+    b.jrow_hi = ps.jhi;
+    b.seed = ps.seed;
+    b.ug = h->ug;
+    b.dcoef = h->dcoef;
+    b.sU = h->sU;
+    GN_TRY_CUDA(launch_jet(b, st, nullptr));
+  }
+  // wall points
+  if (h->p.n_bnd > 0) {
+    JetArgs b = a;
+    b.kind = KIND_WALL;
+    b.mode = ps.mode;
+    b.n = h->p.n_bnd;
+    b.y = h->p.y_bnd;
+    b.ystride = h->p.n_bnd;
+    b.wscale = sqrt(2.0 * h->p.c_bnd / (double)h->p.n_bnd);
+    b.row0 = n * h->ne;
+    b.r = ps.r;
+    b.J = ps.J;
+    b.ldJ = ps.ldJ;
+    b.jrow_lo = ps.jlo;
+    b.jrow_hi = ps.jhi;
+    b.seed = ps.seed;
+    GN_TRY_CUDA(launch_jet(b, st, nullptr));
+  }
+  // normalisation row
+  {
+    JetArgs b = a;
+    b.kind = KIND_NORM;
+    b.mode = ps.mode;
+    b.n = 1;
+    b.y = norm_point(h);
+    b.ystride = 1;
+    b.wscale = sqrt(2.0 * h->p.c_norm_w);
+    b.c_norm = h->p.c_norm;
+    b.row0 = h->n_rows - 1;
+    b.r = ps.r;
+    b.J = ps.J;
+    b.ldJ = ps.ldJ;
+    b.jrow_lo = ps.jlo;
+    b.jrow_hi = ps.jhi;
+    b.seed = ps.seed;
+    GN_TRY_CUDA(launch_jet(b, st, nullptr));
+  }
+  if (h->eq == GN_CCF && ps.mode == MODE_JACOBIAN) {
+    // J[i, :] += sU_i * sum_j' Kf[i][j'] Jg[j', :] for interior rows inside the block
+    const int64_t lo = ps.jlo > 0 ? ps.jlo : 0;
+    const int64_t hi = ps.jhi < n ? ps.jhi : n;
+    if (hi > lo)
+      GN_TRY_CUDA(dgemm(hi - lo, h->Pp, h->Mh, 1.0, h->kf + lo * h->Mh, h->Mh, true, h->Jg, h->ldJ, false, 1.0,
+                        ps.J + (lo - ps.jlo) * ps.ldJ, ps.ldJ, false, h->sU + lo, st));
+  }
+  if (ps.mode == MODE_GRADIENT) {
+    if (h->eq == GN_CCF && n > 0) {
+      // t_j' = sum_i Kf[i][j'] c_i (c = seed * w * dR/dU, left in sU), then node pass seeded by t
+      GN_TRY_CUDA(dgemv_t_scratch(h->kf, h->Mh, n, h->Mh, h->sU, h->tnode, 0.0, h->vtmp, st));
+      JetArgs b = a;
+      b.kind = KIND_NODE;
+      b.mode = MODE_GRADIENT;
+      b.n = h->Mh;
+      b.y = h->snode;
+      b.ystride = h->Mh;
+      b.wscale = 1.0;
+      b.row0 = 0;
+      b.r = nullptr;
+      b.seed = h->tnode;
+      GN_TRY_CUDA(launch_jet(b, st, nullptr));
+    }
+    GN_TRY_CUDA(launch_gpart_reduce(h->gpart, h->gpart_warps, a.ldg, h->Pp, grad, 0, st));
+  }
+  return GN_OK;
+}
+
+// loss = 1/2 |r|^2 into hpin[slot] (device copy, then host after sync)
+int loss_of(gn_handle* h, const double* r, int slot) {
+  GN_TRY_CUDA(sumsq_and_flag(r, h->n_rows, h->red, h->st));
+  GN_TRY_CUDA(finish_sum(h->red, h->red + 256 + slot, h->st));
+  return GN_OK;
+}
+
+int residual_loss(gn_handle* h, const double* theta, double lam, double* r, double* loss) {
+  Pass ps = {MODE_RESIDUAL, r, nullptr, 0, 0, 0, nullptr};
+  int rc = run_pass(h, theta, lam, ps, nullptr);
+  if (rc) return rc;
+  if (loss) {
+    rc = loss_of(h, r, 0);
+    if (rc) return rc;
+    GN_TRY_CUDA(cudaMemcpyAsync(h->hpin, h->red + 256, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    GN_TRY_CUDA(cudaStreamSynchronize(h->st));
+    *loss = 0.5 * h->hpin[0];
+  }
+  return GN_OK;
+}
+
+int gram_into(gn_handle* h, const double* J, int64_t ld, int64_t nrows, const double* r, double* G, double* g,
+              int precision, int accumulate) {
+  const double beta = accumulate ? 1.0 : 0.0;
+  if (precision == GN_PREC_SPLIT_BF16) {
+    int rc = split_gram(h, J, ld, nrows, G, accumulate);
+    if (rc) return rc;
+  } else {
+    GN_TRY_CUDA(dgemm(h->Pp, h->Pp, nrows, 1.0, J, ld, false, J, ld, false, beta, G, h->Pp, true, nullptr, h->st));
+  }
+  if (r && g) GN_TRY_CUDA(dgemv_t_scratch(J, ld, nrows, h->Pp, r, g, beta, h->vtmp, h->st));
+  return GN_OK;
+}
+
+struct Timer {
+  cudaEvent_t ev[9];
+  int n = 0;
+  cudaStream_t st;
+  explicit Timer(cudaStream_t s) : st(s) {
+    for (auto& e : ev) cudaEventCreate(&e);
+  }
+  ~Timer() {
+    for (auto& e : ev) cudaEventDestroy(e);
+  }
+  void mark(int i) { cudaEventRecord(ev[i], st); }
+  double ms(int a, int b) {
+    float v = 0.f;
+    cudaEventElapsedTime(&v, ev[a], ev[b]);
+    return v;
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int64_t gn_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+const char* gn_error_string(int code) {
+  switch (code) {
+    case GN_OK: return "ok";
+    case GN_WARN_NO_DECREASE: return "line search found no decrease; step rejected, damping raised";
+    case GN_ERR_INVALID: return "invalid argument";
+    case GN_ERR_CUDA: return "CUDA runtime error";
+    case GN_ERR_OOM: return "device allocation failed";
+    case GN_ERR_NONFINITE: return "non-finite residual or loss";
+    case GN_ERR_NOT_SPD: return "damped Gauss-Newton matrix not positive definite";
+    case GN_ERR_TIMEOUT: return "bounded device wait timed out";
+    case GN_ERR_UNSUPPORTED: return "unsupported on this device or build";
+    default: return "unknown status";
+  }
+}
+
+int gn_init(const gn_problem* p, void* cuda_stream, gn_handle** out) {
+  if (!out) return GN_ERR_INVALID;
+  *out = nullptr;
+  int rc = validate(p);
+  if (rc) return rc;
+  gn_handle* h = new (std::nothrow) gn_handle;
+  if (!h) return GN_ERR_OOM;
+  memset(h, 0, sizeof(*h));
+  h->p = *p;
+  if (h->p.n_pts == 0) h->p.y = nullptr;
+  GN_TRY_CUDA(cudaGetDevice(&h->dev));
+  h->st = (cudaStream_t)cuda_stream;
+  h->eq = p->equation;
+  h->d = dim_of(h->eq);
+  h->nf = fields_of(h->eq);
+  h->ne = neq_of(h->eq);
+  NetDesc& net = h->net;
+  net.L = p->n_layers;
+  net.maxw = 2;
+  int64_t off = 0, offT = 0;
+  for (int l = 0; l <= net.L; l++) {
+    net.w[l] = p->widths[l];
+    if (net.w[l] > net.maxw) net.maxw = net.w[l];
+  }
+  for (int l = 0; l < net.L; l++) {
+    net.offW[l] = off;
+    net.offT[l] = offT;
+    off += (int64_t)net.w[l] * net.w[l + 1];
+    offT += (int64_t)net.w[l] * net.w[l + 1];
+    net.offB[l] = off;
+    off += net.w[l + 1];
+  }
+  net.P = off;
+  h->P = off;
+  h->Pp = off + 1;
+  h->n_rows = p->n_pts * h->ne + (h->d == 2 ? p->n_bnd : 0) + 1;
+  h->ldJ = round_up(h->Pp, 16);
+  const double jbytes = (double)h->n_rows * h->ldJ * 8.0;
+  const double jcap = 32.0 * (1ull << 30);
+  h->jrows = jbytes <= jcap ? h->n_rows : (int64_t)(jcap / (h->ldJ * 8.0));
+  h->precision = p->precision;
+  h->n_slices = p->n_slices > 0 ? p->n_slices : 4;
+  h->gpart_warps = jet_gpart_warps(net, h->d, h->nf, p->n_pts);
+
+  bool ok = true;
+  auto A = [&](cudaError_t e) {
+    if (e != cudaSuccess) ok = false;
+  };
+  const int64_t Pp = h->Pp;
+  const int64_t nvec = (Pp > h->n_rows ? Pp : h->n_rows);
+  A(dalloc(&h->wt, h->P));
+  A(dalloc(&h->theta_t, h->P));
+  A(dalloc(&h->r, h->n_rows));
+  if (ok) A(dalloc(&h->J, (size_t)h->jrows * h->ldJ));
+  if (ok) A(dalloc(&h->G, (size_t)Pp * Pp));
+  if (ok) A(dalloc(&h->A, (size_t)Pp * Pp));
+  A(dalloc(&h->Linv, (size_t)((Pp + kCholNB - 1) / kCholNB) * kCholNB * kCholNB));
+  A(dalloc(&h->g, Pp));
+  A(dalloc(&h->delta, Pp));
+  A(dalloc(&h->vtmp, (size_t)kGemvChunks * (nvec + 16)));
+  A(dalloc(&h->red, 1024));
+  A(dalloc(&h->flag, 4));
+  if (ok) A(dalloc(&h->gpart, (size_t)h->gpart_warps * round_up(Pp, 16)));
+  if (cudaMallocHost((void**)&h->hpin, 64 * sizeof(double)) != cudaSuccess) ok = false;
+  if (h->eq == GN_CCF) {
+    h->M = p->hilbert_m;
+    h->Mh = h->M / 2;
+    A(dalloc(&h->kf, (size_t)p->n_pts * h->Mh));
+    A(dalloc(&h->dcoef, p->n_pts));
+    A(dalloc(&h->snode, h->Mh));
+    A(dalloc(&h->gnode, h->Mh));
+    A(dalloc(&h->Jg, (size_t)h->Mh * h->ldJ));
+    A(dalloc(&h->ug, p->n_pts));
+    A(dalloc(&h->sU, p->n_pts));
+    A(dalloc(&h->tnode, h->Mh));
+  }
+  if (!ok) {
+    cudaGetLastError();
+    free_all(h);
+    delete h;
+    return GN_ERR_OOM;
+  }
+  cudaError_t e = cudaMemsetAsync(h->flag, 0, 4 * sizeof(int), h->st);
+  double yn[2] = {p->y_norm[0], p->y_norm[1]};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(norm_point(h), yn, 2 * sizeof(double), cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess && h->eq == GN_CCF) e = hilbert_build(p->y, p->n_pts, h->M, h->kf, h->dcoef, h->snode, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return GN_ERR_CUDA;
+  }
+  *out = h;
+  return GN_OK;
+}
+
+int gn_destroy(gn_handle* h) {
+  if (!h) return GN_OK;
+  cudaStreamSynchronize(h->st);
+  free_all(h);
+  if (h->tmaps) free(h->tmaps);
+  delete h;
+  return GN_OK;
+}
+
+int gn_param_count(const gn_handle* h, int64_t* P) {
+  if (!h || !P) return GN_ERR_INVALID;
+  *P = h->P;
+  return GN_OK;
+}
+
+int gn_row_count(const gn_handle* h, int64_t* n_rows) {
+  if (!h || !n_rows) return GN_ERR_INVALID;
+  *n_rows = h->n_rows;
+  return GN_OK;
+}
+
+int gn_set_precision(gn_handle* h, int precision, int n_slices) {
+  if (!h) return GN_ERR_INVALID;
+  if (precision != GN_PREC_FP64 && precision != GN_PREC_SPLIT_BF16) return GN_ERR_INVALID;
+  if (precision == GN_PREC_SPLIT_BF16 && (n_slices < 1 || n_slices > 8)) return GN_ERR_INVALID;
+  h->precision = precision;
+  if (n_slices > 0) h->n_slices = n_slices;
+  return GN_OK;
+}
+
+int gn_residual(gn_handle* h, const double* theta, double lambda, double* r_out, double* loss_out) {
+  if (!h || !theta) return GN_ERR_INVALID;
+  double* r = r_out ? r_out : h->r;
+  double loss = 0.0;
+  int rc = residual_loss(h, theta, lambda, r, loss_out ? &loss : nullptr);
+  if (rc) return rc;
+  if (loss_out) {
+    *loss_out = loss;
+    if (!std::isfinite(loss)) return GN_ERR_NONFINITE;
+  }
+  return GN_OK;
+}
+
+int gn_jacobian(gn_handle* h, const double* theta, double lambda, double* J_out, int64_t ld, int64_t row0,
+                int64_t nrows) {
+  if (!h || !theta || !J_out || ld < h->Pp || row0 < 0 || nrows < 0 || row0 + nrows > h->n_rows)
+    return GN_ERR_INVALID;
+  if (nrows == 0) return GN_OK;
+  Pass ps = {MODE_JACOBIAN, h->r, J_out, ld, row0, row0 + nrows, nullptr};
+  return run_pass(h, theta, lambda, ps, nullptr);
+}
+
+int gn_gradient(gn_handle* h, const double* theta, double lambda, const double* seed, double* grad_out) {
+  if (!h || !theta || !grad_out) return GN_ERR_INVALID;
+  Pass ps = {MODE_GRADIENT, h->r, nullptr, 0, 0, 0, seed};
+  return run_pass(h, theta, lambda, ps, grad_out);
+}
+
+int gn_gram(gn_handle* h, const double* J, int64_t ld, int64_t nrows, const double* r, double* G_out, double* g_out,
+            int precision, int accumulate) {
+  if (!h || !J || !G_out || ld < h->Pp || nrows < 0) return GN_ERR_INVALID;
+  if (precision != GN_PREC_FP64 && precision != GN_PREC_SPLIT_BF16) return GN_ERR_INVALID;
+  return gram_into(h, J, ld, nrows, r, G_out, g_out, precision, accumulate);
+}
+
+int gn_damped_solve(gn_handle* h, const double* G, const double* g, double* gamma, double* delta_out,
+                    int* retries_out) {
+  if (!h || !G || !g || !gamma || !delta_out) return GN_ERR_INVALID;
+  const int64_t Pp = h->Pp;
+  int retries = 0;
+  for (;;) {
+    GN_TRY_CUDA(copy_add_diag(G, h->A, Pp, Pp, *gamma, h->st));
+    GN_TRY_CUDA(cudaMemsetAsync(h->flag + 1, 0, sizeof(int), h->st));
+    GN_TRY_CUDA(cholesky_factor(h->A, Pp, Pp, h->Linv, h->flag + 1, h->st));
+    int hflag = 0;
+    GN_TRY_CUDA(cudaMemcpyAsync(&h->hpin[8], h->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    GN_TRY_CUDA(cudaStreamSynchronize(h->st));
+    memcpy(&hflag, &h->hpin[8], sizeof(int));
+    if (!hflag) break;
+    if (retries == 5) {
+      if (retries_out) *retries_out = retries;
+      return GN_ERR_NOT_SPD;
+    }
+    *gamma *= 10.0;
+    retries++;
+  }
+  if (retries_out) *retries_out = retries;
+  GN_TRY_CUDA(cholesky_solve(h->A, Pp, Pp, h->Linv, g, delta_out, nullptr, h->st));
+  return GN_OK;
+}
+
+int gn_max_residual(gn_handle* h, const double* theta, double lambda, double* out) {
+  if (!h || !theta || !out) return GN_ERR_INVALID;
+  // unweighted interior residuals: evaluate with unit row weights into r
+  Pass ps = {MODE_RESIDUAL, h->r, nullptr, 0, 0, 0, nullptr};
+  int rc = run_pass(h, theta, lambda, ps, nullptr);
+  if (rc) return rc;
+  const int64_t nint = h->p.n_pts * h->ne;
+  // rows carry sqrt(2 rho/(N N_E)); undo it for rho == 1 (documented: max over unweighted R_k)
+  GN_TRY_CUDA(max_abs_rows(h->r, nint, 0, h->red, h->st));
+  GN_TRY_CUDA(finish_max(h->red, h->red + 300, h->st));
+  GN_TRY_CUDA(cudaMemcpyAsync(h->hpin, h->red + 300, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  GN_TRY_CUDA(cudaStreamSynchronize(h->st));
+  const double w = nint > 0 ? sqrt(2.0 / ((double)h->p.n_pts * h->ne)) : 1.0;
+  *out = h->hpin[0] / w;
+  return GN_OK;
+}
+
+int gn_step(gn_handle* h, double* theta, double* lambda, double* damping, gn_step_info* info) {
+  if (!h || !theta || !lambda || !damping) return GN_ERR_INVALID;
+  gn_step_info inf;
+  memset(&inf, 0, sizeof(inf));
+  cudaStream_t st = h->st;
+  const int64_t Pp = h->Pp, P = h->P;
+  const double lam = *lambda;
+  double gamma = *damping;
+  Timer tm(st);
+  tm.mark(0);
+  // 1. rows and Jacobian, Gram and gradient, streamed in row blocks
+  int rc = GN_OK;
+  const int64_t nblk = (h->n_rows + h->jrows - 1) / h->jrows;
+  double t_jac = 0.0, t_gram = 0.0;
+  for (int64_t b = 0; b < nblk; b++) {
+    const int64_t lo = b * h->jrows;
+    const int64_t hi = (lo + h->jrows < h->n_rows) ? lo + h->jrows : h->n_rows;
+    Pass ps = {MODE_JACOBIAN, h->r, h->J, h->ldJ, lo, hi, nullptr};
+    tm.mark(1);
+    rc = run_pass(h, theta, lam, ps, nullptr);
+    if (rc) return rc;
+    tm.mark(2);
+    rc = gram_into(h, h->J, h->ldJ, hi - lo, h->r + lo, h->G, h->g, h->precision, b > 0);
+    if (rc) return rc;
+    tm.mark(3);
+    if (nblk > 1) {
+      GN_TRY_CUDA(cudaEventSynchronize(tm.ev[3]));
+      t_jac += tm.ms(1, 2);
+      t_gram += tm.ms(2, 3);
+    }
+  }
+  GN_TRY_CUDA(mirror_lower(h->G, Pp, Pp, st));
+  rc = loss_of(h, h->r, 0);
+  if (rc) return rc;
+  tm.mark(4);
+  if (nblk == 1) {
+    GN_TRY_CUDA(cudaEventSynchronize(tm.ev[4]));
+    t_jac = tm.ms(1, 2);
+    t_gram = tm.ms(2, 3);
+  }
+  // 2. damped solve
+  int retries = 0;
+  rc = gn_damped_solve(h, h->G, h->g, &gamma, h->delta, &retries);
+  tm.mark(5);
+  inf.chol_retries = retries;
+  inf.gamma_used = gamma;
+  if (rc) {
+    inf.status = rc;
+    if (info) *info = inf;
+    return rc;
+  }
+  // 3. scalars for the model: g.delta, delta.G.delta, delta[P], h0
+  GN_TRY_CUDA(dot_partial(h->g, h->delta, Pp, h->red, st));
+  GN_TRY_CUDA(finish_sum(h->red, h->red + 257, st));
+  GN_TRY_CUDA(dgemv_n(h->G, Pp, Pp, Pp, h->delta, h->vtmp, 0.0, st));
+  GN_TRY_CUDA(dot_partial(h->delta, h->vtmp, Pp, h->red, st));
+  GN_TRY_CUDA(finish_sum(h->red, h->red + 258, st));
+  GN_TRY_CUDA(cudaMemcpyAsync(h->red + 259, h->delta + P, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  GN_TRY_CUDA(cudaMemcpyAsync(h->hpin, h->red + 256, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  GN_TRY_CUDA(cudaStreamSynchronize(st));
+  const double h0 = 0.5 * h->hpin[0];
+  const double gd = h->hpin[1];
+  const double dGd = h->hpin[2];
+  const double dlam = h->hpin[3];
+  inf.loss_before = h0;
+  inf.loss_after = h0;
+  tm.mark(6);
+  if (!std::isfinite(h0)) {
+    inf.status = GN_ERR_NONFINITE;
+    if (info) *info = inf;
+    return GN_ERR_NONFINITE;
+  }
+  // 4. Armijo backtracking on residual-only evaluations
+  const double c1 = 1e-4;
+  double alpha = 1.0;
+  bool accepted = false;
+  double ht = h0;
+  for (int trial = 0; trial < 8; trial++) {
+    GN_TRY_CUDA(axpy_trial(theta, h->delta, alpha, P, h->theta_t, st));
+    const double lt = lam - alpha * dlam;
+    rc = residual_loss(h, h->theta_t, lt, h->r, &ht);
+    if (rc) return rc;
+    inf.n_trials = trial + 1;
+    if (std::isfinite(ht) && ht <= h0 - c1 * alpha * gd) {
+      accepted = true;
+      break;
+    }
+    alpha *= 0.5;
+  }
+  tm.mark(7);
+  if (accepted) {
+    const double pred = alpha * gd - 0.5 * alpha * alpha * dGd;
+    const double rho = pred != 0.0 ? (h0 - ht) / pred : 1.0;
+    if (rho < 0.25) gamma *= 1.5;
+    else if (rho > 0.75) gamma *= 2.0 / 3.0;
+    GN_TRY_CUDA(cudaMemcpyAsync(theta, h->theta_t, P * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    *lambda = lam - alpha * dlam;
+    inf.alpha = alpha;
+    inf.rho = rho;
+    inf.loss_after = ht;
+    inf.status = GN_OK;
+  } else {
+    gamma *= 10.0;
+    inf.status = GN_WARN_NO_DECREASE;
+  }
+  *damping = gamma;
+  tm.mark(8);
+  GN_TRY_CUDA(cudaEventSynchronize(tm.ev[8]));
+  inf.ms_phase[0] = t_jac;
+  inf.ms_phase[1] = t_gram;
+  inf.ms_phase[2] = 0.0;
+  inf.ms_phase[3] = tm.ms(4, 5);
+  inf.ms_phase[4] = tm.ms(5, 6);
+  inf.ms_phase[5] = tm.ms(6, 7);
+  inf.ms_phase[6] = tm.ms(0, 8);
+  if (info) *info = inf;
+  return inf.status;
+}
+
+}  // extern "C"

@@ -1,0 +1,164 @@
+// Internal declarations of libgn: handle layout, network descriptor and the
+// device launchers shared between translation units.  Nothing here is part
+// of the public ABI (include/gn.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "../../include/gn.h"
+
+namespace gn {
+
+constexpr int kWarp = 32;
+
+// Kernels launched by this library in this process (diagnostic, gn_kernel_launches).
+extern std::atomic<long long> g_launches;
+inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// Kinds of "points" whose rows the jet kernel produces.
+enum PointKind : int {
+  KIND_INTERIOR = 0,  // interior collocation point: N_E residual rows
+  KIND_WALL = 1,      // wall point (2D): one row, the stream function value
+  KIND_NORM = 2,      // normalisation point: one row
+  KIND_NODE = 3       // CCF Hilbert node: one row, g = Theta / y at the node
+};
+
+enum JetMode : int { MODE_RESIDUAL = 0, MODE_JACOBIAN = 1, MODE_GRADIENT = 2 };
+
+struct NetDesc {
+  int L;                            // linear layers
+  int w[GN_MAX_LAYERS + 1];         // widths
+  int64_t offW[GN_MAX_LAYERS];      // W_l offset in theta (out x in, row-major)
+  int64_t offB[GN_MAX_LAYERS];      // b_l offset in theta
+  int64_t offT[GN_MAX_LAYERS];      // W_l^T offset in the transposed copy (in x out)
+  int maxw;                         // widest layer (including input / output)
+  int64_t P;                        // parameter count
+};
+
+// Arguments of one jet-kernel launch (one point kind).
+struct JetArgs {
+  NetDesc net;
+  int eq;
+  int kind;
+  int mode;
+  const double* theta;   // [P]
+  const double* wt;      // transposed weights
+  double lam;
+  int64_t n;             // points of this kind
+  const double* y;       // SoA [d][ystride]
+  int64_t ystride;
+  const double* rho;     // interior weights (may be null)
+  double wscale;         // row weight factor (see jet.cu)
+  double c_norm;         // normalisation target (KIND_NORM)
+  int64_t row0;          // row of point 0, first equation
+  double* r;             // r~ output (may be null)
+  double* J;             // Jacobian output (MODE_JACOBIAN)
+  int64_t ldJ;
+  int64_t jrow_lo, jrow_hi;  // rows written are [jrow_lo, jrow_hi), at J + (row - jrow_lo) * ldJ
+  double* gpart;         // MODE_GRADIENT: per-warp partial gradients [total warps][ldg]
+  int64_t ldg;
+  const double* seed;    // MODE_GRADIENT: row seeds (null: seed = r~ itself)
+  const double* ug;      // CCF: sum_j K_ij g_j per interior point
+  const double* dcoef;   // CCF: diagonal coefficient D_i per interior point
+  double* sU;            // CCF out: w_i dR/dU per interior point (times the seed in gradient mode)
+  int* flag;             // bit 0: non-finite residual seen
+};
+
+struct Workspace;
+
+}  // namespace gn
+
+struct gn_handle {
+  gn_problem p;
+  int dev;
+  cudaStream_t st;
+  int eq, d, nf, ne;
+  gn::NetDesc net;
+  int64_t P, Pp;          // P and P+1
+  int64_t n_rows;
+  int64_t ldJ;            // leading dimension of the internal J~ (>= P+1, multiple of 16)
+  int64_t jrows;          // rows of the internal J~ block buffer
+  int precision, n_slices;
+  // device workspace
+  double* wt;             // transposed weights [P]
+  double* theta_t;        // trial parameters [P]
+  double* r;              // r~ [n_rows]
+  double* J;              // J~ row block [jrows x ldJ]
+  double* G;              // Gram [Pp x Pp] row-major, symmetric after mirroring
+  double* A;              // factor workspace [Pp x Pp]
+  double* Linv;           // inverses of the diagonal blocks [nblk x 64 x 64]
+  double* g;              // gradient [Pp]
+  double* delta;          // step [Pp]
+  double* vtmp;           // scratch [max(Pp, n_rows)]
+  double* red;            // reduction partials
+  int* flag;              // device status word
+  double* hpin;           // pinned host scalars
+  double* gpart;          // per-warp gradient partials
+  int64_t gpart_warps;
+  // CCF Hilbert operator (folded on the antisymmetric node pairs)
+  int M, Mh;
+  double* kf;             // [n_pts x Mh]
+  double* dcoef;          // [n_pts]
+  double* snode;          // [Mh] positive node coordinates
+  double* gnode;          // [Mh] g at the nodes
+  double* Jg;             // [Mh x ldJ] Jacobian of g at the nodes (last column d/d lambda)
+  double* ug;             // [n_pts]
+  double* sU;             // [n_pts]
+  double* tnode;          // [Mh] gradient-mode node seeds
+  // split-precision Gram workspace (allocated on first use)
+  void* split_ws;
+  size_t split_ws_bytes;
+  void* tmaps;            // host copies of TMA descriptors
+};
+
+namespace gn {
+
+// ---- launchers (host functions implemented in the .cu files) -----------
+cudaError_t launch_transpose_weights(const NetDesc& net, const double* theta, double* wt, cudaStream_t st);
+cudaError_t launch_jet(const JetArgs& a, cudaStream_t st, int64_t* warps_used);
+int jet_gpart_warps(const NetDesc& net, int d, int nf, int64_t n_max);
+cudaError_t launch_gpart_reduce(const double* gpart, int64_t warps, int64_t ldg, int64_t n,
+                                double* out, int accumulate, cudaStream_t st);
+
+// FP64 GEMM: C(m x n) = alpha * sum_k A(m,k) B(k,n) + beta * C, optional row scale.
+// a_kcontig: A(m,k) = A[m*lda + k] (else A[k*lda + m]); b_kcontig: B(k,n) = B[n*ldb + k]
+// (else B[k*ldb + n]).  lower: only tiles with row tile >= col tile are computed.
+// rowscale (may be null): C[m][n] = beta C + rowscale[m] * alpha * acc.
+cudaError_t dgemm(int64_t m, int64_t n, int64_t k, double alpha, const double* A, int64_t lda,
+                  bool a_kcontig, const double* B, int64_t ldb, bool b_kcontig, double beta, double* C,
+                  int64_t ldc, bool lower, const double* rowscale, cudaStream_t st);
+
+// Vector helpers (deterministic reductions).
+cudaError_t dot_partial(const double* x, const double* y, int64_t n, double* red, cudaStream_t st);
+cudaError_t sumsq_and_flag(const double* x, int64_t n, double* red, cudaStream_t st);
+cudaError_t finish_sum(double* red, double* out_dev, cudaStream_t st);
+cudaError_t axpy_trial(const double* theta, const double* delta, double alpha, int64_t P, double* out,
+                       cudaStream_t st);
+// y[n] = beta*y + A^T x, A is m x n row-major; part: scratch of kGemvChunks * n doubles
+constexpr int kGemvChunks = 64;
+cudaError_t dgemv_t_scratch(const double* A, int64_t lda, int64_t m, int64_t n, const double* x, double* y,
+                            double beta, double* part, cudaStream_t st);
+cudaError_t dgemv_n(const double* A, int64_t lda, int64_t m, int64_t n, const double* x, double* y,
+                    double beta, cudaStream_t st);   // y[m] = beta*y + A x
+cudaError_t mirror_lower(double* G, int64_t n, int64_t ld, cudaStream_t st);
+cudaError_t copy_add_diag(const double* G, double* A, int64_t n, int64_t ld, double gamma, cudaStream_t st);
+cudaError_t max_abs_rows(const double* r, int64_t n, int stride_valid, double* red, cudaStream_t st);
+cudaError_t finish_max(double* red, double* out_dev, cudaStream_t st);
+
+// CCF Hilbert operator construction and contractions.
+cudaError_t hilbert_build(const double* y, int64_t n, int M, double* kf, double* dcoef, double* snode,
+                          cudaStream_t st);
+
+// Cholesky (FP64, blocked, lower, in place on A row-major) and solves.
+constexpr int kCholNB = 64;
+cudaError_t cholesky_factor(double* A, int64_t n, int64_t lda, double* Linv, int* flag, cudaStream_t st);
+cudaError_t cholesky_solve(const double* A, int64_t n, int64_t lda, const double* Linv, const double* b,
+                           double* x, double* tmp, cudaStream_t st);
+
+// Split-precision (Ozaki, BF16 slices on tcgen05) Gram; returns GN_ERR_* codes.
+int split_gram(gn_handle* h, const double* J, int64_t ld, int64_t nrows, double* G, int accumulate);
+
+}  // namespace gn

@@ -1,0 +1,289 @@
+"""Thin Python binding of libgn (include/gn.h): argument marshalling only.
+
+Every step of the Gauss-Newton path runs in the library's CUDA kernels; this
+module converts torch tensors to device pointers and calls the C ABI by the
+same names.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if the shared library is missing, `lib()` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import inputs as _inputs
+
+GN_OK = 0
+GN_WARN_NO_DECREASE = 1
+GN_ERR_INVALID = -1
+GN_ERR_CUDA = -2
+GN_ERR_OOM = -3
+GN_ERR_NONFINITE = -4
+GN_ERR_NOT_SPD = -5
+GN_ERR_TIMEOUT = -6
+GN_ERR_UNSUPPORTED = -7
+
+GN_PREC_FP64 = 0
+GN_PREC_SPLIT_BF16 = 1
+GN_MAX_LAYERS = 8
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libgn.so")
+
+
+class gn_problem(ctypes.Structure):
+    _fields_ = [
+        ("equation", ctypes.c_int),
+        ("n_layers", ctypes.c_int),
+        ("widths", ctypes.c_int * (GN_MAX_LAYERS + 1)),
+        ("n_pts", ctypes.c_int64),
+        ("y", ctypes.c_void_p),
+        ("rho", ctypes.c_void_p),
+        ("n_bnd", ctypes.c_int64),
+        ("y_bnd", ctypes.c_void_p),
+        ("c_bnd", ctypes.c_double),
+        ("y_norm", ctypes.c_double * 2),
+        ("c_norm", ctypes.c_double),
+        ("c_norm_w", ctypes.c_double),
+        ("hilbert_m", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("n_slices", ctypes.c_int),
+    ]
+
+
+class gn_step_info(ctypes.Structure):
+    _fields_ = [
+        ("loss_before", ctypes.c_double),
+        ("loss_after", ctypes.c_double),
+        ("alpha", ctypes.c_double),
+        ("rho", ctypes.c_double),
+        ("gamma_used", ctypes.c_double),
+        ("chol_retries", ctypes.c_int),
+        ("n_trials", ctypes.c_int),
+        ("status", ctypes.c_int),
+        ("ms_phase", ctypes.c_double * 8),
+    ]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k != "ms_phase"}
+        d["ms_phase"] = list(self.ms_phase)
+        return d
+
+
+_LIB = None
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+
+EXPORTS = {
+    "gn_init": (ctypes.c_int, [ctypes.POINTER(gn_problem), _P, ctypes.POINTER(_P)]),
+    "gn_destroy": (ctypes.c_int, [_P]),
+    "gn_param_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "gn_row_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "gn_set_precision": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    "gn_residual": (ctypes.c_int, [_P, _P, _D, _P, ctypes.POINTER(_D)]),
+    "gn_jacobian": (ctypes.c_int, [_P, _P, _D, _P, _I64, _I64, _I64]),
+    "gn_gradient": (ctypes.c_int, [_P, _P, _D, _P, _P]),
+    "gn_gram": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _P, _P, ctypes.c_int, ctypes.c_int]),
+    "gn_damped_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_D), _P, ctypes.POINTER(ctypes.c_int)]),
+    "gn_step": (ctypes.c_int, [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(gn_step_info)]),
+    "gn_max_residual": (ctypes.c_int, [_P, _P, _D, ctypes.POINTER(_D)]),
+    "gn_kernel_launches": (ctypes.c_int64, []),
+    "gn_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def lib():
+    """Load libgn.so (built in-tree by paper_2509_14185_gb300.build)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgn.so is not built ({LIB_PATH}); run paper_2509_14185_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+class GNError(RuntimeError):
+    def __init__(self, code, where):
+        msg = lib().gn_error_string(code).decode()
+        super().__init__(f"{where}: {msg} ({code})")
+        self.code = code
+
+
+def _check(code, where):
+    if code < 0:
+        raise GNError(code, where)
+    return code
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous(), "expected a contiguous cuda float64 tensor"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class GNProblem:
+    """One profile fit bound to a libgn handle (device memory owned by torch and libgn)."""
+
+    def __init__(self, equation, widths, y, y_bnd=None, rho=None, c_bnd=1.0, y_norm=(1.0, 0.0), c_norm=1.0,
+                 c_norm_w=1.0, hilbert_m=1024, precision=GN_PREC_FP64, n_slices=4, device="cuda", stream=None):
+        lib()
+        self.device = torch.device(device)
+        self.equation = int(equation)
+        self.widths = list(widths)
+        self.d = _inputs.EQUATION_DIM[self.equation]
+        y = np.asarray(y, dtype=np.float64).reshape(self.d, -1)
+        self.y = torch.from_numpy(np.ascontiguousarray(y)).to(self.device)
+        self.n_pts = y.shape[1]
+        yb = np.zeros((self.d, 0)) if y_bnd is None else np.asarray(y_bnd, dtype=np.float64).reshape(self.d, -1)
+        self.y_bnd = torch.from_numpy(np.ascontiguousarray(yb)).to(self.device) if yb.size else None
+        self.n_bnd = yb.shape[1] if yb.size else 0
+        self.rho = None if rho is None else torch.as_tensor(rho, dtype=torch.float64, device=self.device).contiguous()
+        p = gn_problem()
+        p.equation = self.equation
+        p.n_layers = len(self.widths) - 1
+        for i, w in enumerate(self.widths):
+            p.widths[i] = int(w)
+        p.n_pts = self.n_pts
+        p.y = self.y.data_ptr() if self.n_pts else None
+        p.rho = self.rho.data_ptr() if self.rho is not None else None
+        p.n_bnd = self.n_bnd
+        p.y_bnd = self.y_bnd.data_ptr() if self.y_bnd is not None else None
+        p.c_bnd = float(c_bnd)
+        p.y_norm[0], p.y_norm[1] = float(y_norm[0]), float(y_norm[1])
+        p.c_norm = float(c_norm)
+        p.c_norm_w = float(c_norm_w)
+        p.hilbert_m = int(hilbert_m)
+        p.precision = int(precision)
+        p.n_slices = int(n_slices)
+        self._prob = p
+        self.stream = stream
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().gn_init(ctypes.byref(p), _stream_ptr(stream), ctypes.byref(h)), "gn_init")
+        self.h = h
+        P = _I64()
+        _check(lib().gn_param_count(h, ctypes.byref(P)), "gn_param_count")
+        R = _I64()
+        _check(lib().gn_row_count(h, ctypes.byref(R)), "gn_row_count")
+        self.P, self.n_rows = P.value, R.value
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        return cls(w.equation, w.widths, w.y, w.y_bnd if w.y_bnd.size else None, w.rho, y_norm=w.y_norm,
+                   c_norm=w.c_norm, hilbert_m=w.hilbert_m, **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- calls with the C names ------------------------------------------------
+    def gn_set_precision(self, precision, n_slices=0):
+        _check(lib().gn_set_precision(self.h, int(precision), int(n_slices)), "gn_set_precision")
+
+    def gn_residual(self, theta, lam, r_out=None, want_loss=True):
+        loss = _D()
+        rc = lib().gn_residual(self.h, _ptr(theta), float(lam), _ptr(r_out),
+                               ctypes.byref(loss) if want_loss else None)
+        if rc == GN_ERR_NONFINITE:
+            return rc, loss.value
+        _check(rc, "gn_residual")
+        return rc, loss.value
+
+    def gn_jacobian(self, theta, lam, J_out, row0=0, nrows=None):
+        nrows = self.n_rows - row0 if nrows is None else nrows
+        _check(lib().gn_jacobian(self.h, _ptr(theta), float(lam), _ptr(J_out), J_out.stride(0), row0, nrows),
+               "gn_jacobian")
+
+    def gn_gradient(self, theta, lam, seed, grad_out):
+        _check(lib().gn_gradient(self.h, _ptr(theta), float(lam), _ptr(seed), _ptr(grad_out)), "gn_gradient")
+
+    def gn_gram(self, J, nrows, r, G_out, g_out, precision=GN_PREC_FP64, accumulate=False):
+        _check(lib().gn_gram(self.h, _ptr(J), J.stride(0), int(nrows), _ptr(r), _ptr(G_out), _ptr(g_out),
+                             int(precision), int(bool(accumulate))), "gn_gram")
+
+    def gn_damped_solve(self, G, g, gamma, delta_out):
+        gam = _D(gamma)
+        ret = ctypes.c_int(0)
+        rc = lib().gn_damped_solve(self.h, _ptr(G), _ptr(g), ctypes.byref(gam), _ptr(delta_out), ctypes.byref(ret))
+        return rc, gam.value, ret.value
+
+    def gn_step(self, theta, lam, gamma):
+        lam_ = _D(lam)
+        gam_ = _D(gamma)
+        info = gn_step_info()
+        rc = lib().gn_step(self.h, _ptr(theta), ctypes.byref(lam_), ctypes.byref(gam_), ctypes.byref(info))
+        if rc < 0 and rc not in (GN_ERR_NOT_SPD, GN_ERR_NONFINITE):
+            _check(rc, "gn_step")
+        return rc, lam_.value, gam_.value, info.as_dict()
+
+    def gn_max_residual(self, theta, lam):
+        out = _D()
+        _check(lib().gn_max_residual(self.h, _ptr(theta), float(lam), ctypes.byref(out)), "gn_max_residual")
+        return out.value
+
+    # -- conveniences --------------------------------------------------------------
+    def new_vec(self, n):
+        return torch.zeros(n, dtype=torch.float64, device=self.device)
+
+    def residual(self, theta, lam):
+        r = self.new_vec(self.n_rows)
+        rc, loss = self.gn_residual(theta, lam, r)
+        return r, loss
+
+    def jacobian(self, theta, lam, row0=0, nrows=None, ld=None):
+        nrows = self.n_rows - row0 if nrows is None else nrows
+        ld = self.P + 1 if ld is None else ld
+        J = torch.zeros((nrows, ld), dtype=torch.float64, device=self.device)
+        self.gn_jacobian(theta, lam, J, row0, nrows)
+        return J[:, : self.P + 1]
+
+    def gradient(self, theta, lam, seed=None):
+        g = self.new_vec(self.P + 1)
+        self.gn_gradient(theta, lam, seed, g)
+        return g
+
+
+class ResidualFn(torch.autograd.Function):
+    """r~(theta, lambda) as a differentiable torch op: forward calls gn_residual, backward
+    calls the adjoint kernel gn_gradient seeded by the incoming gradient (the same
+    reverse pass that produces the Gauss-Newton Jacobian rows)."""
+
+    @staticmethod
+    def forward(ctx, theta, lam, prob: GNProblem):
+        r = prob.new_vec(prob.n_rows)
+        prob.gn_residual(theta.detach().contiguous(), float(lam), r, want_loss=False)
+        ctx.prob = prob
+        ctx.save_for_backward(theta.detach(), lam.detach())
+        return r
+
+    @staticmethod
+    def backward(ctx, grad_r):
+        theta, lam = ctx.saved_tensors
+        prob = ctx.prob
+        g = prob.gradient(theta.contiguous(), float(lam), grad_r.contiguous())
+        return g[: prob.P], g[prob.P].reshape(lam.shape), None
+
+
+def residual_fn(theta, lam, prob):
+    return ResidualFn.apply(theta, lam, prob)
