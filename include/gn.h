@@ -52,6 +52,7 @@ extern "C" {
 #define GN_ERR_NOT_SPD       -5   /* G + gamma I not positive definite after 5 damping escalations */
 #define GN_ERR_TIMEOUT       -6   /* a bounded device-side wait gave up */
 #define GN_ERR_UNSUPPORTED   -7   /* requested precision/path not available on this device */
+#define GN_ERR_TOO_LARGE     -8   /* size exceeds the fixed scratch of gn_jtr_noalloc (16384 columns) */
 
 /* ---- problem description ----------------------------------------------- */
 /* Equations (Results and Methods; residual operators as derived from the
@@ -201,6 +202,24 @@ int gn_step(gn_handle* h, double* theta, double* lambda, double* damping, gn_ste
 /* Max |R_k| over the interior points (Methods, "Validation Metrics", max d0
  * residual) at (theta, lambda), unweighted.  *out: host.  Synchronises. */
 int gn_max_residual(gn_handle* h, const double* theta, double lambda, double* out);
+
+/* g_out[0..ncols) = J^T r without a handle and without allocating anything.
+ * The paper has no counterpart: this is a service for callers that cannot
+ * call cudaMalloc (a host application that owns all device memory through its
+ * own allocator, loops that must avoid the synchronisation an allocation may
+ * imply, plug-ins that only receive device pointers).  J: device, row-major
+ * [nrows x ld] with ncols <= ld used columns; r: device [nrows]; g_out:
+ * device [ncols]; all caller-owned.  Work is queued on cuda_stream (a
+ * cudaStream_t, NULL = legacy default stream); the call does not synchronise.
+ * Scratch lives in a fixed 8 MiB device array inside the library image,
+ * held by every GPU that loads the library until the process exits;
+ * ncols > 16384 returns GN_ERR_TOO_LARGE.  The first call on a device looks
+ * up the array's device address (make it before any stream capture).  All
+ * calls on a device share the array: calls that overlap on the GPU race, so
+ * serialise them.  Returns GN_OK, GN_ERR_INVALID, GN_ERR_TOO_LARGE,
+ * GN_ERR_UNSUPPORTED (device index >= 64) or GN_ERR_CUDA. */
+int gn_jtr_noalloc(const double* J, int64_t ld, int64_t nrows, int64_t ncols, const double* r, double* g_out,
+                   void* cuda_stream);
 
 /* Number of CUDA kernels this library has launched in this process so far
  * (a diagnostic counter; read it before and after a region to count its launches). */

@@ -267,6 +267,7 @@ const char* gn_error_string(int code) {
     case GN_ERR_NOT_SPD: return "damped Gauss-Newton matrix not positive definite";
     case GN_ERR_TIMEOUT: return "bounded device wait timed out";
     case GN_ERR_UNSUPPORTED: return "unsupported on this device or build";
+    case GN_ERR_TOO_LARGE: return "size exceeds the fixed scratch of the allocation-free entry point";
     default: return "unknown status";
   }
 }

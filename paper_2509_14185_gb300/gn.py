@@ -25,6 +25,7 @@ GN_ERR_NONFINITE = -4
 GN_ERR_NOT_SPD = -5
 GN_ERR_TIMEOUT = -6
 GN_ERR_UNSUPPORTED = -7
+GN_ERR_TOO_LARGE = -8
 
 GN_PREC_FP64 = 0
 GN_PREC_SPLIT_BF16 = 1
@@ -90,6 +91,7 @@ EXPORTS = {
     "gn_damped_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_D), _P, ctypes.POINTER(ctypes.c_int)]),
     "gn_step": (ctypes.c_int, [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(gn_step_info)]),
     "gn_max_residual": (ctypes.c_int, [_P, _P, _D, ctypes.POINTER(_D)]),
+    "gn_jtr_noalloc": (ctypes.c_int, [_P, _I64, _I64, _I64, _P, _P, _P]),
     "gn_kernel_launches": (ctypes.c_int64, []),
     "gn_error_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
