@@ -225,6 +225,10 @@ int gn_jtr_noalloc(const double* J, int64_t ld, int64_t nrows, int64_t ncols, co
  * (a diagnostic counter; read it before and after a region to count its launches). */
 int64_t gn_kernel_launches(void);
 
+/* Where the last GN_ERR_CUDA / GN_ERR_UNSUPPORTED of this host thread came
+ * from ("file:line: CUDA message"); empty if none.  Static storage, per thread. */
+const char* gn_last_error_detail(void);
+
 /* Static message for a status code. */
 const char* gn_error_string(int code);
 

@@ -14,12 +14,24 @@ using namespace gn;
 
 std::atomic<long long> gn::g_launches{0};
 
+namespace gn {
+static thread_local char g_detail[256] = "";
+void set_detail(const char* where, int line, const char* what) {
+  const char* base = strrchr(where, '/');
+  snprintf(g_detail, sizeof(g_detail), "%s:%d: %s", base ? base + 1 : where, line, what);
+}
+cudaError_t note_cuda(cudaError_t e, const char* where, int line) {
+  if (e != cudaSuccess) set_detail(where, line, cudaGetErrorString(e));
+  return e;
+}
+}  // namespace gn
+
 namespace {
 
-#define GN_TRY_CUDA(x)                          \
-  do {                                          \
-    cudaError_t e_ = (x);                       \
-    if (e_ != cudaSuccess) return GN_ERR_CUDA;  \
+#define GN_TRY_CUDA(x)                                      \
+  do {                                                      \
+    cudaError_t e_ = GN_NOTE(x);                            \
+    if (e_ != cudaSuccess) return GN_ERR_CUDA;              \
   } while (0)
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
@@ -253,6 +265,8 @@ struct Timer {
 }  // namespace
 
 extern "C" {
+
+const char* gn_last_error_detail(void) { return g_detail; }
 
 int64_t gn_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 

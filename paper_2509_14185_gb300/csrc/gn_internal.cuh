@@ -18,6 +18,11 @@ constexpr int kWarp = 32;
 extern std::atomic<long long> g_launches;
 inline void count_launch(int n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+// Description of the last failing CUDA call on this host thread (gn_last_error_detail).
+void set_detail(const char* where, int line, const char* what);
+cudaError_t note_cuda(cudaError_t e, const char* where, int line);
+#define GN_NOTE(x) ::gn::note_cuda((x), __FILE__, __LINE__)
+
 // Kinds of "points" whose rows the jet kernel produces.
 enum PointKind : int {
   KIND_INTERIOR = 0,  // interior collocation point: N_E residual rows

@@ -93,6 +93,7 @@ EXPORTS = {
     "gn_max_residual": (ctypes.c_int, [_P, _P, _D, ctypes.POINTER(_D)]),
     "gn_jtr_noalloc": (ctypes.c_int, [_P, _I64, _I64, _I64, _P, _P, _P]),
     "gn_kernel_launches": (ctypes.c_int64, []),
+    "gn_last_error_detail": (ctypes.c_char_p, []),
     "gn_error_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
@@ -115,7 +116,8 @@ def lib():
 class GNError(RuntimeError):
     def __init__(self, code, where):
         msg = lib().gn_error_string(code).decode()
-        super().__init__(f"{where}: {msg} ({code})")
+        detail = lib().gn_last_error_detail().decode()
+        super().__init__(f"{where}: {msg} ({code})" + (f" [{detail}]" if detail else ""))
         self.code = code
 
 

@@ -1,0 +1,90 @@
+"""Split-precision (Ozaki, BF16 slices on tcgen05) Gram product vs exact references.
+
+* Bit-exactness: when every column of J has entries that are integers of at
+  most 8 significant bits (|J_ij| <= 200 here), one slice represents J exactly
+  and every partial sum is an integer below 2^24, so G_split must equal the
+  exact Gram matrix (computed in FP64, exact for these integers) bit for bit.
+  This pins the whole path: TMA tiles and swizzle, instruction and shared
+  memory descriptors, the tensor-memory accumulators and the epilogue.
+* Accuracy: for a real Jacobian the error of each entry obeys the bound of
+  the split (scaled columns x = J 2^{-e}, |x| < 1, K rows, S slices):
+      |dG_ij| 2^{-(e_i+e_j)} <= 2^{-8S-1} (|x_:i|_1 + |x_:j|_1)        (digits)
+                               + K 2^{-16S-2} + K S(S-1)/2 2^{-8S-2}  (dropped pairs)
+                               + [S >= 4] (K_pad/16) 2^{-48} K S      (FP32 tail)
+  checked against the oracle's Jacobian and an FP64 product on the CPU.
+"""
+import numpy as np
+import pytest
+import torch
+
+from tests.gpu_cases import dev, gpu_problem, host, oracle_problem, small
+from oracle import gn as ogn
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+SPLIT = 1
+
+
+def split_bound(J, S):
+    """Entrywise bound of the split Gram error (see the module docstring)."""
+    K = J.shape[0]
+    M = np.max(np.abs(J), axis=0)
+    e = np.where(M > 0, np.frexp(M)[1], 0).astype(np.float64)
+    X = J * 2.0 ** (-e)
+    n1 = np.sum(np.abs(X), axis=0)
+    per = 2.0 ** (-8 * S - 1) * (n1[:, None] + n1[None, :]) + K * 2.0 ** (-16 * S - 2) \
+        + K * S * (S - 1) / 2 * 2.0 ** (-8 * S - 2)
+    if S >= 4:
+        kpad = -(-K // 128) * 128
+        per = per + (kpad / 16) * 2.0 ** -48 * K * S
+    return per * 2.0 ** (e[:, None] + e[None, :])
+
+
+def _split_gram(prob, J, slices, accumulate=False, G=None):
+    Pp = prob.P + 1
+    prob.gn_set_precision(SPLIT, slices)
+    if G is None:
+        G = torch.zeros((Pp, Pp), dtype=torch.float64, device="cuda")
+    prob.gn_gram(J, J.shape[0], None, G, None, precision=SPLIT, accumulate=accumulate)
+    torch.cuda.synchronize()
+    return G
+
+
+@pytest.mark.parametrize("nrows", [128, 300])
+def test_split_gram_bit_exact_on_8bit_integers(nrows):
+    w = small("ccf")                     # P' = 1762: 14 column tiles, ragged last tile
+    prob = gpu_problem(w)
+    Pp = prob.P + 1
+    rng = np.random.default_rng(7)
+    Jh = rng.integers(-200, 201, size=(nrows, Pp)).astype(np.float64)
+    Jh[:, 5] = 0.0                       # an all-zero column
+    Jh[:, 7] *= 2.0 ** -20               # a column at a different power-of-two scale
+    G = host(_split_gram(prob, dev(Jh), 1))
+    Gx = Jh.T @ Jh                       # exact: integers below 2^53
+    assert np.array_equal(np.tril(G), np.tril(Gx))
+
+
+@pytest.mark.parametrize("slices", [1, 2, 3, 4, 5, 6])
+def test_split_gram_error_bound(slices):
+    w = small("ccf")
+    p = oracle_problem(w)
+    J = ogn.jacobian(p, w.theta, w.lam)
+    prob = gpu_problem(w)
+    G = np.tril(host(_split_gram(prob, dev(J), slices)))
+    Gx = np.tril(J.T @ J)
+    bound = np.tril(split_bound(J, slices))
+    err = np.abs(G - Gx)
+    assert np.all(err <= 2.0 * bound + 1e-300), float(np.max(err / (bound + 1e-300)))
+
+
+def test_split_gram_accumulate_two_row_blocks():
+    w = small("boussinesq")
+    p = oracle_problem(w)
+    J = ogn.jacobian(p, w.theta, w.lam)
+    prob = gpu_problem(w)
+    h = J.shape[0] // 2
+    G = _split_gram(prob, dev(J[:h]), 4)
+    G = _split_gram(prob, dev(J[h:]), 4, accumulate=True, G=G)
+    Gx = J.T @ J
+    bound = split_bound(J[:h], 4) + split_bound(J[h:], 4)
+    assert np.all(np.tril(np.abs(host(G) - Gx)) <= 2.0 * np.tril(bound) + 1e-300)
