@@ -41,11 +41,63 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="split", choices=["fp64", "split"])
+    ap.add_argument("--precision", default="split_all", choices=["fp64", "split", "split_all"])
     ap.add_argument("--slices", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--micro", default=None, choices=[None, "gram"],
+                    help="time one kernel family alone instead of the GN step (not the bench contract line)")
+    ap.add_argument("--width", type=int, default=44, help="--micro gram: hidden width w of a 1-w-w-1 CCF net")
     return ap.parse_args()
+
+
+def micro_gram(args):
+    """Split (or FP64) Gram product alone on a real CCF Jacobian: 16385 rows x P' columns,
+    P' = w^2 + 4w + 2 (w = 44: 2114 columns, J = 277 MB, larger than L2).  Prints one
+    JSON line with per-launch times from CUDA events (this is the small case used for
+    detailed ncu captures of the Gram kernels)."""
+    import numpy as np
+    import torch
+    from paper_2509_14185_gb300 import build as B
+    B.build()
+    from paper_2509_14185_gb300 import gn, inputs
+    w = inputs.ccf_unstable_1d()
+    w.widths = [1, args.width, args.width, 1]
+    w.theta = inputs.xavier_init(w.widths, 17)
+    prec = {"fp64": gn.GN_PREC_FP64, "split": gn.GN_PREC_SPLIT_BF16, "split_all": gn.GN_PREC_SPLIT_BF16}[args.precision]
+    prob = gn.GNProblem.from_workload(w, precision=prec, n_slices=args.slices)
+    Pp = prob.P + 1
+    theta = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
+    J = torch.zeros((prob.n_rows, Pp), dtype=torch.float64, device="cuda")
+    prob.gn_jacobian(theta, w.lam, J)
+    G = torch.zeros((Pp, Pp), dtype=torch.float64, device="cuda")
+    g = prob.new_vec(Pp)
+    r = prob.new_vec(prob.n_rows)
+    for _ in range(args.warmup):
+        prob.gn_gram(J, prob.n_rows, r, G, g, precision=prec)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        prob.gn_gram(J, prob.n_rows, r, G, g, precision=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    rows = prob.n_rows
+    alg = rows * Pp * (Pp + 1.0)
+    out = {"micro": "gram", "precision": args.precision, "slices": args.slices, "rows": rows, "cols": Pp,
+           "ms_median": ms, "fp64_equivalent_tflops": alg / (ms * 1e-3) / 1e12}
+    if prec != gn.GN_PREC_FP64:
+        S = args.slices
+        nt = -(-Pp // 128)
+        kpad = -(-rows // 32) * 32
+        executed = S * (S + 1) / 2 * (nt * (nt + 1) / 2) * 128 * 128 * kpad * 2.0
+        out["tensor_tflops_incl_prepass"] = executed / (ms * 1e-3) / 1e12
+    print(json.dumps(out))
+    prob.close()
+    return 0
 
 
 def dist_env():
@@ -264,6 +316,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.micro == "gram":
+        return micro_gram(args)
     import numpy as np
     import torch
 
@@ -278,7 +332,7 @@ def main():
 
     # replicas: every rank fits its own seeded profile (no data-path collective)
     w = inputs.ccf_unstable_1d(seed=2 + rank)
-    prec = gn.GN_PREC_FP64 if args.precision == "fp64" else gn.GN_PREC_SPLIT_BF16
+    prec = {"fp64": gn.GN_PREC_FP64, "split": gn.GN_PREC_SPLIT_BF16, "split_all": gn.GN_PREC_SPLIT_ALL}[args.precision]
     prob = gn.GNProblem.from_workload(w, precision=prec, n_slices=args.slices)
     stream = torch.cuda.current_stream()
     theta = torch.tensor(w.theta, dtype=torch.float64, device="cuda")

@@ -74,10 +74,18 @@ enum gn_equation {
  * everything else is always FP64). */
 enum gn_precision {
   GN_PREC_FP64 = 0,        /* native FP64 (DFMA) Gram */
-  GN_PREC_SPLIT_BF16 = 1   /* Ozaki split: each FP64 column of J~ scaled by a power of two and
+  GN_PREC_SPLIT_BF16 = 1,  /* Ozaki split: each FP64 column of J~ scaled by a power of two and
                               split into n_slices BF16 slices; slice products on the tcgen05
                               tensor cores with exactly representable FP32 partial sums,
                               combined in double-FP32 and returned as FP64 */
+  GN_PREC_SPLIT_ALL = 2    /* as GN_PREC_SPLIT_BF16, and the other two dense contractions too:
+                              the CCF Hilbert contraction J_U = K J_g and the trailing updates
+                              of the blocked Cholesky factorisation (diagonal blocks, panel
+                              solves and the triangular solves stay FP64).  Entrywise error of
+                              each split product, in units of 2^(e_i+e_j) with |x| < 1 the
+                              power-of-two scaled operands and K the contraction length:
+                              2^(-8S-1)(|x_i|_1+|x_j|_1) + K 2^(-16S-2) + K S(S-1) 2^(-8S-3)
+                              + [S>=4] K_pad K S 2^(-52)                                    */
 };
 
 #define GN_MAX_LAYERS 8
@@ -99,7 +107,7 @@ typedef struct gn_problem {
   double c_norm_w;           /* weight c_norm of the normalisation row */
   int hilbert_m;             /* CCF only: nodes M of the discrete Hilbert operator (even, 8..16384) */
   int precision;             /* enum gn_precision used by gn_step for the Gram */
-  int n_slices;              /* split precision only: BF16 slices per FP64 value (1..8) */
+  int n_slices;              /* split precision only: BF16 slices per FP64 value (1..6) */
 } gn_problem;
 
 /* Normalisation row (data loss) per equation, fixed by the library:

@@ -143,6 +143,43 @@ cudaError_t cholesky_factor(double* A, int64_t n, int64_t lda, double* Linv, int
   return cudaSuccess;
 }
 
+// Same blocked factorisation with the trailing update A22 -= L21 L21^T on the
+// tensor cores (split GEMM, S slices): the diagonal blocks and the panel solve
+// stay FP64; the bulk (P'^3/3 of the work) becomes BF16 slice products with
+// exact level accumulation.  *rc_out receives a GN_ERR_* code on failure.
+cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t lda, double* Linv, int* flag, int S,
+                                  int* rc_out) {
+  cudaStream_t st = h->st;
+  *rc_out = GN_OK;
+  const size_t opb = oz_operand_bytes(S, n, NB);
+  int rc = ensure_split_ws(h, opb + 256);
+  if (rc) {
+    *rc_out = rc;
+    return cudaErrorMemoryAllocation;
+  }
+  cudaError_t err = cudaSuccess;
+  for (int64_t k0 = 0; k0 < n; k0 += NB) {
+    const int kb = (int)((n - k0) < NB ? (n - k0) : NB);
+    potrf_diag_kernel<<<1, 256, 0, st>>>(A, lda, k0, kb, Linv, flag);
+    count_launch();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    const int64_t k1 = k0 + kb;
+    if (k1 >= n) break;
+    const double* Lk = Linv + (k0 / NB) * NB * NB;
+    err = dgemm(n - k1, kb, kb, 1.0, A + k1 * lda + k0, lda, true, Lk, NB, true, 0.0, A + k1 * lda + k0, lda,
+                false, nullptr, st);
+    if (err != cudaSuccess) return err;
+    OzOperand L = oz_operand_at(h->split_ws, S, n - k1, kb);
+    rc = oz_prepare_rows(S, A + k1 * lda + k0, lda, n - k1, kb, L, st);
+    if (!rc) rc = oz_gemm(S, true, L, L, n - k1, n - k1, A + k1 * lda + k1, lda, 2, nullptr, h->flag + 2, st);
+    if (rc) {
+      *rc_out = rc;
+      return cudaErrorUnknown;
+    }
+  }
+  return cudaSuccess;
+}
+
 cudaError_t cholesky_solve(const double* A, int64_t n, int64_t lda, const double* Linv, const double* b, double* x,
                            double* tmp, cudaStream_t st) {
   (void)tmp;

@@ -54,8 +54,8 @@ int validate(const gn_problem* p) {
   if (p->equation == GN_CCF) {
     if (p->hilbert_m < 8 || p->hilbert_m > 16384 || (p->hilbert_m & 1)) return GN_ERR_INVALID;
   }
-  if (p->precision != GN_PREC_FP64 && p->precision != GN_PREC_SPLIT_BF16) return GN_ERR_INVALID;
-  if (p->precision == GN_PREC_SPLIT_BF16 && (p->n_slices < 1 || p->n_slices > 8)) return GN_ERR_INVALID;
+  if (p->precision < GN_PREC_FP64 || p->precision > GN_PREC_SPLIT_ALL) return GN_ERR_INVALID;
+  if (p->precision != GN_PREC_FP64 && (p->n_slices < 1 || p->n_slices > 6)) return GN_ERR_INVALID;
   return GN_OK;
 }
 
@@ -185,9 +185,28 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
     // J[i, :] += sU_i * sum_j' Kf[i][j'] Jg[j', :] for interior rows inside the block
     const int64_t lo = ps.jlo > 0 ? ps.jlo : 0;
     const int64_t hi = ps.jhi < n ? ps.jhi : n;
-    if (hi > lo)
+    if (hi > lo && h->precision == GN_PREC_SPLIT_ALL) {
+      // the same contraction as a split GEMM on the tensor cores: A = Kf rows
+      // (row-scaled), B = J_g columns (column-scaled), C += sU_i * value
+      const int S = h->n_slices;
+      const size_t ba = oz_operand_bytes(S, hi - lo, h->Mh), bb = oz_operand_bytes(S, h->Pp, h->Mh);
+      const size_t bp = (size_t)64 * ((h->Pp + 127) / 128 * 128) * 8;
+      int rc = ensure_split_ws(h, ba + bb + bp + 512);
+      if (rc) return rc;
+      unsigned char* base = static_cast<unsigned char*>(h->split_ws);
+      OzOperand A = oz_operand_at(base, S, hi - lo, h->Mh);
+      OzOperand B = oz_operand_at(base + ba, S, h->Pp, h->Mh);
+      double* part = reinterpret_cast<double*>(base + ba + bb);
+      rc = oz_prepare_rows(S, h->kf + lo * h->Mh, h->Mh, hi - lo, h->Mh, A, st);
+      if (!rc) rc = oz_prepare_cols(S, h->Jg, h->ldJ, h->Mh, h->Pp, B, part, st);
+      if (!rc)
+        rc = oz_gemm(S, false, A, B, hi - lo, h->Pp, ps.J + (lo - ps.jlo) * ps.ldJ, ps.ldJ, 1, h->sU + lo,
+                     h->flag + 2, st);
+      if (rc) return rc;
+    } else if (hi > lo) {
       GN_TRY_CUDA(dgemm(hi - lo, h->Pp, h->Mh, 1.0, h->kf + lo * h->Mh, h->Mh, true, h->Jg, h->ldJ, false, 1.0,
                         ps.J + (lo - ps.jlo) * ps.ldJ, ps.ldJ, false, h->sU + lo, st));
+    }
   }
   if (ps.mode == MODE_GRADIENT) {
     if (h->eq == GN_CCF && n > 0) {
@@ -234,7 +253,7 @@ int residual_loss(gn_handle* h, const double* theta, double lam, double* r, doub
 int gram_into(gn_handle* h, const double* J, int64_t ld, int64_t nrows, const double* r, double* G, double* g,
               int precision, int accumulate) {
   const double beta = accumulate ? 1.0 : 0.0;
-  if (precision == GN_PREC_SPLIT_BF16) {
+  if (precision != GN_PREC_FP64) {
     int rc = split_gram(h, J, ld, nrows, G, accumulate);
     if (rc) return rc;
   } else {
@@ -405,8 +424,8 @@ int gn_row_count(const gn_handle* h, int64_t* n_rows) {
 
 int gn_set_precision(gn_handle* h, int precision, int n_slices) {
   if (!h) return GN_ERR_INVALID;
-  if (precision != GN_PREC_FP64 && precision != GN_PREC_SPLIT_BF16) return GN_ERR_INVALID;
-  if (precision == GN_PREC_SPLIT_BF16 && (n_slices < 1 || n_slices > 8)) return GN_ERR_INVALID;
+  if (precision < GN_PREC_FP64 || precision > GN_PREC_SPLIT_ALL) return GN_ERR_INVALID;
+  if (precision != GN_PREC_FP64 && (n_slices < 1 || n_slices > 6)) return GN_ERR_INVALID;
   h->precision = precision;
   if (n_slices > 0) h->n_slices = n_slices;
   return GN_OK;
@@ -443,8 +462,17 @@ int gn_gradient(gn_handle* h, const double* theta, double lambda, const double* 
 int gn_gram(gn_handle* h, const double* J, int64_t ld, int64_t nrows, const double* r, double* G_out, double* g_out,
             int precision, int accumulate) {
   if (!h || !J || !G_out || ld < h->Pp || nrows < 0) return GN_ERR_INVALID;
-  if (precision != GN_PREC_FP64 && precision != GN_PREC_SPLIT_BF16) return GN_ERR_INVALID;
-  return gram_into(h, J, ld, nrows, r, G_out, g_out, precision, accumulate);
+  if (precision < GN_PREC_FP64 || precision > GN_PREC_SPLIT_ALL) return GN_ERR_INVALID;
+  if (precision == GN_PREC_FP64) return gram_into(h, J, ld, nrows, r, G_out, g_out, precision, accumulate);
+  // split precision: report a timed-out tensor-core wait before returning
+  GN_TRY_CUDA(cudaMemsetAsync(h->flag + 2, 0, sizeof(int), h->st));
+  int rc = gram_into(h, J, ld, nrows, r, G_out, g_out, precision, accumulate);
+  if (rc) return rc;
+  GN_TRY_CUDA(cudaMemcpyAsync(&h->hpin[9], h->flag + 2, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  GN_TRY_CUDA(cudaStreamSynchronize(h->st));
+  int f = 0;
+  memcpy(&f, &h->hpin[9], sizeof(int));
+  return (f & 2) ? GN_ERR_TIMEOUT : GN_OK;
 }
 
 int gn_damped_solve(gn_handle* h, const double* G, const double* g, double* gamma, double* delta_out,
@@ -455,12 +483,23 @@ int gn_damped_solve(gn_handle* h, const double* G, const double* g, double* gamm
   for (;;) {
     GN_TRY_CUDA(copy_add_diag(G, h->A, Pp, Pp, *gamma, h->st));
     GN_TRY_CUDA(cudaMemsetAsync(h->flag + 1, 0, sizeof(int), h->st));
-    GN_TRY_CUDA(cholesky_factor(h->A, Pp, Pp, h->Linv, h->flag + 1, h->st));
-    int hflag = 0;
-    GN_TRY_CUDA(cudaMemcpyAsync(&h->hpin[8], h->flag + 1, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    if (h->precision == GN_PREC_SPLIT_ALL) {
+      int rc = GN_OK;
+      cudaError_t e = cholesky_factor_split(h, h->A, Pp, Pp, h->Linv, h->flag + 1, h->n_slices, &rc);
+      if (rc) return rc;
+      GN_TRY_CUDA(e);
+    } else {
+      GN_TRY_CUDA(cholesky_factor(h->A, Pp, Pp, h->Linv, h->flag + 1, h->st));
+    }
+    int hflag[2] = {0, 0};
+    GN_TRY_CUDA(cudaMemcpyAsync(&h->hpin[8], h->flag + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->st));
     GN_TRY_CUDA(cudaStreamSynchronize(h->st));
-    memcpy(&hflag, &h->hpin[8], sizeof(int));
-    if (!hflag) break;
+    memcpy(hflag, &h->hpin[8], 2 * sizeof(int));
+    if (hflag[1] & 2) {
+      set_detail(__FILE__, __LINE__, "a bounded wait in a tensor-core kernel timed out");
+      return GN_ERR_TIMEOUT;
+    }
+    if (!hflag[0]) break;
     if (retries == 5) {
       if (retries_out) *retries_out = retries;
       return GN_ERR_NOT_SPD;
@@ -499,6 +538,7 @@ int gn_step(gn_handle* h, double* theta, double* lambda, double* damping, gn_ste
   const double lam = *lambda;
   double gamma = *damping;
   Timer tm(st);
+  GN_TRY_CUDA(cudaMemsetAsync(h->flag + 2, 0, sizeof(int), st));
   tm.mark(0);
   // 1. rows and Jacobian, Gram and gradient, streamed in row blocks
   int rc = GN_OK;

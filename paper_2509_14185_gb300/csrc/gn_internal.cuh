@@ -163,7 +163,33 @@ cudaError_t cholesky_factor(double* A, int64_t n, int64_t lda, double* Linv, int
 cudaError_t cholesky_solve(const double* A, int64_t n, int64_t lda, const double* Linv, const double* b,
                            double* x, double* tmp, cudaStream_t st);
 
-// Split-precision (Ozaki, BF16 slices on tcgen05) Gram; returns GN_ERR_* codes.
+// Split-precision (Ozaki, BF16 slices on tcgen05) GEMM C op= A B^T (ozaki.cu).
+// An operand holds S BF16 slices [S][npad][kpad] (K-major) and one power-of-two
+// exponent per row (npad rows, padded with zeros).
+constexpr int kOzMaxSlices = 6;
+struct OzOperand {
+  void* slices;   // __nv_bfloat16 [S][npad][kpad]
+  int* e;         // [npad]
+  int64_t npad, kpad;
+};
+size_t oz_operand_bytes(int S, int64_t n, int64_t k);
+OzOperand oz_operand_at(void* base, int S, int64_t n, int64_t k);
+// X is K x n row-major (operand row j = column j of X); part: 64 * npad doubles of scratch
+int oz_prepare_cols(int S, const double* X, int64_t ld, int64_t k, int64_t n, const OzOperand& op, double* part,
+                    cudaStream_t st);
+// X is n x K row-major (operand row j = row j of X)
+int oz_prepare_rows(int S, const double* X, int64_t ld, int64_t n, int64_t k, const OzOperand& op,
+                    cudaStream_t st);
+// C (M x N, ldc) op= A B^T; sym: only tiles with row tile >= column tile (A must equal B);
+// mode 0: C = v, 1: C += rowscale[i] v (rowscale may be null), 2: C -= v.  flag: bit 1 on timeout.
+int oz_gemm(int S, bool sym, const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, double* C, int64_t ldc,
+            int mode, const double* rowscale, int* flag, cudaStream_t st);
+// Gram through oz_gemm (lower tiles); returns GN_ERR_* codes.
 int split_gram(gn_handle* h, const double* J, int64_t ld, int64_t nrows, double* G, int accumulate);
+// grow the handle's split workspace to at least `need` bytes
+int ensure_split_ws(gn_handle* h, size_t need);
+// blocked Cholesky whose trailing updates run through oz_gemm
+cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t lda, double* Linv, int* flag, int S,
+                                  int* rc_out);
 
 }  // namespace gn

@@ -1,35 +1,40 @@
-// Split-precision (Ozaki) Gram product G = J~^T J~ on the tcgen05 tensor cores.
+// Split-precision (Ozaki) GEMM on the tcgen05 tensor cores: C op= A B^T with
+// FP64 operands split into BF16 slices.  Used for the three dense
+// contractions of the Gauss-Newton step (Methods, "Second-order Optimizer"):
+// the Gram product G = J~^T J~, the CCF Hilbert contraction J_U = K J_g, and
+// the trailing updates of the blocked Cholesky factorisation.  GB300 runs
+// BF16 on its tensor cores ~1600x faster than FP64, so the FP64 values are
+// split and the slice products accumulated exactly (Ozaki, Ogita, Oishi &
+// Rump, "Error-free transformations of matrix multiplication by using fast
+// routines of matrix multiplication and its applications", Numer. Algorithms
+// 2012):
 //
-// The Gauss-Newton matrix (Methods, "Second-order Optimizer") is the one truly
-// dense contraction of the step.  GB300 runs BF16 on its tensor cores ~1600x
-// faster than FP64, so the FP64 columns of J~ are split into BF16 slices and
-// the slice products are accumulated exactly (Ozaki, Ogita, Oishi & Rump,
-// "Error-free transformations of matrix multiplication by using fast routines
-// of matrix multiplication and its applications", Numer. Algorithms 2012):
-//
-//  1. column scale: e_j with max_i |J_ij| < 2^{e_j} (a power of two, exact);
-//  2. digits: v = round(J_ij 2^{8S - e_j}) as a 64-bit integer, written as S
+//  1. scale: each output index j (a column of a K x n operand, or a row of an
+//     n x K operand) gets e_j with max_k |X_kj| < 2^{e_j}; scaling is exact;
+//  2. digits: v = round(X_kj 2^{8S - e_j}) as a 64-bit integer, written as S
 //     balanced base-256 digits a_1..a_S (|a_1| <= 256, |a_t| <= 128); slice t
 //     holds a_t 2^{-8t}, exactly representable in BF16 (8-bit significand);
 //  3. products: slice pairs (s, t) with s + t <= S + 1, grouped by level
 //     l = s + t.  Within a level every product is an integer times 2^{-8l};
-//     over a 128-row chunk the integer partial sums stay below 2^24, so the
-//     FP32 accumulation in tensor memory is exact for levels 2, 3, 4.  Those
+//     over a 128-long K chunk the integer partial sums stay below 2^24, so the
+//     FP32 accumulation in tensor memory is exact for levels 2, 3, 4; those
 //     are flushed after each chunk into double-FP32 (hi, lo) registers.
-//     Levels >= 5 share one accumulator over the whole K range: its FP32
-//     rounding is ~2^-24 of a term that is itself <= 2^-24 of G.
-//  4. G_ij = 2^{e_i + e_j} (hi + lo), written in FP64.
-// Truncation error: |G_split - G|_ij <~ (S + 1) 2^{-8S} |J_:i|_2 |J_:j|_2.
+//     Levels >= 5 share one accumulator over the whole K range.
+//  4. C_ij op= 2^{e_i + e_j} (hi + lo), in FP64.
+// Entrywise error, scaled units x = X 2^{-e} (|x| < 1), K the contraction length:
+//   2^{-8S-1} (|x_i|_1 + |x_j|_1) + K 2^{-16S-2} + K S(S-1)/2 2^{-8S-2}
+//   + [S >= 4] (K_pad/16) 2^{-48} K S       (the last term: FP32 tail accumulator).
 //
-// Kernel structure (one 128 x 128 lower-triangular output tile per CTA,
-// 320 threads): warp 0 issues TMA loads of the 2 S slice tiles of each
-// 32-wide K stage into a multi-stage shared-memory ring (64-byte swizzle);
-// warp 1 allocates the 512 tensor-memory columns and one lane issues the
-// tcgen05.mma instructions (M = N = 128, K = 16, BF16 in, FP32 accumulate);
-// warps 2..9 read the accumulators with tcgen05.ld and own the double-FP32
-// sums (warp w reads tensor-memory lanes 32 (w % 4) .. + 31, columns
-// 64 ((w - 2) / 4) .. + 63).  Every mbarrier wait is bounded in time; a timeout
-// sets bit 1 of the device status word and the CTA drains and exits.
+// Kernel (one 128 x 128 output tile per CTA, 320 threads): warp 0 issues TMA
+// loads of the 2 S slice tiles of each 32-wide K stage into a shared-memory
+// ring (64-byte swizzle); warp 1 allocates the 512 tensor-memory columns and
+// one lane issues tcgen05.mma (M = N = 128, K = 16, BF16 in, FP32 accumulate)
+// into four 128-column accumulators (levels 2, 3, 4, tail); warps 2..9 read
+// them with tcgen05.ld (warp w: lanes 32 (w % 4) .. + 31, columns
+// 64 ((w - 2) / 4) .. + 63) and own the double-FP32 sums; at the end the
+// operand ring is reused to park the tile for coalesced FP64 stores.  Every
+// mbarrier wait is bounded in time; a timeout sets bit 1 of the status word
+// and the CTA drains its copies and MMAs and exits.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -43,14 +48,13 @@
 namespace gn {
 namespace {
 
-constexpr int TM = 128;            // output tile (rows of G)
-constexpr int TN = 128;            // output tile (cols of G)
+constexpr int TM = 128;            // output tile rows
+constexpr int TN = 128;            // output tile cols
 constexpr int BKS = 32;            // K per stage (64-byte rows, SWIZZLE_64B)
-constexpr int KC = 128;            // exact-accumulation chunk (rows of J)
+constexpr int SPC = 4;             // stages per exact-accumulation chunk (K = 128)
 constexpr int SLICE_BYTES = TM * BKS * 2;   // one slice tile: 8 KB
-constexpr int NTHREADS = 320;   // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
+constexpr int NTHREADS = 320;      // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
 constexpr unsigned long long kWaitNs = 4000000000ull;   // 4 s bound on any wait
-constexpr int kMaxSlices = 6;
 
 __host__ __device__ constexpr int n_stages(int S) {
   return (2 * S * SLICE_BYTES * 4 <= 200 * 1024) ? 4 : (2 * S * SLICE_BYTES * 3 <= 200 * 1024) ? 3 : 2;
@@ -130,20 +134,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
-}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
   asm volatile(
@@ -165,25 +155,36 @@ __device__ __forceinline__ void dd_add(float& hi, float& lo, float v) {
   lo = __fadd_rn(lo, err);
   hi = s;
 }
-
 // 2^e as a double (exact); the bit construction covers the normal range.
 __device__ __forceinline__ double pow2(int e) {
   return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
 }
-
 // Level of a slice pair and its tensor-memory slot: levels 2, 3, 4 -> slots 0, 1, 2; >= 5 -> 3.
 __device__ __forceinline__ int slot_of(int s, int t) {
   const int l = s + t + 2;  // s, t are 0-based
   return l <= 4 ? l - 2 : 3;
 }
 
+struct OzArgs {
+  int64_t rowsA, rowsB;   // rows per slice of A and B in their 2D slice views (padded)
+  int64_t Kpad;           // padded contraction length (multiple of 32)
+  int64_t M, N;           // valid output rows / cols
+  int nt;                 // column tiles (rectangular decode)
+  const int* eA;          // exponents of A rows (padded)
+  const int* eB;          // exponents of B rows (padded)
+  double* C;
+  int64_t ldc;
+  int mode;               // 0: C = v, 1: C += rs_i v, 2: C -= v
+  const double* rowscale; // mode 1 (may be null: 1)
+  int* flag;
+};
+
 // ---------------------------------------------------------------------------
 // main kernel
 // ---------------------------------------------------------------------------
-template <int S>
+template <int S, bool SYM>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    gram_split_kernel(const __grid_constant__ CUtensorMap tmap, int64_t Ppad, int64_t Kpad, int64_t Pp,
-                      const int* __restrict__ ecol, double* G, int64_t ldg, int accumulate, int* flag) {
+    ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const OzArgs p) {
   constexpr int NST = n_stages(S);
   constexpr int STAGE_BYTES = 2 * S * SLICE_BYTES;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -195,18 +196,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* done = acc_empty + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   __shared__ int abort_cta;
-  __shared__ int ecs[2][TM];   // column exponents of this tile's rows (0) and columns (1)
+  __shared__ int ecs[2][TM];   // exponents of this tile's rows (0) and columns (1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // lower-triangular tile (ti >= tj) of this CTA
-  const int64_t t = blockIdx.x;
-  int64_t ti = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-  while ((ti + 1) * (ti + 2) / 2 <= t) ti++;
-  while (ti * (ti + 1) / 2 > t) ti--;
-  const int64_t tj = t - ti * (ti + 1) / 2;
-  const int nk = (int)(Kpad / BKS);
-  const int nchunk = (int)(Kpad / KC);
-  constexpr int SPC = KC / BKS;  // stages per chunk
+  int64_t ti, tj;
+  if (SYM) {  // lower-triangular tile ti >= tj
+    const int64_t t = blockIdx.x;
+    ti = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((ti + 1) * (ti + 2) / 2 <= t) ti++;
+    while (ti * (ti + 1) / 2 > t) ti--;
+    tj = t - ti * (ti + 1) / 2;
+  } else {
+    ti = blockIdx.x / p.nt;
+    tj = blockIdx.x % p.nt;
+  }
+  const int nk = (int)(p.Kpad / BKS);
+  const int nchunk = (nk + SPC - 1) / SPC;
+  int* flag = p.flag;
 
   if (threadIdx.x == 0) {
     abort_cta = 0;
@@ -247,20 +253,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_expect_tx(&full[st], STAGE_BYTES);
 #pragma unroll
         for (int s = 0; s < S; s++) {
-          tma_load_2d(base + s * SLICE_BYTES, &tmap, kt * BKS, (int)(s * Ppad) + rowA, &full[st]);
-          tma_load_2d(base + (S + s) * SLICE_BYTES, &tmap, kt * BKS, (int)(s * Ppad) + rowB, &full[st]);
+          tma_load_2d(base + s * SLICE_BYTES, &tmA, kt * BKS, (int)(s * p.rowsA) + rowA, &full[st]);
+          tma_load_2d(base + (S + s) * SLICE_BYTES, &tmB, kt * BKS, (int)(s * p.rowsB) + rowB, &full[st]);
         }
         issued = kt + 1;
       }
       // drain: every issued stage must land before the CTA may exit
-      for (int kt = (issued > NST ? issued - NST : 0); kt < issued; kt++) mbar_wait(&full[kt % NST], (kt / NST) & 1, flag);
+      for (int kt = (issued > NST ? issued - NST : 0); kt < issued; kt++)
+        mbar_wait(&full[kt % NST], (kt / NST) & 1, flag);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       bool ok = true;
       for (int c = 0; c < nchunk && ok; c++) {
-        for (int q = 0; q < SPC && ok; q++) {
+        const int q_end = (nk - c * SPC) < SPC ? (nk - c * SPC) : SPC;
+        for (int q = 0; q < q_end && ok; q++) {
           const int kt = c * SPC + q;
           const int st = kt % NST;
           if (!mbar_wait(&full[st], (kt / NST) & 1, flag)) { ok = false; break; }
@@ -280,16 +288,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               for (int kk = 0; kk < BKS / 16; kk++) {
                 const uint64_t da = smem_desc(base + s * SLICE_BYTES + kk * 32);
                 const uint64_t db = smem_desc(base + (S + u) * SLICE_BYTES + kk * 32);
-                // first contribution of this slot in the chunk (head) or in the whole run (tail) resets it
-                bool first;
-                if (slot < 3) {
-                  // first pair of this level within the chunk: smallest s with s + u fixed
-                  const int lvl = s + u;
-                  const int s_first = 0;
-                  first = (q == 0 && kk == 0 && s == s_first && u == lvl - s_first);
-                } else {
-                  first = (kt == 0 && kk == 0 && s == 0 && u == 3);
-                }
+                // the first pair of a level (s = 0) resets the slot: per chunk for the
+                // exact head levels, once for the tail
+                const bool first = (slot < 3) ? (q == 0 && kk == 0 && s == 0) : (kt == 0 && kk == 0 && s == 0 && u == 3);
                 mma_bf16(tmem + slot * TN, da, db, first ? 0u : 1u);
               }
             }
@@ -309,11 +310,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int qcol = (warp - 2) >> 2;          // column half 0..1
     const int row = quad * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(qcol * EC);
-    {
-      // stage the tile's column exponents (Ppad-padded, so always in range)
-      ecs[qcol][row] = ecol[(qcol == 0 ? ti * TM : tj * TN) + row];
-      asm volatile("bar.sync 1, 256;" ::: "memory");   // the 8 epilogue warps only
-    }
+    ecs[qcol][row] = (qcol == 0) ? p.eA[ti * TM + row] : p.eB[tj * TN + row];
+    asm volatile("bar.sync 1, 256;" ::: "memory");   // the 8 epilogue warps only
     float hi[EC], lo[EC];
 #pragma unroll
     for (int i = 0; i < EC; i++) { hi[i] = 0.f; lo[i] = 0.f; }
@@ -359,11 +357,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int idx = et; idx < TM * TN; idx += 256) {
         const int r = idx / TN, cc = idx % TN;
         const int64_t gi = ti * TM + r, gj = tj * TN + cc;
-        if (gi < Pp && gj < Pp) {
+        if (gi < p.M && gj < p.N) {
           const float2 hl = park[r * (TN + 1) + cc];
-          double v = ((double)hl.x + (double)hl.y) * pow2(ecs[0][r]) * pow2(ecs[1][cc]);
-          if (accumulate) v += G[gi * ldg + gj];
-          G[gi * ldg + gj] = v;
+          const double v = ((double)hl.x + (double)hl.y) * pow2(ecs[0][r]) * pow2(ecs[1][cc]);
+          double* cp = p.C + gi * p.ldc + gj;
+          if (p.mode == 0) *cp = v;
+          else if (p.mode == 1) *cp += (p.rowscale ? p.rowscale[gi] : 1.0) * v;
+          else *cp -= v;
         }
       }
     }
@@ -377,68 +377,102 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
-// pre-pass: column exponents and the slice split (transposed, K-major)
+// operand preparation: exponents and slices (K-major, [S][npad][kpad] BF16)
 // ---------------------------------------------------------------------------
+// digits of one value x with exponent e into the S slice values
+template <int S>
+__device__ __forceinline__ void digits(double x, int e, __nv_bfloat16* out, int64_t stride) {
+  long long v = llrint(ldexp(x, 8 * S - e));
+  int a[S];
+#pragma unroll
+  for (int q = S - 1; q >= 1; q--) {
+    const long long d = (v + 128) >> 8;
+    a[q] = (int)(v - (d << 8));
+    v = d;
+  }
+  a[0] = (int)v;
+#pragma unroll
+  for (int q = 0; q < S; q++) out[q * stride] = __float2bfloat16_rn(ldexpf((float)a[q], -8 * (q + 1)));
+}
+
+// columns of a K x n row-major matrix (J layout): partial column maxima over 64 row chunks
 constexpr int CM_CHUNKS = 64;
-__global__ void colmax_partial(const double* __restrict__ J, int64_t ld, int64_t nrows, int64_t ncols, double* part) {
+__global__ void colmax_partial(const double* __restrict__ X, int64_t ld, int64_t nrows, int64_t ncols,
+                               double* part) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= ncols) return;
   const int c = blockIdx.y;
   const int64_t per = (nrows + CM_CHUNKS - 1) / CM_CHUNKS;
   const int64_t r0 = c * per, r1 = (r0 + per < nrows) ? r0 + per : nrows;
   double m = 0.0;
-  for (int64_t r = r0; r < r1; r++) m = fmax(m, fabs(J[r * ld + j]));
+  for (int64_t r = r0; r < r1; r++) m = fmax(m, fabs(X[r * ld + j]));
   part[(int64_t)c * ncols + j] = m;
 }
-__global__ void colexp_kernel(const double* __restrict__ part, int64_t ncols, int64_t Ppad, int* ecol) {
+__global__ void colexp_kernel(const double* __restrict__ part, int64_t ncols, int64_t npad, int* e) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= Ppad) return;
-  int e = 0;
+  if (j >= npad) return;
+  int ex = 0;
   if (j < ncols) {
     double m = 0.0;
     for (int c = 0; c < CM_CHUNKS; c++) m = fmax(m, part[(int64_t)c * ncols + j]);
-    if (m > 0.0 && isfinite(m)) frexp(m, &e);  // m = f 2^e, f in [0.5, 1): 2^e > m
+    if (m > 0.0 && isfinite(m)) frexp(m, &ex);  // m = f 2^ex, f in [0.5, 1): 2^ex > m
   }
-  ecol[j] = e;
+  e[j] = ex;
 }
-
-// 64 rows x 32 columns of J per block -> S slice rows of 64 BF16 each (per column).
+// 64 rows x 32 columns per block, transposed through shared memory
 template <int S>
-__global__ void __launch_bounds__(256) split_kernel(const double* __restrict__ J, int64_t ld, int64_t nrows,
-                                                    int64_t ncols, const int* __restrict__ ecol, int64_t Ppad,
-                                                    int64_t Kpad, __nv_bfloat16* out) {
+__global__ void __launch_bounds__(256) split_cols_kernel(const double* __restrict__ X, int64_t ld, int64_t nrows,
+                                                         int64_t ncols, const int* __restrict__ e, int64_t npad,
+                                                         int64_t kpad, __nv_bfloat16* out) {
   __shared__ __align__(16) __nv_bfloat16 sl[S][32][64 + 8];
   const int t = threadIdx.x;
   const int64_t k0 = (int64_t)blockIdx.x * 64, j0 = (int64_t)blockIdx.y * 32;
   const int jj = t & 31;
   const int64_t j = j0 + jj;
-  const int e = (j < Ppad) ? ecol[j] : 0;
+  const int ex = (j < npad) ? e[j] : 0;
 #pragma unroll
   for (int r = 0; r < 8; r++) {
     const int kk = (t >> 5) + 8 * r;
     const int64_t k = k0 + kk;
-    double x = (k < nrows && j < ncols) ? J[k * ld + j] : 0.0;
-    long long v = llrint(ldexp(x, 8 * S - e));
-    int a[S];
-#pragma unroll
-    for (int q = S - 1; q >= 1; q--) {
-      const long long d = (v + 128) >> 8;
-      a[q] = (int)(v - (d << 8));
-      v = d;
-    }
-    a[0] = (int)v;
-#pragma unroll
-    for (int q = 0; q < S; q++) sl[q][jj][kk] = __float2bfloat16_rn(ldexpf((float)a[q], -8 * (q + 1)));
+    const double x = (k < nrows && j < ncols) ? X[k * ld + j] : 0.0;
+    digits<S>(x, ex, &sl[0][jj][kk], 32 * (64 + 8));
   }
   __syncthreads();
-  // write: per (slice, column) 64 BF16 = 128 bytes, 16 bytes per thread
   for (int idx = t; idx < S * 32 * 8; idx += 256) {
     const int q = idx / (32 * 8), rem = idx % (32 * 8);
     const int c = rem / 8, seg = rem % 8;
     const int64_t col = j0 + c;
-    if (col >= Ppad || k0 + seg * 8 >= Kpad) continue;
+    if (col >= npad || k0 + seg * 8 >= kpad) continue;
     const uint4 val = *reinterpret_cast<const uint4*>(&sl[q][c][seg * 8]);
-    *reinterpret_cast<uint4*>(out + ((int64_t)q * Ppad + col) * Kpad + k0 + seg * 8) = val;
+    *reinterpret_cast<uint4*>(out + ((int64_t)q * npad + col) * kpad + k0 + seg * 8) = val;
+  }
+}
+// rows of an n x K row-major matrix: one warp per row for the exponent
+__global__ void rowexp_kernel(const double* __restrict__ X, int64_t ld, int64_t nrows, int64_t k, int64_t npad,
+                              int* e) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= npad) return;
+  double m = 0.0;
+  if (row < nrows)
+    for (int64_t c = lane; c < k; c += 32) m = fmax(m, fabs(X[row * ld + c]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+  if (lane == 0) {
+    int ex = 0;
+    if (m > 0.0 && isfinite(m)) frexp(m, &ex);
+    e[row] = ex;
+  }
+}
+template <int S>
+__global__ void split_rows_kernel(const double* __restrict__ X, int64_t ld, int64_t nrows, int64_t k,
+                                  const int* __restrict__ e, int64_t npad, int64_t kpad, __nv_bfloat16* out) {
+  const int64_t total = npad * kpad;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = idx / kpad, c = idx - row * kpad;
+    const double x = (row < nrows && c < k) ? X[row * ld + c] : 0.0;
+    digits<S>(x, e[row], out + row * kpad + c, npad * kpad);
   }
 }
 
@@ -452,52 +486,29 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 EncodeTiledFn get_encode() {
   static EncodeTiledFn fn = nullptr;
   if (!fn) {
-    void* p = nullptr;
+    void* ptr = nullptr;
     cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &ptr, cudaEnableDefault, &q) == cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
   }
   return fn;
 }
 
-struct SplitWs {
-  int64_t Ppad, Kpad;
-  int S;
-  __nv_bfloat16* slices;
-  int* ecol;
-  double* part;
-  size_t bytes;
-};
+int64_t rup(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
-template <int S>
-int launch_split(gn_handle* h, const double* J, int64_t ld, int64_t nrows, double* G, int accumulate, SplitWs& ws) {
-  cudaStream_t st = h->st;
-  const int64_t Pp = h->Pp;
-  // pre-pass
-  {
-    dim3 g((unsigned)((Pp + 127) / 128), CM_CHUNKS);
-    colmax_partial<<<g, 128, 0, st>>>(J, ld, nrows, Pp, ws.part);
-    count_launch();
-    colexp_kernel<<<(unsigned)((ws.Ppad + 255) / 256), 256, 0, st>>>(ws.part, Pp, ws.Ppad, ws.ecol);
-    count_launch();
-    dim3 gs((unsigned)(ws.Kpad / 64), (unsigned)(ws.Ppad / 32));
-    split_kernel<S><<<gs, 256, 0, st>>>(J, ld, nrows, Pp, ws.ecol, ws.Ppad, ws.Kpad, ws.slices);
-    count_launch();
-  }
-  if (GN_NOTE(cudaGetLastError()) != cudaSuccess) return GN_ERR_CUDA;
+int encode(const OzOperand& op, int S, CUtensorMap* map) {
   EncodeTiledFn enc = get_encode();
   if (!enc) {
     set_detail(__FILE__, __LINE__, "cuTensorMapEncodeTiled entry point not found");
     return GN_ERR_UNSUPPORTED;
   }
-  CUtensorMap map;
-  memset(&map, 0, sizeof(map));
-  cuuint64_t dims[2] = {(cuuint64_t)ws.Kpad, (cuuint64_t)(S * ws.Ppad)};
-  cuuint64_t strides[1] = {(cuuint64_t)(ws.Kpad * 2)};
+  memset(map, 0, sizeof(*map));
+  cuuint64_t dims[2] = {(cuuint64_t)op.kpad, (cuuint64_t)(S * op.npad)};
+  cuuint64_t strides[1] = {(cuuint64_t)(op.kpad * 2)};
   cuuint32_t box[2] = {BKS, TM};
   cuuint32_t estr[2] = {1, 1};
-  CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ws.slices, dims, strides, box, estr,
+  CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, op.slices, dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) {
@@ -506,62 +517,156 @@ int launch_split(gn_handle* h, const double* J, int64_t ld, int64_t nrows, doubl
     set_detail(__FILE__, __LINE__, msg);
     return GN_ERR_CUDA;
   }
-  constexpr int NST = n_stages(S);
+  return GN_OK;
+}
+
+template <int S>
+int prep_cols(const double* X, int64_t ld, int64_t k, int64_t n, const OzOperand& op, double* part,
+              cudaStream_t st) {
+  dim3 g((unsigned)((n + 127) / 128), CM_CHUNKS);
+  colmax_partial<<<g, 128, 0, st>>>(X, ld, k, n, part);
+  count_launch();
+  colexp_kernel<<<(unsigned)((op.npad + 255) / 256), 256, 0, st>>>(part, n, op.npad, op.e);
+  count_launch();
+  dim3 gs((unsigned)((op.kpad + 63) / 64), (unsigned)(op.npad / 32));   // kpad is a multiple of 32
+  split_cols_kernel<S><<<gs, 256, 0, st>>>(X, ld, k, n, op.e, op.npad, op.kpad,
+                                          static_cast<__nv_bfloat16*>(op.slices));
+  count_launch();
+  return GN_NOTE(cudaGetLastError()) == cudaSuccess ? GN_OK : GN_ERR_CUDA;
+}
+
+template <int S>
+int prep_rows(const double* X, int64_t ld, int64_t n, int64_t k, const OzOperand& op, cudaStream_t st) {
+  rowexp_kernel<<<(unsigned)((op.npad * 32 + 255) / 256), 256, 0, st>>>(X, ld, n, k, op.npad, op.e);
+  count_launch();
+  int64_t blocks = (op.npad * op.kpad + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  split_rows_kernel<S><<<(unsigned)blocks, 256, 0, st>>>(X, ld, n, k, op.e, op.npad, op.kpad,
+                                                         static_cast<__nv_bfloat16*>(op.slices));
+  count_launch();
+  return GN_NOTE(cudaGetLastError()) == cudaSuccess ? GN_OK : GN_ERR_CUDA;
+}
+
+template <int S, bool SYM>
+int launch_oz(const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, double* C, int64_t ldc, int mode,
+              const double* rowscale, int* flag, cudaStream_t st) {
+  CUtensorMap ma, mb;
+  int rc = encode(A, S, &ma);
+  if (rc) return rc;
+  rc = encode(B, S, &mb);
+  if (rc) return rc;
   const size_t smem = (size_t)bar_offset(S) + 1024 + 256;
-  if (GN_NOTE(cudaFuncSetAttribute(gram_split_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+  if (GN_NOTE(cudaFuncSetAttribute(ozaki_kernel<S, SYM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
       cudaSuccess)
     return GN_ERR_CUDA;
-  const int64_t nt = ws.Ppad / TM;
-  const int64_t tiles = nt * (nt + 1) / 2;
-  if (GN_NOTE(cudaMemsetAsync(h->flag + 2, 0, sizeof(int), st)) != cudaSuccess) return GN_ERR_CUDA;
-  gram_split_kernel<S><<<(unsigned)tiles, NTHREADS, smem, st>>>(map, ws.Ppad, ws.Kpad, Pp, ws.ecol, G, Pp,
-                                                                 accumulate, h->flag + 2);
+  OzArgs a;
+  a.rowsA = A.npad;
+  a.rowsB = B.npad;
+  a.Kpad = A.kpad;
+  a.M = M;
+  a.N = N;
+  const int64_t mt = (M + TM - 1) / TM, nt = (N + TN - 1) / TN;
+  a.nt = (int)nt;
+  a.eA = A.e;
+  a.eB = B.e;
+  a.C = C;
+  a.ldc = ldc;
+  a.mode = mode;
+  a.rowscale = rowscale;
+  a.flag = flag;
+  const int64_t tiles = SYM ? mt * (mt + 1) / 2 : mt * nt;
+  if (tiles <= 0) return GN_OK;
+  ozaki_kernel<S, SYM><<<(unsigned)tiles, NTHREADS, smem, st>>>(ma, mb, a);
   count_launch();
-  if (GN_NOTE(cudaGetLastError()) != cudaSuccess) return GN_ERR_CUDA;
-  int hflag = 0;
-  if (GN_NOTE(cudaMemcpyAsync(&h->hpin[9], h->flag + 2, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-      GN_NOTE(cudaStreamSynchronize(st)) != cudaSuccess)
-    return GN_ERR_CUDA;
-  memcpy(&hflag, &h->hpin[9], sizeof(int));
-  if (hflag & 2) return GN_ERR_TIMEOUT;
-  return GN_OK;
+  return GN_NOTE(cudaGetLastError()) == cudaSuccess ? GN_OK : GN_ERR_CUDA;
 }
 
 }  // namespace
 
+size_t oz_operand_bytes(int S, int64_t n, int64_t k) {
+  const int64_t npad = rup(n > 0 ? n : 1, TM), kpad = rup(k > 0 ? k : 1, BKS);
+  return rup((size_t)S * npad * kpad * 2, 256) + rup((size_t)npad * sizeof(int), 256);
+}
+
+OzOperand oz_operand_at(void* base, int S, int64_t n, int64_t k) {
+  OzOperand op;
+  op.npad = rup(n > 0 ? n : 1, TM);
+  op.kpad = rup(k > 0 ? k : 1, BKS);
+  op.slices = static_cast<__nv_bfloat16*>(base);
+  op.e = reinterpret_cast<int*>(static_cast<unsigned char*>(base) + rup((size_t)S * op.npad * op.kpad * 2, 256));
+  return op;
+}
+
+int oz_prepare_cols(int S, const double* X, int64_t ld, int64_t k, int64_t n, const OzOperand& op, double* part,
+                    cudaStream_t st) {
+  switch (S) {
+    case 1: return prep_cols<1>(X, ld, k, n, op, part, st);
+    case 2: return prep_cols<2>(X, ld, k, n, op, part, st);
+    case 3: return prep_cols<3>(X, ld, k, n, op, part, st);
+    case 4: return prep_cols<4>(X, ld, k, n, op, part, st);
+    case 5: return prep_cols<5>(X, ld, k, n, op, part, st);
+    case 6: return prep_cols<6>(X, ld, k, n, op, part, st);
+    default: return GN_ERR_UNSUPPORTED;
+  }
+}
+
+int oz_prepare_rows(int S, const double* X, int64_t ld, int64_t n, int64_t k, const OzOperand& op,
+                    cudaStream_t st) {
+  switch (S) {
+    case 1: return prep_rows<1>(X, ld, n, k, op, st);
+    case 2: return prep_rows<2>(X, ld, n, k, op, st);
+    case 3: return prep_rows<3>(X, ld, n, k, op, st);
+    case 4: return prep_rows<4>(X, ld, n, k, op, st);
+    case 5: return prep_rows<5>(X, ld, n, k, op, st);
+    case 6: return prep_rows<6>(X, ld, n, k, op, st);
+    default: return GN_ERR_UNSUPPORTED;
+  }
+}
+
+int oz_gemm(int S, bool sym, const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, double* C, int64_t ldc,
+            int mode, const double* rowscale, int* flag, cudaStream_t st) {
+  if (A.kpad != B.kpad) return GN_ERR_INVALID;
+#define GN_OZ_CASE(s)                                                                     \
+  case s:                                                                                 \
+    return sym ? launch_oz<s, true>(A, B, M, N, C, ldc, mode, rowscale, flag, st)         \
+               : launch_oz<s, false>(A, B, M, N, C, ldc, mode, rowscale, flag, st);
+  switch (S) {
+    GN_OZ_CASE(1)
+    GN_OZ_CASE(2)
+    GN_OZ_CASE(3)
+    GN_OZ_CASE(4)
+    GN_OZ_CASE(5)
+    GN_OZ_CASE(6)
+    default: return GN_ERR_UNSUPPORTED;
+  }
+#undef GN_OZ_CASE
+}
+
+int ensure_split_ws(gn_handle* h, size_t need) {
+  if (h->split_ws_bytes >= need) return GN_OK;
+  if (h->split_ws) cudaFree(h->split_ws);   // synchronises: no kernel still reads it
+  h->split_ws = nullptr;
+  h->split_ws_bytes = 0;
+  if (GN_NOTE(cudaMalloc(&h->split_ws, need)) != cudaSuccess) return GN_ERR_OOM;
+  h->split_ws_bytes = need;
+  return GN_OK;
+}
+
+// Gram through the split GEMM: G (lower tiles) = J^T J or += (accumulate).
 int split_gram(gn_handle* h, const double* J, int64_t ld, int64_t nrows, double* G, int accumulate) {
   const int S = h->n_slices;
-  if (S < 1 || S > kMaxSlices) return GN_ERR_UNSUPPORTED;
+  if (S < 1 || S > kOzMaxSlices) return GN_ERR_UNSUPPORTED;
   if (nrows <= 0) return GN_OK;
-  int major = 0, minor = 0;
-  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, h->dev);
-  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, h->dev);
-  if (major != 10) return GN_ERR_UNSUPPORTED;
-  SplitWs ws;
-  ws.S = S;
-  ws.Ppad = (h->Pp + TM - 1) / TM * TM;
-  ws.Kpad = (nrows + KC - 1) / KC * KC;
-  const size_t slice_bytes = (size_t)S * ws.Ppad * ws.Kpad * 2;
-  const size_t need = slice_bytes + (size_t)ws.Ppad * sizeof(int) + (size_t)CM_CHUNKS * ws.Ppad * 8 + 4096;
-  if (h->split_ws_bytes < need) {
-    if (h->split_ws) cudaFree(h->split_ws);
-    h->split_ws = nullptr;
-    h->split_ws_bytes = 0;
-    if (cudaMalloc(&h->split_ws, need) != cudaSuccess) return GN_ERR_OOM;
-    h->split_ws_bytes = need;
-  }
-  unsigned char* p = static_cast<unsigned char*>(h->split_ws);
-  ws.slices = reinterpret_cast<__nv_bfloat16*>(p);
-  ws.part = reinterpret_cast<double*>(p + ((slice_bytes + 255) / 256) * 256);
-  ws.ecol = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(ws.part) + (size_t)CM_CHUNKS * ws.Ppad * 8);
-  switch (S) {
-    case 1: return launch_split<1>(h, J, ld, nrows, G, accumulate, ws);
-    case 2: return launch_split<2>(h, J, ld, nrows, G, accumulate, ws);
-    case 3: return launch_split<3>(h, J, ld, nrows, G, accumulate, ws);
-    case 4: return launch_split<4>(h, J, ld, nrows, G, accumulate, ws);
-    case 5: return launch_split<5>(h, J, ld, nrows, G, accumulate, ws);
-    default: return launch_split<6>(h, J, ld, nrows, G, accumulate, ws);
-  }
+  const size_t opb = oz_operand_bytes(S, h->Pp, nrows);
+  int rc = ensure_split_ws(h, opb + (size_t)CM_CHUNKS * rup(h->Pp, TM) * 8 + 256);
+  if (rc) return rc;
+  OzOperand op = oz_operand_at(h->split_ws, S, h->Pp, nrows);
+  double* part = reinterpret_cast<double*>(static_cast<unsigned char*>(h->split_ws) + opb);
+  rc = oz_prepare_cols(S, J, ld, nrows, h->Pp, op, part, h->st);
+  if (rc) return rc;
+  rc = oz_gemm(S, true, op, op, h->Pp, h->Pp, G, h->Pp, accumulate ? 1 : 0, nullptr, h->flag + 2, h->st);
+  if (rc) return rc;
+  return GN_OK;
 }
 
 }  // namespace gn

@@ -29,6 +29,7 @@ GN_ERR_TOO_LARGE = -8
 
 GN_PREC_FP64 = 0
 GN_PREC_SPLIT_BF16 = 1
+GN_PREC_SPLIT_ALL = 2
 GN_MAX_LAYERS = 8
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libgn.so")

@@ -88,3 +88,56 @@ def test_split_gram_accumulate_two_row_blocks():
     Gx = J.T @ J
     bound = split_bound(J[:h], 4) + split_bound(J[h:], 4)
     assert np.all(np.tril(np.abs(host(G) - Gx)) <= 2.0 * np.tril(bound) + 1e-300)
+
+
+SPLIT_ALL = 2
+
+
+def test_split_all_jacobian_hilbert_contraction():
+    """CCF Jacobian with the Hilbert contraction J_U = K J_g on the tensor cores (S = 6)."""
+    from tests.gpu_cases import TOL, rel
+    w = small("ccf")
+    p = oracle_problem(w)
+    J_o = ogn.jacobian(p, w.theta, w.lam)
+    prob = gpu_problem(w, precision=SPLIT_ALL, n_slices=6)
+    J = host(prob.jacobian(dev(w.theta), w.lam))
+    assert rel(J, J_o) <= TOL
+
+
+def test_split_all_damped_solve():
+    """Blocked Cholesky with split trailing updates: backward error and agreement with the oracle."""
+    w = small("ccf")
+    p = oracle_problem(w)
+    J_o = ogn.jacobian(p, w.theta, w.lam)
+    r_o = p.rows(w.theta, w.lam)
+    Go, go = J_o.T @ J_o, J_o.T @ r_o
+    prob = gpu_problem(w, precision=SPLIT_ALL, n_slices=6)
+    delta = prob.new_vec(prob.P + 1)
+    rc, gam, retries = prob.gn_damped_solve(dev(Go), dev(go), 1e-6, delta)
+    assert rc == 0 and retries == 0
+    A = Go + 1e-6 * np.eye(len(go))
+    d = host(delta)
+    assert np.max(np.abs(A @ d - go)) / (np.max(np.abs(A)) * np.max(np.abs(d))) <= 1e-12
+    d_o, _, _, _ = ogn.damped_solve(Go, go, 1e-6)
+    assert np.max(np.abs(d - d_o)) / np.max(np.abs(d_o)) <= max(1e-12, 1e-14 * np.linalg.cond(A))
+
+
+@pytest.mark.parametrize("name", ["ccf", "ipm"])
+def test_split_all_gn_step_matches_oracle(name):
+    w = small(name)
+    p = oracle_problem(w)
+    th_o, lam_o, gam_o, info_o = ogn.gn_step(p, w.theta, w.lam, w.gamma)
+    prob = gpu_problem(w, precision=SPLIT_ALL, n_slices=6)
+    theta = dev(w.theta)
+    rc, lam, gam, info = prob.gn_step(theta, w.lam, w.gamma)
+    assert rc == info_o["status"] and info["alpha"] == info_o["alpha"]
+    assert gam == pytest.approx(gam_o, rel=1e-15)
+    if rc != 0:     # both rejected the step: theta and lambda are unchanged
+        assert np.array_equal(host(theta), w.theta) and lam == w.lam
+        return
+    cond = np.linalg.cond(info_o["G"] + info_o["gamma_used"] * np.eye(p.P + 1))
+    d_gpu = np.concatenate([w.theta - host(theta), [w.lam - lam]])
+    d_o = np.concatenate([w.theta - th_o, [w.lam - lam_o]])
+    # G, J_U and the factorisation each carry ~1e-13 relative error at S = 6
+    # (FP32 tail accumulator); the step amplifies it by cond(G + gamma I)
+    assert np.max(np.abs(d_gpu - d_o)) / np.max(np.abs(d_o)) <= max(1e-12, 2e-13 * cond)
