@@ -48,7 +48,75 @@ def parse():
     ap.add_argument("--micro", default=None, choices=[None, "gram"],
                     help="time one kernel family alone instead of the GN step (not the bench contract line)")
     ap.add_argument("--width", type=int, default=44, help="--micro gram: hidden width w of a 1-w-w-1 CCF net")
+    ap.add_argument("--equal-residual", action="store_true",
+                    help="FP64 path for --er-steps steps vs split path to the same max residual (own JSON line)")
+    ap.add_argument("--er-steps", type=int, default=50)
     return ap.parse_args()
+
+
+def validation_grid_1d(n_log=60000, n_uni=40000):
+    """Dense validation grid for the 1D max-d0 residual (the paper's grids are in its SI):
+    log-spaced on [1e-4, 1e5] plus uniform on [0, 10] (uniform points start at 1e-4)."""
+    import numpy as np
+    g = np.concatenate([10.0 ** np.linspace(-4, 5, n_log), np.linspace(1e-4, 10.0, n_uni)])
+    return g.reshape(1, -1)
+
+
+def equal_residual(args):
+    """Residual reached by the FP64 path after N GN steps, and the device time the split
+    path needs to reach 1.1x that residual from the same initialisation.  The residual
+    compared is the training loss h = |r~|^2/2 (the d0 loss the step minimises, which
+    the line search makes monotone); the max d0 residual on a 1e5-point validation grid
+    is reported beside it (evaluated outside the timed region)."""
+    import torch
+    from paper_2509_14185_gb300 import build as B
+    B.build()
+    from paper_2509_14185_gb300 import gn, inputs
+    w = inputs.ccf_unstable_1d()
+    grid = validation_grid_1d()
+    val = gn.GNProblem(w.equation, w.widths, grid, y_norm=w.y_norm, c_norm=w.c_norm, hilbert_m=w.hilbert_m)
+
+    def run(prec, max_steps, target=None):
+        prob = gn.GNProblem.from_workload(w, precision=prec, n_slices=args.slices)
+        theta = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
+        lam, gam = w.lam, w.gamma
+        t_ms, hist = 0.0, []
+        for k in range(max_steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            rc, lam, gam, info = prob.gn_step(theta, lam, gam)
+            e1.record()
+            torch.cuda.synchronize()
+            t_ms += e0.elapsed_time(e1)
+            res = val.gn_max_residual(theta, lam)
+            hist.append({"step": k + 1, "ms": t_ms, "max_res": res, "lambda": lam, "loss": info["loss_after"],
+                         "rc": rc})
+            if target is not None and info["loss_after"] <= target:
+                break
+        prob.close()
+        return hist
+
+    h64 = run(gn.GN_PREC_FP64, args.er_steps)
+    target = h64[-1]["loss"] * 1.1
+    prec = {"split": gn.GN_PREC_SPLIT_BF16, "split_all": gn.GN_PREC_SPLIT_ALL}.get(args.precision,
+                                                                                gn.GN_PREC_SPLIT_ALL)
+    hs = run(prec, 4 * args.er_steps, target)
+    reached = hs[-1]["loss"] <= target
+    out = {"mode": "equal_residual", "workload": w.name, "grid_points": int(grid.shape[1]),
+           "compared": "training loss h (monotone under accepted GN steps); grid max d0 residual reported",
+           "fp64": {"steps": len(h64), "device_s": h64[-1]["ms"] / 1e3, "loss": h64[-1]["loss"],
+                    "max_res": h64[-1]["max_res"], "lambda": h64[-1]["lambda"]},
+           "split": {"precision": args.precision, "slices": args.slices, "reached": reached,
+                     "steps": len(hs), "device_s": hs[-1]["ms"] / 1e3, "loss": hs[-1]["loss"],
+                     "max_res": hs[-1]["max_res"], "lambda": hs[-1]["lambda"]},
+           "target_loss": target,
+           "speedup_to_equal_residual": (h64[-1]["ms"] / hs[-1]["ms"]) if reached else None,
+           "fp64_curve": [(h["step"], h["loss"], h["max_res"]) for h in h64[::5]],
+           "split_curve": [(h["step"], h["loss"], h["max_res"]) for h in hs[::5]]}
+    print(json.dumps(out))
+    val.close()
+    return 0
 
 
 def micro_gram(args):
@@ -318,6 +386,8 @@ def main():
         return run_reference(args)
     if args.micro == "gram":
         return micro_gram(args)
+    if args.equal_residual:
+        return equal_residual(args)
     import numpy as np
     import torch
 

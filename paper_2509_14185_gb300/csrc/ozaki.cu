@@ -159,6 +159,19 @@ __device__ __forceinline__ void dd_add(float& hi, float& lo, float v) {
 __device__ __forceinline__ double pow2(int e) {
   return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
 }
+__device__ __forceinline__ float pow2f(int e) {
+  return (e >= -126 && e <= 127) ? __int_as_float((e + 127) << 23) : ldexpf(1.0f, e);
+}
+// (u.x, u.y) += (h, l), both double-FP32 (TwoSum, then Fast2Sum renormalisation)
+__device__ __forceinline__ void dd2_add(float2& u, float h, float l) {
+  const float s = __fadd_rn(u.x, h);
+  const float bb = __fsub_rn(s, u.x);
+  const float err = __fadd_rn(__fsub_rn(u.x, __fsub_rn(s, bb)), __fsub_rn(h, bb));
+  const float t = __fadd_rn(__fadd_rn(u.y, l), err);
+  const float hi = __fadd_rn(s, t);
+  u.y = __fsub_rn(t, __fsub_rn(hi, s));
+  u.x = hi;
+}
 // Level of a slice pair and its tensor-memory slot: levels 2, 3, 4 -> slots 0, 1, 2; >= 5 -> 3.
 __device__ __forceinline__ int slot_of(int s, int t) {
   const int l = s + t + 2;  // s, t are 0-based
@@ -174,7 +187,7 @@ struct OzArgs {
   const int* eB;          // exponents of B rows (padded)
   double* C;
   int64_t ldc;
-  int mode;               // 0: C = v, 1: C += rs_i v, 2: C -= v
+  int mode;               // 0: C = v, 1: C += rs_i v, 2: C -= v, 3: C2 += v in double-FP32 (FP32 pipe)
   const double* rowscale; // mode 1 (may be null: 1)
   int* flag;
 };
@@ -272,28 +285,37 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           const int kt = c * SPC + q;
           const int st = kt % NST;
           if (!mbar_wait(&full[st], (kt / NST) & 1, flag)) { ok = false; break; }
-          if (q == 0 && c > 0) {
-            // head accumulators must have been read before they are reset
-            if (!mbar_wait(acc_empty, (c - 1) & 1, flag)) { ok = false; break; }
-          }
           tc_fence_after();
           const uint32_t base = smem_u32(smem + st * STAGE_BYTES);
+          // pass 0: tail levels (>= 5), which the epilogue's per-chunk flush does not
+          // read, so they overlap the flush of the previous chunk; pass 1: the exact
+          // head levels, after the flush has released their accumulators.
 #pragma unroll
-          for (int s = 0; s < S; s++)
-#pragma unroll
-            for (int u = 0; u < S; u++) {
-              if (s + u > S - 1) continue;  // keep levels s + t <= S + 1 (1-based)
-              const int slot = slot_of(s, u);
-#pragma unroll
-              for (int kk = 0; kk < BKS / 16; kk++) {
-                const uint64_t da = smem_desc(base + s * SLICE_BYTES + kk * 32);
-                const uint64_t db = smem_desc(base + (S + u) * SLICE_BYTES + kk * 32);
-                // the first pair of a level (s = 0) resets the slot: per chunk for the
-                // exact head levels, once for the tail
-                const bool first = (slot < 3) ? (q == 0 && kk == 0 && s == 0) : (kt == 0 && kk == 0 && s == 0 && u == 3);
-                mma_bf16(tmem + slot * TN, da, db, first ? 0u : 1u);
-              }
+          for (int pass = 0; pass < 2; pass++) {
+            if (pass == 1 && q == 0 && c > 0) {
+              if (!mbar_wait(acc_empty, (c - 1) & 1, flag)) { ok = false; break; }
+              tc_fence_after();
             }
+#pragma unroll
+            for (int s = 0; s < S; s++)
+#pragma unroll
+              for (int u = 0; u < S; u++) {
+                if (s + u > S - 1) continue;  // keep levels s + t <= S + 1 (1-based)
+                const int slot = slot_of(s, u);
+                if ((slot == 3) != (pass == 0)) continue;
+#pragma unroll
+                for (int kk = 0; kk < BKS / 16; kk++) {
+                  const uint64_t da = smem_desc(base + s * SLICE_BYTES + kk * 32);
+                  const uint64_t db = smem_desc(base + (S + u) * SLICE_BYTES + kk * 32);
+                  // the first pair of a level (s = 0) resets the slot: per chunk for the
+                  // exact head levels, once for the tail
+                  const bool first =
+                      (slot < 3) ? (q == 0 && kk == 0 && s == 0) : (kt == 0 && kk == 0 && s == 0 && u == 3);
+                  mma_bf16(tmem + slot * TN, da, db, first ? 0u : 1u);
+                }
+              }
+          }
+          if (!ok) break;
           mma_commit(&empty[st]);
         }
         if (ok) mma_commit(acc_full);
@@ -353,17 +375,52 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     asm volatile("bar.sync 1, 256;" ::: "memory");
     if (ok) {
+      // 64 elements per thread, in batches of 8 whose global loads are issued
+      // together (a load-modify-store loop would expose one memory latency per element)
       const int et = (warp - 2) * 32 + lane;
-      for (int idx = et; idx < TM * TN; idx += 256) {
-        const int r = idx / TN, cc = idx % TN;
-        const int64_t gi = ti * TM + r, gj = tj * TN + cc;
-        if (gi < p.M && gj < p.N) {
-          const float2 hl = park[r * (TN + 1) + cc];
-          const double v = ((double)hl.x + (double)hl.y) * pow2(ecs[0][r]) * pow2(ecs[1][cc]);
-          double* cp = p.C + gi * p.ldc + gj;
-          if (p.mode == 0) *cp = v;
-          else if (p.mode == 1) *cp += (p.rowscale ? p.rowscale[gi] : 1.0) * v;
-          else *cp -= v;
+      constexpr int B8 = 8;
+      for (int base_i = 0; base_i < TM * TN / 256; base_i += B8) {
+        int64_t off[B8];
+        bool in[B8];
+        float2 hl[B8];
+        double cv[B8];
+        float2 uv[B8];
+        double rs[B8];
+#pragma unroll
+        for (int q = 0; q < B8; q++) {
+          const int idx = et + (base_i + q) * 256;
+          const int r = idx / TN, cc = idx % TN;
+          const int64_t gi = ti * TM + r, gj = tj * TN + cc;
+          in[q] = (gi < p.M && gj < p.N);
+          off[q] = gi * p.ldc + gj;
+          hl[q] = park[r * (TN + 1) + cc];
+          if (p.mode == 3) hl[q] = make_float2(hl[q].x * pow2f(ecs[0][r] + ecs[1][cc]),
+                                              hl[q].y * pow2f(ecs[0][r] + ecs[1][cc]));
+          else cv[q] = ((double)hl[q].x + (double)hl[q].y) * pow2(ecs[0][r] + ecs[1][cc]);
+          rs[q] = (p.mode == 1 && p.rowscale && in[q]) ? p.rowscale[gi] : 1.0;
+        }
+        if (p.mode == 3) {
+          // accumulate without any FP64 arithmetic (GB300's FP64 rate is ~1/60 of FP32)
+          float2* U = reinterpret_cast<float2*>(p.C);
+#pragma unroll
+          for (int q = 0; q < B8; q++) uv[q] = in[q] ? U[off[q]] : make_float2(0.f, 0.f);
+#pragma unroll
+          for (int q = 0; q < B8; q++)
+            if (in[q]) {
+              dd2_add(uv[q], hl[q].x, hl[q].y);
+              U[off[q]] = uv[q];
+            }
+        } else if (p.mode == 0) {
+#pragma unroll
+          for (int q = 0; q < B8; q++)
+            if (in[q]) p.C[off[q]] = cv[q];
+        } else {
+          double old[B8];
+#pragma unroll
+          for (int q = 0; q < B8; q++) old[q] = in[q] ? p.C[off[q]] : 0.0;
+#pragma unroll
+          for (int q = 0; q < B8; q++)
+            if (in[q]) p.C[off[q]] = (p.mode == 1) ? fma(rs[q], cv[q], old[q]) : old[q] - cv[q];
         }
       }
     }
