@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--equal-residual", action="store_true",
                     help="FP64 path for --er-steps steps vs split path to the same max residual (own JSON line)")
     ap.add_argument("--er-steps", type=int, default=50)
+    ap.add_argument("--workload", default="ccf_unstable1",
+                    choices=["ccf_unstable1", "ccf_stable", "ipm", "boussinesq", "batched"],
+                    help="ccf_unstable1 is the headline line; the others print their own line")
+    ap.add_argument("--streams", type=int, default=8, help="--workload batched: CUDA streams (host workers)")
     return ap.parse_args()
 
 
@@ -168,6 +172,27 @@ def micro_gram(args):
     return 0
 
 
+def replica_workload(name, rank):
+    """Replicas: rank k fits its own profile, seeded with the workload's default seed + k
+    (no data-path collective; the units of all ranks add up)."""
+    from paper_2509_14185_gb300 import inputs
+    if name == "batched":
+        return inputs.batched_ccf_sweep(seed=3 + rank)
+    make = inputs.WORKLOADS[name]
+    return make(seed=make.__defaults__[0] + rank)
+
+
+def max_over_ranks(x, device):
+    """The slowest rank's time (the bench reports whole-job throughput over it)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -230,7 +255,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded sample (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
-def oracle_step_estimate(budget_cols=12, chol_n=512, gram_cols=512, _cache={}):
+def oracle_step_estimate(budget_cols=12, chol_n=512, gram_cols=512, workload="ccf_unstable1", _cache={}):
     """Time the oracle's pieces of one GN step on a bounded sample and extrapolate.
 
     Sample: complex-step Jacobian columns (`budget_cols` of the 8514, each a full
@@ -248,12 +273,13 @@ def oracle_step_estimate(budget_cols=12, chol_n=512, gram_cols=512, _cache={}):
     from paper_2509_14185_gb300 import inputs as I
 
     warnings.filterwarnings("ignore", category=RuntimeWarning)
-    if "p" not in _cache:
-        w = I.ccf_unstable_1d()
-        p = Pb.Problem(w.equation, w.widths, w.y, y_norm=w.y_norm, c_norm=w.c_norm, hilbert_m=w.hilbert_m)
+    if workload not in _cache:
+        w = I.WORKLOADS[workload]()
+        p = Pb.Problem(w.equation, w.widths, w.y, w.y_bnd if w.y_bnd.size else None, w.rho, y_norm=w.y_norm,
+                       c_norm=w.c_norm, hilbert_m=w.hilbert_m)
         p.rows(w.theta, w.lam)   # first call pays numpy/BLAS start-up; not timed
-        _cache["p"], _cache["w"] = p, w
-    p, w = _cache["p"], _cache["w"]
+        _cache[workload] = (p, w)
+    p, w = _cache[workload]
     Pp = p.P + 1
     t0 = time.perf_counter()
     r = p.rows(w.theta, w.lam)
@@ -280,8 +306,8 @@ def oracle_step_estimate(budget_cols=12, chol_n=512, gram_cols=512, _cache={}):
         cores = max([i.get("num_threads", 1) for i in threadpool_info()] + [1])
     except Exception:
         cores = os.cpu_count() or 1
-    sample = (f"oracle (numpy FP64, complex-step J) on the same workload: {budget_cols} of {Pp} Jacobian "
-              f"columns over all {p.n_rows} rows, Gram on a {gram_cols}-column slice, textbook Cholesky "
+    sample = (f"oracle (numpy FP64, complex-step J) on the same workload ({w.name}): {budget_cols} of {Pp} "
+              f"Jacobian columns over all {p.n_rows} rows, Gram on a {gram_cols}-column slice, textbook Cholesky "
               f"n={chol_n}, 1 residual pass; extrapolated to one full step ({total:.1f} s)")
     return {"value": 1.0 / total, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
             "seconds_per_step_extrapolated": total, "parts_s": {"jacobian": Pp * t_col, "gram": t_gram,
@@ -296,57 +322,86 @@ def measured_peak(key, default):
         return default, "fallback"
 
 
+def gram_executed_flops(rows, Pp, S):
+    """Tensor-pipe FLOP of one split Gram launch: S(S+1)/2 slice pairs over the 128 x 128
+    lower-triangular tiles of G and the 128-padded K (the Ozaki overhead included)."""
+    nt = -(-Pp // 128)
+    kpad = -(-rows // 128) * 128
+    return S * (S + 1) / 2 * (nt * (nt + 1) / 2) * 128 * 128 * kpad * 2.0
+
+
 def kernel_report(prob, args, phases):
     """Roofline entries of the step's dense phases (algorithmic FLOP / measured phase time).
 
     Gram: rows * P'(P'+1) FLOP (symmetric half).  FP64 path: DFMA pipe against the
-    nominal FP64 peak.  Split path: FP64-equivalent TFLOP/s, plus the tensor-pipe
-    utilisation of the slice products actually executed (S(S+1)/2 pairs over the
-    128 x 128 lower-triangular tiles and the 128-padded K).  Cholesky: P'^3/3 FLOP
-    on the DFMA pipe."""
+    nominal FP64 peak.  Split paths: the tensor-pipe utilisation of the slice
+    products actually executed (S(S+1)/2 pairs over the 128 x 128 lower-triangular
+    tiles and the 128-padded K) against the measured sustained BF16 peak, plus the
+    FP64-equivalent TFLOP/s.  Cholesky: P'^3/3 FLOP; on the FP64 path against the
+    DFMA pipe, on the SPLIT_ALL path reported as FP64-equivalent TFLOP/s only (its
+    time is shared between the FP64 diagonal factors, which are latency-bound on one
+    SM each, and the tensor-core panel solves and trailing updates)."""
     Pp = prob.P + 1
     rows = prob.n_rows
     gram_ms, chol_ms = phases[1], phases[3]
     gram_flops = rows * Pp * (Pp + 1.0)
+    fp64_src = "GB300 nominal FP64 1.25 TFLOP/s (DFMA probe on this pool: 1.19)"
     out = {}
     if args.precision == "fp64":
         a = gram_flops / (gram_ms * 1e-3) / 1e12
         out["gram"] = {"bound": "alu", "achieved": a, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                        "frac": a / FP64_NOMINAL_TFLOPS, "traffic": None, "ms": gram_ms,
                        "kernel": "dgemm_kernel<0,0> (FP64 Gram G = J~^T J~, DFMA pipe)",
-                       "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (DFMA probe on this pool: 1.19)",
-                       "algorithmic_flops_per_launch": gram_flops}
+                       "peak_source": fp64_src, "algorithmic_flops_per_launch": gram_flops}
     else:
         S = args.slices
         pk, src = measured_peak("bf16_tflops_sustained", 1700.0)
-        nt = -(-Pp // 128)
-        kpad = -(-rows // 128) * 128
-        executed = S * (S + 1) / 2 * (nt * (nt + 1) / 2) * 128 * 128 * kpad * 2.0
+        executed = gram_executed_flops(rows, Pp, S)
         tens = executed / (gram_ms * 1e-3) / 1e12
         out["gram"] = {"bound": "tensor", "achieved": tens, "peak": pk, "unit": "TFLOP/s", "frac": tens / pk,
                        "traffic": None, "ms": gram_ms,
-                       "kernel": f"gram_split_kernel<{S}> (BF16 slice products on tcgen05; pre-pass included)",
+                       "kernel": f"ozaki_kernel<{S},1> (BF16 slice products on tcgen05, TMEM accumulators; "
+                                 "the slicing pre-pass is inside the timed phase)",
                        "peak_source": src + ", sustained: the kernel runs inside a long step",
                        "executed_flops_per_launch": executed,
                        "fp64_equivalent_tflops": gram_flops / (gram_ms * 1e-3) / 1e12,
                        "algorithmic_flops_per_launch": gram_flops}
     cf = Pp ** 3 / 3.0
     c = cf / (chol_ms * 1e-3) / 1e12
-    out["cholesky"] = {"bound": "alu", "achieved": c, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                       "frac": c / FP64_NOMINAL_TFLOPS, "traffic": None, "ms": chol_ms,
-                       "kernel": "potrf_diag + dgemm_kernel<1,1> (blocked FP64 Cholesky, DFMA pipe)",
-                       "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (DFMA probe on this pool: 1.19)",
-                       "algorithmic_flops_per_launch": cf}
-    out["jacobian"] = {"ms": phases[0], "note": "jets + residual + J rows (FP64 pipe) and the CCF Hilbert "
-                                                "contraction (FP64 DGEMM)"}
+    if args.precision == "split_all":
+        out["cholesky"] = {"bound": "mixed", "fp64_equivalent_tflops": c, "ms": chol_ms,
+                           "kernel": f"potrf_diag (FP64, one SM per 64 x 64 block) + ozaki_kernel<{args.slices},0> "
+                                     f"(panel solves) + ozaki_kernel<{args.slices},1> (trailing updates, "
+                                     "double-FP32 accumulation)",
+                           "algorithmic_flops_per_launch": cf}
+    else:
+        out["cholesky"] = {"bound": "alu", "achieved": c, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                           "frac": c / FP64_NOMINAL_TFLOPS, "traffic": None, "ms": chol_ms,
+                           "kernel": "potrf_diag + dgemm_kernel<1,1> (blocked FP64 Cholesky, DFMA pipe)",
+                           "peak_source": fp64_src, "algorithmic_flops_per_launch": cf}
+    out["jacobian"] = {"ms": phases[0], "note": "jets + residual + J rows (FP64 pipe); CCF adds the Hilbert "
+                                                "contraction (FP64 DGEMM, or split on tcgen05 under SPLIT_ALL)"}
     return out
 
 
+def mlp_name(widths):
+    inner = widths[1:-1]
+    if len(set(inner)) == 1 and len(inner) > 1:
+        return f"{widths[0]}-{inner[0]}x{len(inner)}-{widths[-1]} tanh"
+    return "-".join(str(v) for v in widths) + " tanh"
+
+
 def workload_config(w, precision, slices):
-    return {"workload": w.name, "equation": "ccf", "mlp": "1-64-64-64-1 tanh", "params": int(w.n_params) + 1,
-            "n_pts": int(w.n_pts), "rows": int(w.n_pts + 1), "hilbert_nodes": int(w.hilbert_m),
+    from paper_2509_14185_gb300 import inputs as I
+    rows = w.n_pts * I.EQUATION_FIELDS[w.equation] + w.n_bnd + 1
+    J_gb = rows * (w.n_params + 1) * 8 / 1e9
+    return {"workload": w.name, "equation": I.EQUATION_NAMES[w.equation],
+            "mlp": mlp_name(w.widths), "params": int(w.n_params) + 1, "n_pts": int(w.n_pts),
+            "n_bnd": int(w.n_bnd), "rows": int(rows),
+            "hilbert_nodes": int(w.hilbert_m) if w.equation == I.CCF else None,
             "gram_precision": precision if precision == "fp64" else f"split_bf16_s{slices}",
-            "l2": "working set (J~ 1.1 GB, G 0.58 GB) larger than L2; no flush needed",
+            "l2": f"working set (J~ {J_gb:.2f} GB) larger than the 129 MB L2; no flush needed"
+                  if J_gb > 0.2 else "small working set: fits in L2 between steps",
             "parallelism": "replicas"}
 
 
@@ -377,6 +432,90 @@ def run_reference(args):
     return 0
 
 
+def run_batched(args):
+    """64 uneven CCF fits (widths 16..64, depth 2-3, 2048..16384 points, lambda ~ U[0.5, 3])
+    stepped together through gn_batch_step on `--streams` CUDA streams.  value = fit-steps/s
+    (64 x steps / time).  gn_step returns only after its stream is idle, so the span between
+    two events on an otherwise idle stream, recorded before and after the K batched steps,
+    is the device-clock time of the whole batch."""
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2509_14185_gb300 import build as B
+    B.build()
+    from paper_2509_14185_gb300 import gn, inputs
+    fits = replica_workload("batched", rank)
+    prec = {"fp64": gn.GN_PREC_FP64, "split": gn.GN_PREC_SPLIT_BF16, "split_all": gn.GN_PREC_SPLIT_ALL}[args.precision]
+    batch = gn.GNBatch(fits, n_streams=args.streams, precision=prec, n_slices=args.slices)
+    thetas = [torch.tensor(w.theta, dtype=torch.float64, device="cuda") for w in fits]
+    lams = [w.lam for w in fits]
+    gams = [w.gamma for w in fits]
+    for _ in range(args.warmup):
+        lams, gams, infos, st = batch.gn_batch_step(thetas, lams, gams)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    L = gn.lib()
+    launches0 = L.gn_kernel_launches()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    statuses = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        lams, gams, infos, st = batch.gn_batch_step(thetas, lams, gams)
+        statuses.append(st)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    launches = L.gn_kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        ms = max_over_ranks(ms, "cuda")
+        dist.barrier()
+    n = len(fits)
+    value = world * n * 1000.0 / ms
+    rows = [w.n_pts + 1 for w in fits]
+    Pps = [w.n_params + 1 for w in fits]
+    gram_flops = sum(r * p * (p + 1.0) for r, p in zip(rows, Pps))
+    chol_flops = sum(p ** 3 / 3.0 for p in Pps)
+    line = None
+    if rank == 0:
+        kern = {"batched_step": {"ms": ms, "fp64_equivalent_gram_tflops": gram_flops / (ms * 1e-3) / 1e12,
+                                 "fp64_equivalent_cholesky_tflops_if_alone": chol_flops / (ms * 1e-3) / 1e12}}
+        roof = None
+        if prec != gn.GN_PREC_FP64:
+            pk, src = measured_peak("bf16_tflops_sustained", 1700.0)
+            ex = sum(gram_executed_flops(r, p, args.slices) for r, p in zip(rows, Pps))
+            a = ex / (ms * 1e-3) / 1e12
+            roof = {"bound": "tensor", "achieved": a, "peak": pk, "unit": "TFLOP/s", "frac": a / pk,
+                    "traffic": None, "kernel": f"ozaki_kernel<{args.slices},1> Gram launches of all fits",
+                    "note": "executed Gram slice-product FLOP of all fits / whole batched step time "
+                            "(a lower bound on the Gram kernels' own rate)", "peak_source": src}
+        line = {"metric": "gn_fit_steps_per_s", "value": value, "unit": "fit-steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"batched_ccf_sweep_{n}_fits", "fits": n, "streams": args.streams,
+                           "params_range": [min(Pps), max(Pps)], "n_pts_range": [min(rows) - 1, max(rows) - 1],
+                           "gram_precision": args.precision if args.precision == "fp64"
+                           else f"split_bf16_s{args.slices}",
+                           "l2": "working set (all fits' J~, several GB) larger than L2; no flush needed",
+                           "parallelism": "replicas"},
+                "roofline": roof, "kernels": kern, "cpu_baseline": None, "e2e": None, "clocks": clocks,
+                "gpu_launches": int(launches),
+                "final": {"loss_mean": statistics.mean(i["loss_after"] for i in infos),
+                          "warnings": sum(1 for st in statuses for x in st if x != 0)}}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    batch.close()
+    return 0
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -388,6 +527,8 @@ def main():
         return micro_gram(args)
     if args.equal_residual:
         return equal_residual(args)
+    if args.workload == "batched":
+        return run_batched(args)
     import numpy as np
     import torch
 
@@ -401,7 +542,7 @@ def main():
     from paper_2509_14185_gb300 import gn, inputs
 
     # replicas: every rank fits its own seeded profile (no data-path collective)
-    w = inputs.ccf_unstable_1d(seed=2 + rank)
+    w = replica_workload(args.workload, rank)
     prec = {"fp64": gn.GN_PREC_FP64, "split": gn.GN_PREC_SPLIT_BF16, "split_all": gn.GN_PREC_SPLIT_ALL}[args.precision]
     prob = gn.GNProblem.from_workload(w, precision=prec, n_slices=args.slices)
     stream = torch.cuda.current_stream()
@@ -418,25 +559,45 @@ def main():
     launches0 = L.gn_kernel_launches()
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     infos = []
+    # a working set below the L2 size is flushed between timed steps (outside the events)
+    flush = None
+    if prob.n_rows * (prob.P + 1) * 8 < 512e6:
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        rc, lam, gam, info = prob.gn_step(theta, lam, gam)
-        if rc < 0:
-            raise RuntimeError(f"gn_step failed: {rc}")
-        infos.append(info)
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    if flush is None:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            rc, lam, gam, info = prob.gn_step(theta, lam, gam)
+            if rc < 0:
+                raise RuntimeError(f"gn_step failed: {rc}")
+            infos.append(info)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        launches = L.gn_kernel_launches() - launches0
+    else:
+        per = []
+        launches = 0
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0 = L.gn_kernel_launches()
+            ev0.record(stream)
+            rc, lam, gam, info = prob.gn_step(theta, lam, gam)
+            ev1.record(stream)
+            launches += L.gn_kernel_launches() - l0
+            if rc < 0:
+                raise RuntimeError(f"gn_step failed: {rc}")
+            infos.append(info)
+            torch.cuda.synchronize()
+            per.append(ev0.elapsed_time(ev1))
+        ms = statistics.mean(per)
     clocks = sampler.stop()
-    launches = L.gn_kernel_launches() - launches0
-    ms = ev0.elapsed_time(ev1) / args.steps
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = max_over_ranks(ms, "cuda")
         dist.barrier()
-        ms = float(t.item())
     value = world * 1000.0 / ms
 
     # per-phase device times (library CUDA events on the launch stream, averaged over the timed steps)
@@ -464,9 +625,7 @@ def main():
         torch.cuda.synchronize()
         ms_e2e = e0.elapsed_time(e1) / args.steps
         if world > 1:
-            t = torch.tensor([ms_e2e], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = float(t.item())
+            ms_e2e = max_over_ranks(ms_e2e, "cuda")
         nb = prob.P * 8
         e2e = {"value": world * 1000.0 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": nb,
                "d2h_bytes_per_step": nb + 8,
@@ -475,13 +634,17 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_step_estimate()
+        cpu = oracle_step_estimate(workload=args.workload,
+                                   budget_cols=12 if w.d == 1 else 3,
+                                   gram_cols=512 if w.d == 1 else 256)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": workload_config(w, args.precision, args.slices),
+                "config": dict(workload_config(w, args.precision, args.slices),
+                               **({"l2": "L2 flushed (256 MB write) between timed steps"} if flush is not None
+                                  else {})),
                 "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches),
                 "phase_ms": {"jacobian": phases[0], "gram": phases[1], "factor": phases[3], "solve": phases[4],

@@ -207,6 +207,27 @@ int gn_damped_solve(gn_handle* h, const double* G, const double* g, double* gamm
  * library's choice because the paper gives none. */
 int gn_step(gn_handle* h, double* theta, double* lambda, double* damping, gn_step_info* info);
 
+/* ---- batched fits ---------------------------------------------------------- */
+/* Many independent profile fits of uneven size (lambda seeds, widths, depths,
+ * point counts), as in the paper's sweeps over lambda and seeds (Methods,
+ * "Identifying Admissible lambda Values" and "Validation of lambda").  The
+ * fits share nothing; they are dealt round-robin onto n_streams CUDA streams
+ * created by the batch, and gn_batch_step drives one damped GN step of every
+ * fit with one host worker thread per stream, so their kernels overlap on the
+ * GPU.  problems: host array [n_fits] (point arrays borrowed as in gn_init).
+ * Errors: as gn_init; on failure nothing is left allocated. */
+typedef struct gn_batch gn_batch;
+int gn_batch_init(const gn_problem* problems, int n_fits, int n_streams, gn_batch** out);
+/* The handle of one fit (owned by the batch; valid until gn_batch_destroy). */
+int gn_batch_handle(gn_batch* b, int fit, gn_handle** out);
+/* One gn_step of every fit.  thetas: host array of n_fits device pointers;
+ * lambdas, dampings: host [n_fits] in/out; infos (host [n_fits], may be NULL);
+ * status (host [n_fits], may be NULL) receives each fit's return code.
+ * Returns GN_OK or the most negative error code of any fit.  Synchronises. */
+int gn_batch_step(gn_batch* b, double* const* thetas, double* lambdas, double* dampings, gn_step_info* infos,
+                  int* status);
+int gn_batch_destroy(gn_batch* b);
+
 /* Max |R_k| over the interior points (Methods, "Validation Metrics", max d0
  * residual) at (theta, lambda), unweighted.  *out: host.  Synchronises. */
 int gn_max_residual(gn_handle* h, const double* theta, double lambda, double* out);

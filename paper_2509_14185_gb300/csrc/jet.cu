@@ -507,12 +507,15 @@ cudaError_t launch_eq(const JetArgs& a, cudaStream_t st, int64_t* warps_used) {
   constexpr int CR = JT<D>::CR;
   constexpr int CF = (MODE == MODE_RESIDUAL) ? CR : JT<D>::CF;
   const int64_t per_warp = jet_smem_doubles(a.net, CF, CR, NF) * (int64_t)sizeof(double);
+  constexpr int64_t kSmemCap = 200 * 1024;
   int wpb = 8;
-  while (wpb > 1 && per_warp * wpb > 200 * 1024) wpb--;
-  if (per_warp > 200 * 1024) return cudaErrorInvalidValue;
+  while (wpb > 1 && per_warp * wpb > kSmemCap) wpb--;
+  if (per_warp > kSmemCap) return cudaErrorInvalidValue;
   const size_t smem = (size_t)per_warp * wpb;
+  // the opt-in limit is the same for every launch: handles stepped from several host
+  // threads must not lower it under one another's launches
   cudaError_t err = cudaFuncSetAttribute(jet_kernel<EQ, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+                                         (int)kSmemCap);
   if (err != cudaSuccess) return err;
   int64_t blocks = (a.n + wpb - 1) / wpb;
   const int64_t cap = kJetMaxBlocks;

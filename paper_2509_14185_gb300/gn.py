@@ -93,6 +93,10 @@ EXPORTS = {
     "gn_step": (ctypes.c_int, [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(gn_step_info)]),
     "gn_max_residual": (ctypes.c_int, [_P, _P, _D, ctypes.POINTER(_D)]),
     "gn_jtr_noalloc": (ctypes.c_int, [_P, _I64, _I64, _I64, _P, _P, _P]),
+    "gn_batch_init": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P)]),
+    "gn_batch_handle": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
+    "gn_batch_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "gn_batch_destroy": (ctypes.c_int, [_P]),
     "gn_kernel_launches": (ctypes.c_int64, []),
     "gn_last_error_detail": (ctypes.c_char_p, []),
     "gn_error_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -292,3 +296,75 @@ class ResidualFn(torch.autograd.Function):
 
 def residual_fn(theta, lam, prob):
     return ResidualFn.apply(theta, lam, prob)
+
+
+class GNBatch:
+    """Many independent profile fits stepped together (gn_batch_*): each fit keeps its
+    own libgn handle; fits are spread over `n_streams` CUDA streams."""
+
+    def __init__(self, workloads, n_streams=8, precision=GN_PREC_FP64, n_slices=6, device="cuda"):
+        lib()
+        self.device = torch.device(device)
+        self.keep = []
+        probs = (gn_problem * len(workloads))()
+        for k, w in enumerate(workloads):
+            d = _inputs.EQUATION_DIM[w.equation]
+            y = torch.from_numpy(np.ascontiguousarray(np.asarray(w.y, dtype=np.float64).reshape(d, -1))).to(self.device)
+            yb = None
+            if w.y_bnd.size:
+                yb = torch.from_numpy(np.ascontiguousarray(w.y_bnd)).to(self.device)
+            rho = None if w.rho is None else torch.as_tensor(w.rho, dtype=torch.float64,
+                                                             device=self.device).contiguous()
+            self.keep += [y, yb, rho]
+            p = probs[k]
+            p.equation = w.equation
+            p.n_layers = len(w.widths) - 1
+            for i, wd in enumerate(w.widths):
+                p.widths[i] = int(wd)
+            p.n_pts = y.shape[1]
+            p.y = y.data_ptr()
+            p.rho = None if rho is None else rho.data_ptr()
+            p.n_bnd = 0 if yb is None else yb.shape[1]
+            p.y_bnd = None if yb is None else yb.data_ptr()
+            p.c_bnd = 1.0
+            p.y_norm[0], p.y_norm[1] = float(w.y_norm[0]), float(w.y_norm[1])
+            p.c_norm = float(w.c_norm)
+            p.c_norm_w = 1.0
+            p.hilbert_m = int(w.hilbert_m)
+            p.precision = int(precision)
+            p.n_slices = int(n_slices)
+        self._probs = probs
+        b = ctypes.c_void_p()
+        _check(lib().gn_batch_init(probs, len(workloads), int(n_streams), ctypes.byref(b)), "gn_batch_init")
+        self.b = b
+        self.n = len(workloads)
+        self.P = []
+        for f in range(self.n):
+            h = ctypes.c_void_p()
+            _check(lib().gn_batch_handle(b, f, ctypes.byref(h)), "gn_batch_handle")
+            P = _I64()
+            lib().gn_param_count(h, ctypes.byref(P))
+            self.P.append(P.value)
+
+    def gn_batch_step(self, thetas, lambdas, dampings):
+        """thetas: list of device tensors (updated in place); lambdas, dampings: lists (returned updated)."""
+        ptrs = (ctypes.c_void_p * self.n)(*[t.data_ptr() for t in thetas])
+        lam = (ctypes.c_double * self.n)(*lambdas)
+        gam = (ctypes.c_double * self.n)(*dampings)
+        infos = (gn_step_info * self.n)()
+        st = (ctypes.c_int * self.n)()
+        torch.cuda.synchronize(self.device)     # the batch's streams do not wait on torch's
+        rc = lib().gn_batch_step(self.b, ptrs, lam, gam, infos, st)
+        _check(rc if rc < 0 and rc not in (GN_ERR_NOT_SPD, GN_ERR_NONFINITE) else 0, "gn_batch_step")
+        return list(lam), list(gam), [infos[i].as_dict() for i in range(self.n)], list(st)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().gn_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
