@@ -45,9 +45,11 @@ def parse():
     ap.add_argument("--slices", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--micro", default=None, choices=[None, "gram"],
+    ap.add_argument("--micro", default=None, choices=[None, "gram", "chol"],
                     help="time one kernel family alone instead of the GN step (not the bench contract line)")
-    ap.add_argument("--width", type=int, default=44, help="--micro gram: hidden width w of a 1-w-w-1 CCF net")
+    ap.add_argument("--width", type=int, default=None,
+                    help="--micro: hidden width w of a 1-w-w-1 CCF net (gram: default 44; chol: default the "
+                         "benchmark's 1-64-64-64-1 net)")
     ap.add_argument("--equal-residual", action="store_true",
                     help="FP64 path for --er-steps steps vs split path to the same max residual (own JSON line)")
     ap.add_argument("--er-steps", type=int, default=50)
@@ -134,7 +136,8 @@ def micro_gram(args):
     B.build()
     from paper_2509_14185_gb300 import gn, inputs
     w = inputs.ccf_unstable_1d()
-    w.widths = [1, args.width, args.width, 1]
+    width = args.width or 44
+    w.widths = [1, width, width, 1]
     w.theta = inputs.xavier_init(w.widths, 17)
     prec = {"fp64": gn.GN_PREC_FP64, "split": gn.GN_PREC_SPLIT_BF16, "split_all": gn.GN_PREC_SPLIT_BF16}[args.precision]
     prob = gn.GNProblem.from_workload(w, precision=prec, n_slices=args.slices)
@@ -312,6 +315,51 @@ def oracle_step_estimate(budget_cols=12, chol_n=512, gram_cols=512, workload="cc
     return {"value": 1.0 / total, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
             "seconds_per_step_extrapolated": total, "parts_s": {"jacobian": Pp * t_col, "gram": t_gram,
                                                                   "cholesky": t_chol, "residuals": 2 * t_res}}
+
+
+def micro_chol(args):
+    """Damped Cholesky solve alone on the benchmark's own Gram matrix (CCF 1st unstable,
+    P' = 8514): G from the GPU Jacobian, then gn_damped_solve timed with CUDA events.
+    Prints one JSON line (not the bench contract line)."""
+    import torch
+    from paper_2509_14185_gb300 import build as B
+    B.build()
+    from paper_2509_14185_gb300 import gn, inputs
+    w = inputs.ccf_unstable_1d()
+    if args.width:
+        w.widths = [1, args.width, args.width, 1]
+        w.theta = inputs.xavier_init(w.widths, 17)
+    prec = {"fp64": gn.GN_PREC_FP64, "split": gn.GN_PREC_SPLIT_BF16, "split_all": gn.GN_PREC_SPLIT_ALL}[args.precision]
+    prob = gn.GNProblem.from_workload(w, precision=prec, n_slices=args.slices)
+    Pp = prob.P + 1
+    theta = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
+    J = torch.zeros((prob.n_rows, Pp), dtype=torch.float64, device="cuda")
+    prob.gn_jacobian(theta, w.lam, J)
+    r, _ = prob.residual(theta, w.lam)
+    G = torch.zeros((Pp, Pp), dtype=torch.float64, device="cuda")
+    g = prob.new_vec(Pp)
+    prob.gn_gram(J, prob.n_rows, r, G, g, precision=gn.GN_PREC_FP64)
+    G = torch.tril(G) + torch.tril(G, -1).T
+    del J
+    delta = prob.new_vec(Pp)
+    for _ in range(args.warmup):
+        prob.gn_damped_solve(G, g, w.gamma, delta)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rc, gam, retries = prob.gn_damped_solve(G, g, w.gamma, delta)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    A = G + gam * torch.eye(Pp, dtype=torch.float64, device="cuda")
+    res = float((A @ delta - g).abs().max() / (A.abs().max() * delta.abs().max()))
+    print(json.dumps({"micro": "chol", "precision": args.precision, "n": Pp, "ms_median": statistics.median(times),
+                      "ms_min": min(times), "rc": rc, "retries": retries, "backward_error": res,
+                      "diag_arith": "fp64" if os.environ.get("GN_DIAG_FP64") else "df"}))
+    prob.close()
+    return 0
 
 
 def measured_peak(key, default):
@@ -525,6 +573,8 @@ def main():
         return run_reference(args)
     if args.micro == "gram":
         return micro_gram(args)
+    if args.micro == "chol":
+        return micro_chol(args)
     if args.equal_residual:
         return equal_residual(args)
     if args.workload == "batched":

@@ -3,15 +3,19 @@
 //
 // Blocked right-looking factorisation on a row-major matrix, lower triangle,
 // block size 64:
-//   1. one CTA factors the 64 x 64 diagonal block in shared memory and also
-//      forms its inverse Linv_k (kept for the triangular solves);
-//   2. the panel below it is solved as a GEMM, L21 = A21 Linv_k^T;
+//   1. one CTA factors the 64 x 64 diagonal block in shared memory and forms
+//      its inverse Linv_k in the same sweep (kept for the panel and the
+//      triangular solves);
+//   2. the panel below it is solved on the CUDA cores, L21 = A21 Linv_k^T
+//      (FP64), and on the split path the same kernel writes L21's BF16 slices
+//      for the trailing update;
 //   3. the trailing matrix is updated A22 -= L21 L21^T (lower tiles only).
 // A non-positive pivot sets a device flag; later blocks skip their work and
 // the host escalates the damping.  The triangular solves use the stored
 // diagonal inverses: a tiny 64 x 64 product per block plus a GEMV of the
 // remaining vector spread over all SMs.
 #include <cmath>
+#include <type_traits>
 
 #include "gn_internal.cuh"
 
@@ -20,133 +24,669 @@ namespace {
 
 constexpr int NB = kCholNB;
 
-__global__ void __launch_bounds__(256) potrf_diag_kernel(double* A, int64_t lda, int64_t k0, int kb, double* Linv,
-                                                         int* flag) {
-  // S: the factor in the lower triangle; the inverse's strict lower part is
-  // kept transposed in S's strict upper triangle and its diagonal in xd.
-  __shared__ double S[NB][NB + 1];
-  __shared__ double xd[NB];
-  __shared__ int bad;
+// 2^e (exact) for the exponent range of a scaled block, ldexp outside it
+__device__ __forceinline__ double p2(int e) {
+  return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52) : ldexp(1.0, e);
+}
+__device__ __forceinline__ float p2f(int e) {   // e in [-126, 127]
+  return __int_as_float((e + 127) << 23);
+}
+
+// Arithmetic of the diagonal-block factor.  Arith64 is plain FP64.  ArithDF
+// carries each value as an unevaluated sum of two floats (hi + lo, about 48
+// significant bits) on the FP32 pipe: the sweep is a chain of 64 dependent
+// steps, and GB300's FP64 units are both narrow (about 1/60 of the FP32 rate)
+// and long-latency, so the FP32 pipe runs it several times faster.  Each also
+// provides the scaled load (A - U) 2^k, the scaled store v 2^k and 1/sqrt(d).
+struct Arith64 {
+  using T = double;
+  static __device__ __forceinline__ T one() { return 1.0; }
+  static __device__ __forceinline__ T zero() { return 0.0; }
+  static __device__ __forceinline__ bool positive(T d) { return d > 0.0 && isfinite(d); }
+  static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+  static __device__ __forceinline__ T fnma(T s, T a, T b) { return fma(-a, b, s); }   // s - a b
+  static __device__ __forceinline__ T rcp(T d) { return 1.0 / d; }
+  static __device__ __forceinline__ T rsqrt(T d) { return 1.0 / sqrt(d); }
+  static __device__ __forceinline__ T load_scaled(double a, const float2* u, int k) {
+    if (u) a -= (double)u->x + (double)u->y;
+    return a * p2(k);
+  }
+  static __device__ __forceinline__ double store_scaled(T v, int k) { return v * p2(k); }
+};
+
+struct DF {
+  float h, l;
+};
+
+// a 2^k as a double-float pair, by integer operations on the bits (no FP64
+// arithmetic): the top 24 significand bits form hi exactly, the low 29 bits
+// rounded to 24 form lo.  Returns false (caller falls back) for zero-exponent
+// or non-finite a and for results outside [2^-70, 2^127).
+__device__ __forceinline__ bool df_split_scaled(double a, int k, float& h, float& l) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+  if ((b << 1) == 0ull) {
+    h = l = 0.f;
+    return true;
+  }
+  const int ex = (int)((b >> 52) & 0x7ff);
+  const int e = ex - 1023 + k;
+  if (ex == 0 || ex == 0x7ff || e < -70 || e > 126) return false;
+  const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  h = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | ((unsigned)(mant >> 29) & 0x7fffffu));
+  const float lo = __fmul_rn(__uint2float_rn((unsigned)(mant & ((1u << 29) - 1))), p2f(e - 52));
+  l = sign ? -lo : lo;
+  return true;
+}
+// x 2^k as a double, by integer operations (exact for normal x and a normal result)
+__device__ __forceinline__ double f2d_scaled(float x, int k) {
+  const unsigned b = __float_as_uint(x);
+  const int ex = (int)((b >> 23) & 0xff);
+  if (ex == 0 || ex == 0xff) return (double)x * p2(k);   // zero, subnormal or non-finite: FP64 path
+  const int e = ex - 127 + k + 1023;
+  if (e <= 0 || e >= 2047) return (double)x * p2(k);
+  return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) |
+                                          ((unsigned long long)e << 52) |
+                                          ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
+struct ArithDF {
+  using T = DF;
+  static __device__ __forceinline__ T from(double a) {
+    const float h = __double2float_rn(a);
+    return {h, __double2float_rn(a - (double)h)};
+  }
+  static __device__ __forceinline__ T one() { return {1.f, 0.f}; }
+  static __device__ __forceinline__ T zero() { return {0.f, 0.f}; }
+  static __device__ __forceinline__ bool positive(T d) { return d.h > 0.f && isfinite(d.h); }
+  // a + b (TwoSum of the high parts, low parts added, Fast2Sum renormalisation)
+  static __device__ __forceinline__ T add(T a, T b) {
+    const float s = __fadd_rn(a.h, b.h);
+    const float bb = __fsub_rn(s, a.h);
+    const float err = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+    const float t = __fadd_rn(err, __fadd_rn(a.l, b.l));
+    const float hi = __fadd_rn(s, t);
+    return {hi, __fsub_rn(t, __fsub_rn(hi, s))};
+  }
+  // a b: exact product of the high parts (FMA) plus the cross terms, renormalised (Fast2Sum)
+  static __device__ __forceinline__ T mul(T a, T b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+    const float hi = __fadd_rn(p, e);
+    return {hi, __fsub_rn(e, __fsub_rn(hi, p))};
+  }
+  // s - a b: the product as above, its high part subtracted exactly (TwoSum)
+  static __device__ __forceinline__ T fnma(T s, T a, T b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float pe = __fmaf_rn(a.h, b.h, -p);
+    pe = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, pe));
+    const float d = __fsub_rn(s.h, p);
+    const float bb = __fsub_rn(d, s.h);
+    const float err = __fadd_rn(__fsub_rn(s.h, __fsub_rn(d, bb)), __fsub_rn(-p, bb));
+    const float t = __fadd_rn(err, __fsub_rn(s.l, pe));
+    const float hi = __fadd_rn(d, t);
+    return {hi, __fsub_rn(t, __fsub_rn(hi, d))};
+  }
+  // 1 / d: the FP32 reciprocal r and one Newton correction r (1 - d r) kept as the low part
+  static __device__ __forceinline__ T rcp(T d) {
+    const float r = __frcp_rn(d.h);
+    float e = __fmaf_rn(-d.h, r, 1.0f);
+    e = __fmaf_rn(-d.l, r, e);
+    const float c = __fmul_rn(r, e);
+    const float hi = __fadd_rn(r, c);
+    return {hi, __fsub_rn(c, __fsub_rn(hi, r))};
+  }
+  // 1 / sqrt(d): FP32 estimate, then two Newton steps r += r (1 - d r^2) / 2 in double-float
+  static __device__ __forceinline__ T rsqrt(T d) {
+    T r = {rsqrtf(d.h), 0.f};
+#pragma unroll
+    for (int it = 0; it < 2; it++) {
+      const T e = add(one(), mul({-d.h, -d.l}, mul(r, r)));   // 1 - d r^2
+      r = add(r, mul(r, {0.5f * e.h, 0.5f * e.l}));
+    }
+    return r;
+  }
+  static __device__ __forceinline__ T load_scaled(double a, const float2* u, int k) {
+    float h, l;
+    if (!df_split_scaled(a, k, h, l) || (u && (k < -126 || k > 127))) {
+      if (u) a -= (double)u->x + (double)u->y;   // out of the fast path's range: FP64
+      return from(a * p2(k));
+    }
+    T v = {h, l};
+    if (u) {
+      const float s = p2f(k);   // exact power-of-two scaling of U's pair
+      v = add(v, {-__fmul_rn(u->x, s), -__fmul_rn(u->y, s)});
+    }
+    return v;
+  }
+  static __device__ __forceinline__ double store_scaled(T v, int k) { return f2d_scaled(v.h, k) + f2d_scaled(v.l, k); }
+};
+
+constexpr int kPotrfThreads = 512;
+constexpr size_t kPotrfSmem = (size_t)(NB * (NB + 1) + 4 * NB) * 8;   // final columns + 2 x 2 broadcast rows
+
+// Factor and invert the diagonal block B = A[k0:k0+kb, k0:k0+kb] (minus U, the
+// double-FP32 sum of earlier trailing updates, when U is given).
+//
+// B is first scaled symmetrically by powers of two, B' = D B D with
+// D_ii = 2^-sc[i] and B'_ii in [1, 4), so every value stays O(1) (exact; it
+// also keeps the double-float variant inside FP32's exponent range).  The
+// sweep is the LDL^T form of right-looking elimination: at column j every row
+// i > j applies, with d_j = S[j][j] and a_i = S[i][j] / d_j,
+//     S[i][c] -= a_i S[c][j]    (j < c <= i: the trailing block)
+//     Y[i][c] -= a_i Y[j][c]    (c <= j: the inverse, Y = I at the start)
+// so no value is rescaled inside the chain.  S[i][c] and Y[i][c] share one
+// register: column c of S is final (and published) at step c, exactly when
+// Y[i][c] starts to accumulate.  Thread (i, g) holds row i's elements
+// c = g + 8m (m = 0..7) in registers: eight independent chains per thread.
+// Each step publishes column j of S and row j of Y to shared memory (double
+// buffered, so one barrier per column suffices).  At the end
+// L'[i][j] = S[i][j] / sqrt(d_j) and L'^{-1}[i][c] = Y[i][c] / sqrt(d_i);
+// undoing D gives L = D^-1 L' and Linv = L'^{-1} D, written in FP64.
+template <class AR>
+__global__ void __launch_bounds__(kPotrfThreads) potrf_inv_kernel(double* A, int64_t lda, int64_t k0, int kb,
+                                                                  const float2* __restrict__ U, int64_t ldu,
+                                                                  double* Linv, float2* LinvDF, int* scOut,
+                                                                  const double* fw, double* fy, float2* fyDF,
+                                                                  int* flag) {
+  using T = typename AR::T;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T (*Lf)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw);   // unscaled final columns S[i][j], i >= j
+  T* colbuf = reinterpret_cast<T*>(smraw) + NB * (NB + 1);     // [2][NB]: column j of S
+  T* rowbuf = colbuf + 2 * NB;                                 // [2][NB]: row j of Y; reused for 1/sqrt(d)
+  __shared__ int sc[NB];
   if (*flag) return;
-  const int t = threadIdx.x;
-  if (t == 0) bad = 0;
-  for (int idx = t; idx < NB * NB; idx += blockDim.x) {
-    const int i = idx / NB, j = idx % NB;
-    S[i][j] = (i < kb && j < kb && j <= i) ? A[(k0 + i) * lda + k0 + j] : 0.0;
+  const int t = threadIdx.x, i = t >> 3, g = t & 7;
+  if (t < NB) {
+    int e = 0;
+    if (t < kb) {
+      double d = A[(k0 + t) * lda + k0 + t];
+      if (U) {
+        const float2 u = U[(k0 + t) * ldu + k0 + t];
+        d -= (double)u.x + (double)u.y;
+      }
+      if (d > 0.0 && isfinite(d)) e = ilogb(d) >> 1;   // floor(log2(d) / 2)
+    }
+    sc[t] = e;
   }
   __syncthreads();
-  __shared__ double rinv;
+  T X[8];
+#pragma unroll
+  for (int m = 0; m < 8; m++) {
+    const int c = g + 8 * m;
+    X[m] = AR::zero();
+    if (i < kb && c <= i) {
+      float2 u;
+      if (U) u = U[(k0 + i) * ldu + k0 + c];
+      X[m] = AR::load_scaled(A[(k0 + i) * lda + k0 + c], U ? &u : nullptr, -(sc[i] + sc[c]));
+    }
+  }
+  bool bad = false;
   for (int j = 0; j < kb; j++) {
-    if (t == 0) {
-      const double d = S[j][j];
-      if (!(d > 0.0) || !isfinite(d)) bad = 1;
-      const double piv = sqrt(d);
-      S[j][j] = piv;
-      rinv = 1.0 / piv;   // one division per column; the column is scaled by multiplication
+    T* cb = colbuf + (j & 1) * NB;
+    T* rb = rowbuf + (j & 1) * NB;
+    if (i < kb) {
+      if (g == (j & 7) && i >= j) {
+        // the owner of column j: constant register indices only (no indexed registers)
+        T v;
+        switch (j >> 3) {
+          case 0: v = X[0]; X[0] = AR::zero(); break;
+          case 1: v = X[1]; X[1] = AR::zero(); break;
+          case 2: v = X[2]; X[2] = AR::zero(); break;
+          case 3: v = X[3]; X[3] = AR::zero(); break;
+          case 4: v = X[4]; X[4] = AR::zero(); break;
+          case 5: v = X[5]; X[5] = AR::zero(); break;
+          case 6: v = X[6]; X[6] = AR::zero(); break;
+          default: v = X[7]; X[7] = AR::zero(); break;
+        }
+        // from here on the register accumulates Y[i][j] (0 below the diagonal of I)
+        cb[i] = v;
+        Lf[i][j] = v;
+      }
+      if (i == j) {
+#pragma unroll
+        for (int m = 0; m < 8; m++)
+          if (g + 8 * m < j) rb[g + 8 * m] = X[m];
+      }
     }
     __syncthreads();
-    if (bad) break;
-    const double r = rinv;
-    for (int i = j + 1 + t; i < kb; i += blockDim.x) S[i][j] *= r;
-    __syncthreads();
-    // trailing update of the lower triangle of the diagonal block (lower pairs only)
-    const int rem = kb - j - 1;
-    const int npair = rem * (rem + 1) / 2;
-    for (int idx = t; idx < npair; idx += blockDim.x) {
-      // idx -> (a, b) with 0 <= b <= a < rem, row-major over the lower triangle
-      int a = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
-      while ((a + 1) * (a + 2) / 2 <= idx) a++;
-      while (a * (a + 1) / 2 > idx) a--;
-      const int b = idx - a * (a + 1) / 2;
-      const int i = j + 1 + a, c = j + 1 + b;
-      S[i][c] = fma(-S[i][j], S[c][j], S[i][c]);
+    const T d = cb[j];
+    if (!AR::positive(d)) {   // every thread reads the same pivot: the exit is uniform
+      bad = true;
+      break;
     }
-    __syncthreads();
+    if (i > j && i < kb) {
+      const T a = AR::mul(cb[i], AR::rcp(d));
+      const int mmax = (i - g) >> 3;   // columns c = g + 8m <= i (floor division: none when i < g)
+#pragma unroll
+      for (int m = 0; m < 8; m++) {
+        if (m > mmax) break;
+        const int c = g + 8 * m;
+        // trailing: S[c][j] (column j); inverse: Y[j][c] (row j), with Y[j][j] = 1
+        const T* src = (c > j) ? &cb[c] : &rb[c];
+        const T v = (c == j) ? AR::one() : *src;
+        X[m] = AR::fnma(X[m], a, v);
+      }
+    }
   }
   if (bad) {
     if (t == 0) atomicExch(flag, 1);
     return;
   }
-  // inverse of the lower-triangular factor:
-  // X[c][c] = 1/L[c][c], X[i][c] = -(sum_{q=c}^{i-1} L[i][q] X[q][c]) / L[i][i].
-  // Dependent FP64 operations are slow on this part, so each column's dot
-  // products are split over 4 threads (lanes 4c .. 4c+3 of one warp) and the
-  // reciprocals of the pivots are formed once, in parallel.
-  if (t < kb) xd[t] = 1.0 / S[t][t];
   __syncthreads();
-  {
-    const int c = t >> 2, part = t & 3;
-    for (int i = 1; i < NB; i++) {   // uniform trip count: the shuffles need the whole warp
-      const bool act = (c < kb && i < kb && i > c);
-      double s = 0.0;
-      if (act) {
-        if (part == 0) s = S[i][c] * xd[c];
-        for (int q = c + 1 + part; q < i; q += 4) s = fma(S[i][q], S[c][q], s);
-      }
-      s += __shfl_xor_sync(0xffffffffu, s, 1);
-      s += __shfl_xor_sync(0xffffffffu, s, 2);
-      if (act && part == 0) S[c][i] = -s * xd[i];
-      __syncwarp();
-    }
-  }
+  T* rs = rowbuf;   // 1/sqrt(d_j)
+  if (t < kb) rs[t] = AR::rsqrt(Lf[t][t]);
   __syncthreads();
   double* Lk = Linv + (k0 / NB) * NB * NB;
-  for (int idx = t; idx < NB * NB; idx += blockDim.x) {
-    const int i = idx / NB, j = idx % NB;
-    if (i < kb && j < kb && j <= i) A[(k0 + i) * lda + k0 + j] = S[i][j];
-    double x = 0.0;
-    if (i < kb && j < kb) x = (i == j) ? xd[i] : (i > j ? S[j][i] : 0.0);
-    Lk[idx] = x;
-  }
-}
-
-// A[i][j] -= U[i][j] (double-FP32 -> FP64) for the panel columns j in [k0, k0+kb), rows i >= j
-__global__ void panel_fix_kernel(double* A, int64_t lda, const float2* __restrict__ U, int64_t ldu, int64_t k0,
-                                 int kb, int64_t n) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t i = k0 + idx / kb, j = k0 + idx % kb;
-  if (i >= n || j > i) return;
-  const float2 u = U[i * ldu + j];
-  A[i * lda + j] -= (double)u.x + (double)u.y;
-}
-
-// x_k = Linv_k v_k (trans = 0) or Linv_k^T v_k (trans = 1), in place on v[k0 .. k0+kb)
-__global__ void tri_block_kernel(const double* __restrict__ Lk, double* v, int64_t k0, int kb, int trans) {
-  __shared__ double s[NB];
-  const int i = threadIdx.x;
-  if (i < kb) s[i] = v[k0 + i];
-  __syncthreads();
-  if (i < kb) {
-    double acc = 0.0;
-    if (!trans) {
-      for (int q = 0; q <= i; q++) acc = fma(Lk[i * NB + q], s[q], acc);
-    } else {
-      for (int q = i; q < kb; q++) acc = fma(Lk[q * NB + i], s[q], acc);
-    }
-    v[k0 + i] = acc;
-  }
-}
-
-// forward update: v[k1 + r] -= sum_t L[k1 + r][k0 + t] v[k0 + t], one warp per row
-__global__ void fwd_update_kernel(const double* __restrict__ L, int64_t lda, double* v, int64_t k0, int kb,
-                                  int64_t k1, int64_t n) {
-  const int64_t row = k1 + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= n) return;
-  double acc = 0.0;
-  for (int q = lane; q < kb; q += 32) acc = fma(L[row * lda + k0 + q], v[k0 + q], acc);
+  float2* Lf2 = LinvDF ? LinvDF + (k0 / NB) * NB * NB : nullptr;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if (lane == 0) v[row] -= acc;
+  for (int m = 0; m < 8; m++) {
+    const int c = g + 8 * m;
+    T v = AR::zero();
+    if (i < kb && c <= i) v = (c == i) ? rs[i] : AR::mul(X[m], rs[i]);   // L'^{-1}[i][c] = Y[i][c] / sqrt(d_i)
+    Lk[i * NB + c] = (i < kb && c <= i) ? AR::store_scaled(v, -sc[c]) : 0.0;
+    if constexpr (std::is_same<T, DF>::value) {
+      if (Lf2) Lf2[i * NB + c] = make_float2(v.h, v.l);   // for the double-float panel solve (without D)
+    }
+  }
+  if (Lf2 && t < NB) scOut[(k0 / NB) * NB + t] = sc[t];
+  if constexpr (std::is_same<T, DF>::value) {
+    // forward substitution, block k: y_k = Linv_k w_k = L'^{-1} (D w_k); thread (i, g) sums its
+    // eight columns, the eight threads of row i combine their sums (lanes 8(i mod 4) .. +7)
+    if (fw) {
+      T acc = AR::zero();
+#pragma unroll
+      for (int m = 0; m < 8; m++) {
+        const int c = g + 8 * m;
+        if (i < kb && c <= i) {
+          const T v = (c == i) ? rs[i] : AR::mul(X[m], rs[i]);
+          acc = AR::add(acc, AR::mul(v, AR::load_scaled(fw[k0 + c], nullptr, -sc[c])));
+        }
+      }
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        const T other = {__shfl_xor_sync(0xffffffffu, acc.h, o), __shfl_xor_sync(0xffffffffu, acc.l, o)};
+        acc = AR::add(acc, other);
+      }
+      if (g == 0 && i < kb) {
+        fy[k0 + i] = AR::store_scaled(acc, 0);
+        fyDF[i] = make_float2(acc.h, acc.l);
+      }
+    }
+  }
+  for (int idx = t; idx < NB * NB; idx += blockDim.x) {
+    const int r = idx / NB, c = idx % NB;
+    if (r < kb && c <= r) A[(k0 + r) * lda + k0 + c] = AR::store_scaled(AR::mul(Lf[r][c], rs[c]), sc[r]);
+  }
 }
 
-// backward update: v[j] -= sum_t L[k0 + t][j] v[k0 + t] for j < k0 (coalesced over j)
-__global__ void bwd_update_kernel(const double* __restrict__ L, int64_t lda, double* v, int64_t k0, int kb) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= k0) return;
+// Panel solve L21 = A21 Linv_k^T in FP64 on the CUDA cores (the FP64 path), in
+// place, for the rows [k1, n) of the panel columns [k0, k0 + kb).  32 rows per
+// CTA, 128 threads, 4 x 4 outputs per thread (rows ty + 8a, columns tx + 16b);
+// Linv_k is lower triangular, so the K loop runs in four 16-wide segments and
+// segment s only feeds the columns b >= s.
+constexpr int kPanelRows = 32;
+constexpr size_t kPanelSmem = (size_t)(kPanelRows + NB) * (NB + 1) * 8;
+
+__global__ void __launch_bounds__(128) panel_solve_kernel(double* A, int64_t lda, int64_t k0, int kb, int64_t k1,
+                                                          int64_t n, const double* __restrict__ Lk, const int* flag) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double (*As)[NB + 1] = reinterpret_cast<double (*)[NB + 1]>(smraw);
+  double (*Lt)[NB + 1] = As + kPanelRows;   // Lt[q][j] = Linv_k[j][q]
+  if (*flag) return;
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int64_t rb = k1 + (int64_t)blockIdx.x * kPanelRows;   // first row of this CTA
+  for (int idx = t; idx < NB * NB; idx += blockDim.x) {
+    const int j = idx / NB, q = idx % NB;
+    Lt[q][j] = (j < kb && q < kb) ? Lk[j * NB + q] : 0.0;
+  }
+  for (int idx = t; idx < kPanelRows * NB; idx += blockDim.x) {
+    const int rr = idx / NB, q = idx % NB;
+    const int64_t r = rb + rr;
+    As[rr][q] = (r < n && q < kb) ? A[r * lda + k0 + q] : 0.0;
+  }
+  __syncthreads();
+  double acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int b = 0; b < 4; b++) acc[a][b] = 0.0;
+#pragma unroll
+  for (int seg = 0; seg < 4; seg++) {
+#pragma unroll 4
+    for (int tt = 0; tt < 16; tt++) {
+      const int q = 16 * seg + tt;
+      double av[4], lv[4];
+#pragma unroll
+      for (int a = 0; a < 4; a++) av[a] = As[ty + 8 * a][q];
+#pragma unroll
+      for (int b = seg; b < 4; b++) lv[b] = Lt[q][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = seg; b < 4; b++) acc[a][b] = fma(av[a], lv[b], acc[a][b]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    const int64_t r = rb + ty + 8 * a;
+    if (r >= n) continue;
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+      const int j = tx + 16 * b;
+      if (j >= kb) continue;
+      A[r * lda + k0 + j] = acc[a][b];
+    }
+  }
+}
+
+// The split path's panel solve in double-float arithmetic on the FP32 pipe
+// (about 48 significant bits, the precision of U and of the split GEMM):
+// L21 = (A21 - U21) D L'^{-T}, with L'^{-1} (LkDF) and the power-of-two scales
+// D = diag(2^-sc) from the diagonal factor.  Same tiling as the FP64 kernel;
+// each product is the exact FP32 product of the high parts plus the cross
+// terms, its high part added exactly (TwoSum) and the low parts accumulated
+// in FP32, renormalised at the end.  Writes L21 in FP64 and its S BF16 slices
+// into the strip operand (row r at r - row_base, columns kofs + j, exponent ex[r]).
+constexpr size_t kPanelDFSmem = (size_t)(kPanelRows + NB) * (NB + 1) * sizeof(float2);
+
+template <int S>
+__global__ void __launch_bounds__(128) panel_df_kernel(double* A, int64_t lda, int64_t k0, int kb, int64_t k1,
+                                                       int64_t n, const float2* __restrict__ U, int64_t ldu,
+                                                       const float2* __restrict__ LkDF, const int* __restrict__ sck,
+                                                       __nv_bfloat16* slices, const int* __restrict__ ex,
+                                                       int64_t row_base, int64_t npad, int64_t kpad, int kofs,
+                                                       const float2* __restrict__ fyDF, double* fw, const int* flag) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2 (*As)[NB + 1] = reinterpret_cast<float2 (*)[NB + 1]>(smraw);
+  float2 (*Lt)[NB + 1] = As + kPanelRows;   // Lt[q][j] = L'^{-1}[j][q]
+  __shared__ float colscale[NB];   // 2^-sc[q]; 0 marks a scale outside FP32's range
+  if (*flag) return;
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int64_t rb = k1 + (int64_t)blockIdx.x * kPanelRows;
+  if (t < NB) colscale[t] = (t < kb && sck[t] >= -120 && sck[t] <= 120) ? ldexpf(1.0f, -sck[t]) : 0.0f;
+  for (int idx = t; idx < NB * NB; idx += blockDim.x) {
+    const int j = idx / NB, q = idx % NB;
+    Lt[q][j] = (j < kb && q < kb) ? LkDF[j * NB + q] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  for (int idx = t; idx < kPanelRows * NB; idx += blockDim.x) {
+    const int rr = idx / NB, q = idx % NB;
+    const int64_t r = rb + rr;
+    float h = 0.f, l = 0.f;
+    if (r < n && q < kb && colscale[q] == 0.0f) {   // extreme scale: subtract and scale in FP64
+      double a = A[r * lda + k0 + q];
+      if (U) {
+        const float2 u = U[r * ldu + k0 + q];
+        a -= (double)u.x + (double)u.y;
+      }
+      a *= p2(-sck[q]);
+      h = __double2float_rn(a);
+      l = __double2float_rn(a - (double)h);
+    } else if (r < n && q < kb) {
+      const double a = A[r * lda + k0 + q];
+      h = __double2float_rn(a);
+      l = __double2float_rn(a - (double)h);
+      if (U) {   // (h, l) -= (u.x, u.y): TwoSum of the high parts, low parts added
+        const float2 u = U[r * ldu + k0 + q];
+        const float s1 = __fsub_rn(h, u.x);
+        const float bb = __fsub_rn(s1, h);
+        const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s1, bb)), __fsub_rn(-u.x, bb));
+        const float tl = __fadd_rn(err, __fsub_rn(l, u.y));
+        h = __fadd_rn(s1, tl);
+        l = __fsub_rn(tl, __fsub_rn(h, s1));
+      }
+      const float sc = colscale[q];   // exact power of two
+      h = __fmul_rn(h, sc);
+      l = __fmul_rn(l, sc);
+    }
+    As[rr][q] = make_float2(h, l);
+  }
+  __syncthreads();
+  float ah[4][4], al[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int b = 0; b < 4; b++) ah[a][b] = al[a][b] = 0.f;
+#pragma unroll
+  for (int seg = 0; seg < 4; seg++) {
+#pragma unroll 2
+    for (int tt = 0; tt < 16; tt++) {
+      const int q = 16 * seg + tt;
+      float2 av[4], lv[4];
+#pragma unroll
+      for (int a = 0; a < 4; a++) av[a] = As[ty + 8 * a][q];
+#pragma unroll
+      for (int b = seg; b < 4; b++) lv[b] = Lt[q][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = seg; b < 4; b++) {
+          const float p = __fmul_rn(av[a].x, lv[b].x);
+          float pe = __fmaf_rn(av[a].x, lv[b].x, -p);
+          pe = __fmaf_rn(av[a].x, lv[b].y, __fmaf_rn(av[a].y, lv[b].x, pe));
+          const float s1 = __fadd_rn(ah[a][b], p);
+          const float bb = __fsub_rn(s1, ah[a][b]);
+          const float err = __fadd_rn(__fsub_rn(ah[a][b], __fsub_rn(s1, bb)), __fsub_rn(p, bb));
+          ah[a][b] = s1;
+          al[a][b] = __fadd_rn(al[a][b], __fadd_rn(pe, err));
+        }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; a++)
+#pragma unroll
+    for (int b = 0; b < 4; b++) {   // renormalise (Fast2Sum)
+      const float hi = __fadd_rn(ah[a][b], al[a][b]);
+      al[a][b] = __fsub_rn(al[a][b], __fsub_rn(hi, ah[a][b]));
+      ah[a][b] = hi;
+    }
+  if (fw) {
+    // forward substitution: w[r] -= L21[r][:] y_k, the 16 lanes of a row (a half warp) combining
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+      DF acc = {0.f, 0.f};
+#pragma unroll
+      for (int b = 0; b < 4; b++) {
+        const int j = tx + 16 * b;
+        if (j < kb) {
+          const float2 yv = fyDF[j];
+          acc = ArithDF::add(acc, ArithDF::mul({ah[a][b], al[a][b]}, {yv.x, yv.y}));
+        }
+      }
+#pragma unroll
+      for (int o = 1; o < 16; o <<= 1) {
+        const DF other = {__shfl_xor_sync(0xffffffffu, acc.h, o), __shfl_xor_sync(0xffffffffu, acc.l, o)};
+        acc = ArithDF::add(acc, other);
+      }
+      const int64_t r = rb + ty + 8 * a;
+      if (tx == 0 && r < n) fw[r] = (fw[r] - (double)acc.h) - (double)acc.l;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; a++) {
+    const int64_t r = rb + ty + 8 * a;
+    if (r >= n) continue;
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+      const int j = tx + 16 * b;
+      if (j >= kb) continue;
+      const double x = (double)ah[a][b] + (double)al[a][b];
+      A[r * lda + k0 + j] = x;
+      oz_digits<S>(x, ex[r], slices + (r - row_base) * kpad + kofs + j, npad * kpad);
+    }
+  }
+}
+
+// Row exponents of one strip of the split factor.  When the columns before s0
+// are eliminated, the rest of row r of L has squared norm equal to the Schur
+// complement's diagonal, S_rr = A[r][r] - U[r][r], so sqrt(S_rr) bounds every
+// entry of row r in this strip and in later ones.  U carries ~2^-46 relative
+// precision, so S_rr is taken with a floor of 2^-44 A[r][r] (a bound that still
+// holds when the computed difference is only rounding noise), and
+// ex[r] = floor((ilogb(S) + 3) / 2) makes 2^ex[r] exceed sqrt(S) by at least
+// sqrt(2) (a margin for rounding in the computed factor).  Rows >= n get 0.
+__global__ void strip_exponent_kernel(const double* __restrict__ A, int64_t lda, const float2* __restrict__ U,
+                                      int64_t ldu, int64_t s0, int64_t n, int64_t total, int* ex) {
+  const int64_t r = s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= total) return;
+  int e = 0;
+  if (r < n) {
+    const double a = A[r * lda + r];
+    double d = a;
+    if (U) {
+      const float2 u = U[r * ldu + r];
+      d -= (double)u.x + (double)u.y;
+    }
+    const double m2 = fmax(d, 0.0) + ldexp(fabs(a), -44);
+    if (m2 > 0.0 && isfinite(m2)) e = (ilogb(m2) + 3) >> 1;
+  }
+  ex[r] = e;
+}
+
+// Blocked triangular solves with the stored diagonal inverses.  One launch per
+// block: every CTA forms z = Linv_k w_k (or Linv_k^T w_k) itself from the 64
+// values of w it reads (2080 FMAs, cheaper than a second launch), CTA 0 stores
+// z, and all CTAs apply it to their rows of the remaining vector.  w is the
+// work vector; z goes to a separate output, so no CTA overwrites values
+// another CTA of the same launch still reads.
+constexpr int kSolveThreads = 256;
+
+__device__ __forceinline__ void block_tri(const double* __restrict__ Lk, const double* __restrict__ wk, int kb,
+                                          int trans, double (*Ls)[NB + 1], double* ws, double* zs) {
+  const int t = threadIdx.x;
+  // stage Linv_k in shared memory: 16 independent loads per thread, all in flight together
+#pragma unroll
+  for (int m = 0; m < NB * NB / kSolveThreads; m++) {
+    const int idx = t + m * kSolveThreads;
+    Ls[idx / NB][idx % NB] = Lk[idx];
+  }
+  if (t < NB) ws[t] = (t < kb) ? wk[t] : 0.0;
+  __syncthreads();
+  const int i = t >> 2, part = t & 3;   // 4 threads per output row
   double acc = 0.0;
-  for (int q = 0; q < kb; q++) acc = fma(L[(k0 + q) * lda + j], v[k0 + q], acc);
-  v[j] -= acc;
+  if (i < kb) {
+    if (!trans) {
+      for (int q = part; q <= i; q += 4) acc = fma(Ls[i][q], ws[q], acc);
+    } else {
+      for (int q = i + part; q < kb; q += 4) acc = fma(Ls[q][i], ws[q], acc);
+    }
+  }
+  acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+  acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+  if (part == 0) zs[i] = acc;
+  __syncthreads();
+}
+
+// forward block k: y_k = Linv_k w_k; w[r] -= sum_t L[r][k0 + t] y_k[t] for rows r >= k1 (one warp per row)
+__global__ void __launch_bounds__(kSolveThreads) fwd_step_kernel(const double* __restrict__ L, int64_t lda,
+                                                                 const double* __restrict__ Lk, double* w,
+                                                                 double* y, int64_t k0, int kb, int64_t n) {
+  __shared__ double Ls[NB][NB + 1], ws[NB], zs[NB];
+  block_tri(Lk, w + k0, kb, 0, Ls, ws, zs);
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  if (blockIdx.x == 0 && t < kb) y[k0 + t] = zs[t];
+  const int64_t k1 = k0 + kb;
+  for (int64_t row = k1 + (int64_t)blockIdx.x * 8 + warp; row < n; row += (int64_t)gridDim.x * 8) {
+    double acc = 0.0;
+    for (int q = lane; q < kb; q += 32) acc = fma(L[row * lda + k0 + q], zs[q], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) w[row] -= acc;
+  }
+}
+
+// backward block k: x_k = Linv_k^T w_k; w[j] -= sum_t L[k0 + t][j] x_k[t] for j < k0.
+// 64 values of j per CTA, 4 threads per j (16 t each, coalesced over j), partial
+// sums combined in shared memory: FP64 work is spread over many SMs.
+__global__ void __launch_bounds__(kSolveThreads) bwd_step_kernel(const double* __restrict__ L, int64_t lda,
+                                                                 const double* __restrict__ Lk, double* w,
+                                                                 double* x, int64_t k0, int kb) {
+  __shared__ double Ls[NB][NB + 1], ws[NB], zs[NB];
+  __shared__ double part[4][NB];
+  block_tri(Lk, w + k0, kb, 1, Ls, ws, zs);
+  const int t = threadIdx.x;
+  if (blockIdx.x == 0 && t < kb) x[k0 + t] = zs[t];
+  const int jj = t & (NB - 1), qp = t >> 6;
+  const int64_t j = (int64_t)blockIdx.x * NB + jj;
+  double acc0 = 0.0, acc1 = 0.0;
+  if (j < k0) {
+#pragma unroll
+    for (int u = 0; u < 16; u += 2) {
+      const int q0 = qp * 16 + u, q1 = q0 + 1;
+      if (q0 < kb) acc0 = fma(L[(k0 + q0) * lda + j], zs[q0], acc0);
+      if (q1 < kb) acc1 = fma(L[(k0 + q1) * lda + j], zs[q1], acc1);
+    }
+  }
+  part[qp][jj] = acc0 + acc1;
+  __syncthreads();
+  if (t < NB && j < k0) w[j] -= (part[0][jj] + part[1][jj]) + (part[2][jj] + part[3][jj]);
+}
+
+}  // namespace
+
+namespace {
+
+template <class AR>
+cudaError_t launch_potrf(double* A, int64_t lda, int64_t k0, int kb, const float2* U, int64_t ldu, double* Linv,
+                         float2* LinvDF, int* scOut, const double* fw, double* fy, float2* fyDF, int* flag,
+                         cudaStream_t st) {
+  static_assert(kPotrfSmem <= 48 * 1024, "the diagonal factor's shared memory needs no opt-in");
+  potrf_inv_kernel<AR><<<1, kPotrfThreads, kPotrfSmem, st>>>(A, lda, k0, kb, U, ldu, Linv, LinvDF, scOut, fw, fy,
+                                                              fyDF, flag);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_panel(double* A, int64_t lda, int64_t k0, int kb, int64_t k1, int64_t n, const double* Lk,
+                         const int* flag, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(panel_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kPanelSmem);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = (n - k1 + kPanelRows - 1) / kPanelRows;
+  if (blocks <= 0) return cudaSuccess;
+  panel_solve_kernel<<<(unsigned)blocks, 128, kPanelSmem, st>>>(A, lda, k0, kb, k1, n, Lk, flag);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t launch_panel_df(double* A, int64_t lda, int64_t k0, int kb, int64_t k1, int64_t n, const float2* U,
+                            int64_t ldu, const float2* LkDF, const int* sck, const OzOperand& op, const int* ex,
+                            int64_t row_base, int kofs, const float2* fyDF, double* fw, const int* flag,
+                            cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(panel_df_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kPanelDFSmem);
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = (n - k1 + kPanelRows - 1) / kPanelRows;
+  if (blocks <= 0) return cudaSuccess;
+  panel_df_kernel<S><<<(unsigned)blocks, 128, kPanelDFSmem, st>>>(A, lda, k0, kb, k1, n, U, ldu, LkDF, sck,
+                                                                  static_cast<__nv_bfloat16*>(op.slices), ex,
+                                                                  row_base, op.npad, op.kpad, kofs, fyDF, fw,
+                                                                  flag);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_panel_split(int S, double* A, int64_t lda, int64_t k0, int kb, int64_t k1, int64_t n,
+                               const float2* U, int64_t ldu, const float2* LkDF, const int* sck, const OzOperand& op,
+                               const int* ex, int64_t row_base, int kofs, const float2* fyDF, double* fw,
+                               const int* flag, cudaStream_t st) {
+  switch (S) {
+#define GN_PANEL_CASE(s)                                                                                   \
+  case s:                                                                                                  \
+    return launch_panel_df<s>(A, lda, k0, kb, k1, n, U, ldu, LkDF, sck, op, ex, row_base, kofs, fyDF, fw, \
+                              flag, st);
+    GN_PANEL_CASE(1)
+    GN_PANEL_CASE(2)
+    GN_PANEL_CASE(3)
+    GN_PANEL_CASE(4)
+    GN_PANEL_CASE(5)
+    GN_PANEL_CASE(6)
+#undef GN_PANEL_CASE
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace
@@ -155,16 +695,14 @@ cudaError_t cholesky_factor(double* A, int64_t n, int64_t lda, double* Linv, int
   cudaError_t err = cudaSuccess;
   for (int64_t k0 = 0; k0 < n; k0 += NB) {
     const int kb = (int)((n - k0) < NB ? (n - k0) : NB);
-    potrf_diag_kernel<<<1, 256, 0, st>>>(A, lda, k0, kb, Linv, flag);
-    count_launch();
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if ((err = launch_potrf<Arith64>(A, lda, k0, kb, nullptr, 0, Linv, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                     flag, st)) != cudaSuccess)
+      return err;
     const int64_t k1 = k0 + kb;
     if (k1 >= n) break;
     const double* Lk = Linv + (k0 / NB) * NB * NB;
-    // panel: A21 <- A21 Linv_k^T   (C(i,j) = sum_t A21[i][t] Linv_k[j][t])
-    err = dgemm(n - k1, kb, kb, 1.0, A + k1 * lda + k0, lda, true, Lk, NB, true, 0.0, A + k1 * lda + k0, lda,
-                false, nullptr, st);
-    if (err != cudaSuccess) return err;
+    // panel: A21 <- A21 Linv_k^T
+    if ((err = launch_panel(A, lda, k0, kb, k1, n, Lk, flag, st)) != cudaSuccess) return err;
     // trailing: A22 -= L21 L21^T (lower)
     err = dgemm(n - k1, n - k1, kb, -1.0, A + k1 * lda + k0, lda, true, A + k1 * lda + k0, lda, true, 1.0,
                 A + k1 * lda + k1, lda, true, nullptr, st);
@@ -173,91 +711,157 @@ cudaError_t cholesky_factor(double* A, int64_t n, int64_t lda, double* Linv, int
   return cudaSuccess;
 }
 
-// Same blocked factorisation with the trailing update A22 -= L21 L21^T on the
-// tensor cores (split GEMM, S slices): the diagonal blocks and the panel solve
-// stay FP64; the bulk (P'^3/3 of the work) becomes BF16 slice products with
-// exact level accumulation.  *rc_out receives a GN_ERR_* code on failure.
+// Same blocked factorisation with the trailing updates on the tensor cores
+// (split GEMM, S slices).  U, the double-FP32 sum of all updates so far
+// (n x n float2), is accumulated on the FP32 pipe by the split GEMM's
+// epilogue; the diagonal factor and the panel solve subtract it from the 64
+// columns they read, so the FP64 work of the updates drops from O(n^3/64) to
+// O(n^2).
+//
+// Two-level blocking: the 64-wide panels are grouped in strips of kStrip = 256
+// columns, and the bulk update of the trailing matrix runs once per strip (one
+// split GEMM with K = 256), not once per panel: a quarter of the passes over U.
+// Inside the strip, each panel's own 64 columns first get the updates of the
+// strip's earlier panels (a 64-column split GEMM over the K columns already
+// written).  For those in-strip updates every row carries one exponent ex[r],
+// fixed at the strip's start from the Schur complement's diagonal
+// (strip_exponent_kernel), so the panels write their slices side by side into
+// one strip operand as they are solved.
+//
+// The diagonal blocks and the panels are computed in double-float arithmetic
+// (about 48 significant bits, the precision U and the split GEMM carry).
+// With a right-hand side b, the forward substitution L y = b rides along: the
+// diagonal factor forms y_k = Linv_k w_k and the panel kernel applies it to
+// the rows below (w: n doubles of work space, y: n doubles out).
+// *rc_out receives a GN_ERR_* code on failure.
+constexpr int64_t kStrip = 4 * NB;
+
 cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t lda, double* Linv, int* flag, int S,
-                                  int* rc_out) {
-  // Workspace: the L21 operand, the Linv operand, and U, the double-FP32 sum of
-  // all trailing updates L21 L21^T so far (n x n float2).  U is accumulated on
-  // the FP32 pipe by the split GEMM's epilogue; only the 64 columns about to be
-  // factored are converted and applied in FP64 (panel_fix), so the FP64 work of
-  // the trailing updates drops from O(n^3/64) to O(n^2).
+                                  const double* b, double* y, double* w, int* rc_out) {
   cudaStream_t st = h->st;
   *rc_out = GN_OK;
-  const size_t opb = oz_operand_bytes(S, n, NB), opi = oz_operand_bytes(S, NB, NB);
-  const size_t ub = ((size_t)n * n * sizeof(float2) + 255) / 256 * 256;
-  int rc = ensure_split_ws(h, ub + opb + opi + 1024);
+  auto rup = [](int64_t v, int64_t m) { return (v + m - 1) / m * m; };
+  const int64_t npad0 = rup(n, 128);
+  const size_t ub = rup((int64_t)n * n * sizeof(float2), 256);
+  const size_t sb = rup((int64_t)S * npad0 * kStrip * 2, 256);
+  const int64_t ne = npad0 + 1024;   // exponent rows, zero padded past n
+  const size_t bb = oz_operand_bytes(S, n, kStrip);
+  const size_t eb = rup(ne * sizeof(int), 256);
+  const int64_t nblk = (n + NB - 1) / NB;
+  const size_t lb = rup(nblk * NB * NB * sizeof(float2), 256);
+  const size_t cb = rup(nblk * NB * sizeof(int), 256);
+  const size_t yb = rup(NB * sizeof(float2), 256);
+  int rc = ensure_split_ws(h, ub + sb + eb + bb + lb + cb + yb + 256);
   if (rc) {
     *rc_out = rc;
     return cudaErrorMemoryAllocation;
   }
   unsigned char* base = static_cast<unsigned char*>(h->split_ws);
   float2* U = reinterpret_cast<float2*>(base);
+  void* strip_slices = base + ub;
+  int* ex = reinterpret_cast<int*>(base + ub + sb);
+  unsigned char* bulk_base = base + ub + sb + eb;
+  float2* LinvDF = reinterpret_cast<float2*>(base + ub + sb + eb + bb);
+  int* scales = reinterpret_cast<int*>(base + ub + sb + eb + bb + lb);
+  float2* yDF = reinterpret_cast<float2*>(base + ub + sb + eb + bb + lb + cb);
   cudaError_t err = cudaMemsetAsync(U, 0, (size_t)n * n * sizeof(float2), st);
   if (err != cudaSuccess) return err;
-  for (int64_t k0 = 0; k0 < n; k0 += NB) {
-    const int kb = (int)((n - k0) < NB ? (n - k0) : NB);
-    if (k0 > 0) {
-      const int64_t cnt = (n - k0) * kb;
-      panel_fix_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(A, lda, U, n, k0, kb, n);
-      count_launch();
-    }
-    potrf_diag_kernel<<<1, 256, 0, st>>>(A, lda, k0, kb, Linv, flag);
+  if (b && (err = cudaMemcpyAsync(w, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return err;
+  for (int64_t s0 = 0; s0 < n; s0 += kStrip) {
+    const int64_t s1 = (s0 + kStrip < n) ? s0 + kStrip : n;
+    strip_exponent_kernel<<<(unsigned)((ne - s0 + 255) / 256), 256, 0, st>>>(A, lda, s0 > 0 ? U : nullptr, n, s0,
+                                                                             n, ne, ex);
     count_launch();
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
-    const int64_t k1 = k0 + kb;
-    if (k1 >= n) break;
-    double* Lk = Linv + (k0 / NB) * NB * NB;
-    // panel solve L21 = A21 Linv^T as a split GEMM (A21's slices are taken before it is overwritten)
-    OzOperand L = oz_operand_at(base + ub, S, n - k1, kb);
-    OzOperand I = oz_operand_at(base + ub + opb, S, kb, kb);
-    rc = oz_prepare_rows(S, A + k1 * lda + k0, lda, n - k1, kb, L, st);
-    if (!rc) rc = oz_prepare_rows(S, Lk, NB, kb, kb, I, st);
-    if (!rc) rc = oz_gemm(S, false, L, I, n - k1, kb, A + k1 * lda + k0, lda, 0, nullptr, h->flag + 2, st);
-    // trailing update U[k1:, k1:] += L21 L21^T (double-FP32, FP32 pipe)
-    if (!rc) rc = oz_prepare_rows(S, A + k1 * lda + k0, lda, n - k1, kb, L, st);
-    if (!rc)
-      rc = oz_gemm(S, true, L, L, n - k1, n - k1, reinterpret_cast<double*>(U + k1 * n + k1), n, 3, nullptr,
-                   h->flag + 2, st);
-    if (rc) {
-      *rc_out = rc;
-      return cudaErrorUnknown;
+    OzOperand strip;
+    strip.slices = strip_slices;
+    strip.e = ex + s0;
+    strip.npad = rup(n - s0, 128);
+    strip.kpad = kStrip;
+    for (int64_t k0 = s0; k0 < s1; k0 += NB) {
+      const int kb = (int)((n - k0) < NB ? (n - k0) : NB);
+      const int kofs = (int)(k0 - s0);
+      if (kofs > 0) {
+        // U[k0:, k0:k0+kb] += L[k0:, s0:k0] L[k0:k0+kb, s0:k0]^T
+        OzOperand v = oz_operand_rows(strip, S, k0 - s0);
+        v.kuse = kofs;
+        rc = oz_gemm(S, false, v, v, n - k0, kb, reinterpret_cast<double*>(U + k0 * n + k0), n, 3, nullptr,
+                     h->flag + 2, st);
+        if (rc) {
+          *rc_out = rc;
+          return cudaErrorUnknown;
+        }
+      }
+      const float2* Uk = (k0 > 0) ? U : nullptr;
+      err = launch_potrf<ArithDF>(A, lda, k0, kb, Uk, n, Linv, LinvDF, scales, b ? w : nullptr, y, yDF, flag, st);
+      if (err != cudaSuccess) return err;
+      const int64_t k1 = k0 + kb;
+      if (k1 >= n) break;
+      err = launch_panel_split(S, A, lda, k0, kb, k1, n, Uk, n, LinvDF + (k0 / NB) * NB * NB,
+                               scales + (k0 / NB) * NB, strip, ex, s0, kofs, yDF, b ? w : nullptr, flag, st);
+      if (err != cudaSuccess) return err;
+    }
+    if (s1 < n) {
+      // bulk: U[s1:, s1:] += L[s1:, s0:s1] L[s1:, s0:s1]^T (lower tiles).  Its operand is
+      // sliced again from the FP64 panels with each row's own maximum over the strip's
+      // 256 columns (a tighter exponent than the Schur bound, which also covers later
+      // columns): the bulk carries most of the update, so it gets the finer scale.
+      OzOperand w = oz_operand_at(bulk_base, S, n - s1, kStrip);
+      rc = oz_prepare_rows(S, A + s1 * lda + s0, lda, n - s1, s1 - s0, w, st);
+      if (!rc)
+        rc = oz_gemm(S, true, w, w, n - s1, n - s1, reinterpret_cast<double*>(U + s1 * n + s1), n, 3, nullptr,
+                     h->flag + 2, st);
+      if (rc) {
+        *rc_out = rc;
+        return cudaErrorUnknown;
+      }
     }
   }
   return cudaSuccess;
 }
 
-cudaError_t cholesky_solve(const double* A, int64_t n, int64_t lda, const double* Linv, const double* b, double* x,
-                           double* tmp, cudaStream_t st) {
-  (void)tmp;
-  cudaError_t err = cudaMemcpyAsync(x, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+namespace {
+// backward substitution L^T x = y; w: n doubles of work space
+cudaError_t backward_solve(const double* A, int64_t n, int64_t lda, const double* Linv, const double* y, double* x,
+                           double* w, cudaStream_t st) {
+  cudaError_t err = cudaMemcpyAsync(w, y, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
   if (err != cudaSuccess) return err;
   const int64_t nblk = (n + NB - 1) / NB;
-  // forward: L z = b
-  for (int64_t k = 0; k < nblk; k++) {
-    const int64_t k0 = k * NB;
-    const int kb = (int)((n - k0) < NB ? (n - k0) : NB);
-    tri_block_kernel<<<1, NB, 0, st>>>(Linv + k * NB * NB, x, k0, kb, 0);
-    count_launch();
-    const int64_t k1 = k0 + kb;
-    if (k1 < n) {
-      const int64_t threads = (n - k1) * 32;
-      fwd_update_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(A, lda, x, k0, kb, k1, n);
-      count_launch();
-    }
-  }
-  // backward: L^T x = z
   for (int64_t k = nblk - 1; k >= 0; k--) {
     const int64_t k0 = k * NB;
     const int kb = (int)((n - k0) < NB ? (n - k0) : NB);
-    tri_block_kernel<<<1, NB, 0, st>>>(Linv + k * NB * NB, x, k0, kb, 1);
-    count_launch();
-    if (k0 > 0) bwd_update_kernel<<<(unsigned)((k0 + 255) / 256), 256, 0, st>>>(A, lda, x, k0, kb);
+    const int64_t blocks = k0 > 0 ? (k0 + NB - 1) / NB : 1;
+    bwd_step_kernel<<<(unsigned)blocks, kSolveThreads, 0, st>>>(A, lda, Linv + k * NB * NB, w, x, k0, kb);
     count_launch();
   }
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t cholesky_solve(const double* A, int64_t n, int64_t lda, const double* Linv, const double* b, double* x,
+                           double* tmp, cudaStream_t st) {
+  // tmp: 2n doubles (the work vector and the forward result)
+  double* w = tmp;
+  double* y = tmp + n;
+  cudaError_t err = cudaMemcpyAsync(w, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (err != cudaSuccess) return err;
+  const int64_t nblk = (n + NB - 1) / NB;
+  const int64_t cap = 2 * 152;   // two CTAs per SM of a GB300 at most: the redundant 64 x 64 product stays small
+  // forward: L y = b
+  for (int64_t k = 0; k < nblk; k++) {
+    const int64_t k0 = k * NB;
+    const int kb = (int)((n - k0) < NB ? (n - k0) : NB);
+    int64_t blocks = (n - k0 - kb + 7) / 8;
+    blocks = blocks < 1 ? 1 : (blocks > cap ? cap : blocks);
+    fwd_step_kernel<<<(unsigned)blocks, kSolveThreads, 0, st>>>(A, lda, Linv + k * NB * NB, w, y, k0, kb, n);
+    count_launch();
+  }
+  return backward_solve(A, n, lda, Linv, y, x, w, st);
+}
+
+cudaError_t cholesky_solve_backward(const double* A, int64_t n, int64_t lda, const double* Linv, const double* y,
+                                    double* x, double* tmp, cudaStream_t st) {
+  return backward_solve(A, n, lda, Linv, y, x, tmp, st);
 }
 
 }  // namespace gn

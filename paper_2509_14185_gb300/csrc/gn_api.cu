@@ -75,7 +75,7 @@ void free_all(gn_handle* h) {
   if (h->hpin) cudaFreeHost(h->hpin);
 }
 
-// Device copies of the normalisation point live at the end of vtmp's header.
+// Device copy of the normalisation point: red[512 .. 513].
 struct Pass {
   int mode;
   double* r;        // r~ destination (may be null)
@@ -485,7 +485,8 @@ int gn_damped_solve(gn_handle* h, const double* G, const double* g, double* gamm
     GN_TRY_CUDA(cudaMemsetAsync(h->flag + 1, 0, sizeof(int), h->st));
     if (h->precision == GN_PREC_SPLIT_ALL) {
       int rc = GN_OK;
-      cudaError_t e = cholesky_factor_split(h, h->A, Pp, Pp, h->Linv, h->flag + 1, h->n_slices, &rc);
+      cudaError_t e = cholesky_factor_split(h, h->A, Pp, Pp, h->Linv, h->flag + 1, h->n_slices, g, h->vtmp + Pp,
+                                            h->vtmp, &rc);
       if (rc) return rc;
       GN_TRY_CUDA(e);
     } else {
@@ -508,7 +509,11 @@ int gn_damped_solve(gn_handle* h, const double* G, const double* g, double* gamm
     retries++;
   }
   if (retries_out) *retries_out = retries;
-  GN_TRY_CUDA(cholesky_solve(h->A, Pp, Pp, h->Linv, g, delta_out, nullptr, h->st));
+  // vtmp holds >= 2 Pp doubles: the work vector and (split path) the forward result y
+  if (h->precision == GN_PREC_SPLIT_ALL)
+    GN_TRY_CUDA(cholesky_solve_backward(h->A, Pp, Pp, h->Linv, h->vtmp + Pp, delta_out, h->vtmp, h->st));
+  else
+    GN_TRY_CUDA(cholesky_solve(h->A, Pp, Pp, h->Linv, g, delta_out, h->vtmp, h->st));
   return GN_OK;
 }
 

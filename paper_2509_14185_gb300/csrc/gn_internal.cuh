@@ -3,6 +3,7 @@
 // of the public ABI (include/gn.h).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -161,17 +162,42 @@ cudaError_t hilbert_build(const double* y, int64_t n, int M, double* kf, double*
 constexpr int kCholNB = 64;
 cudaError_t cholesky_factor(double* A, int64_t n, int64_t lda, double* Linv, int* flag, cudaStream_t st);
 cudaError_t cholesky_solve(const double* A, int64_t n, int64_t lda, const double* Linv, const double* b,
-                           double* x, double* tmp, cudaStream_t st);
+                           double* x, double* tmp, cudaStream_t st);   // tmp: 2n doubles
+// L^T x = y only (the forward half already done, e.g. inside cholesky_factor_split); tmp: n doubles
+cudaError_t cholesky_solve_backward(const double* A, int64_t n, int64_t lda, const double* Linv, const double* y,
+                                    double* x, double* tmp, cudaStream_t st);
 
 // Split-precision (Ozaki, BF16 slices on tcgen05) GEMM C op= A B^T (ozaki.cu).
 // An operand holds S BF16 slices [S][npad][kpad] (K-major) and one power-of-two
 // exponent per row (npad rows, padded with zeros).
 constexpr int kOzMaxSlices = 6;
 struct OzOperand {
-  void* slices;   // __nv_bfloat16 [S][npad][kpad]
-  int* e;         // [npad]
-  int64_t npad, kpad;
+  void* slices;          // __nv_bfloat16 [S][npad][kpad]
+  int* e;                // [npad]
+  int64_t npad, kpad;    // npad is also the row stride between slices
+  int64_t kuse = 0;      // contraction length actually used (a multiple of 32; 0: kpad)
+  int64_t map_rows = 0;  // rows addressable from `slices` in the 2D slice view (0: S npad)
 };
+// rows [row_off, ...) of op as an operand of its own (same slice stride; row_off % 8 == 0)
+OzOperand oz_operand_rows(const OzOperand& op, int S, int64_t row_off);
+// Slices of one value x of an operand row with exponent e (2^e > max |row|): the
+// integer round(x 2^{8S-e}) written in balanced base-256 digits a_0 .. a_{S-1}
+// (a_0 carries the sign and the rest lie in [-128, 128)); slice q holds
+// a_q 2^{-8(q+1)}, exact in BF16.  out[q * stride] receives slice q.
+template <int S>
+__device__ __forceinline__ void oz_digits(double x, int e, __nv_bfloat16* out, int64_t stride) {
+  long long v = llrint(ldexp(x, 8 * S - e));
+  int a[S];
+#pragma unroll
+  for (int q = S - 1; q >= 1; q--) {
+    const long long d = (v + 128) >> 8;
+    a[q] = (int)(v - (d << 8));
+    v = d;
+  }
+  a[0] = (int)v;
+#pragma unroll
+  for (int q = 0; q < S; q++) out[q * stride] = __float2bfloat16_rn(ldexpf((float)a[q], -8 * (q + 1)));
+}
 size_t oz_operand_bytes(int S, int64_t n, int64_t k);
 OzOperand oz_operand_at(void* base, int S, int64_t n, int64_t k);
 // X is K x n row-major (operand row j = column j of X); part: 64 * npad doubles of scratch
@@ -189,7 +215,8 @@ int split_gram(gn_handle* h, const double* J, int64_t ld, int64_t nrows, double*
 // grow the handle's split workspace to at least `need` bytes
 int ensure_split_ws(gn_handle* h, size_t need);
 // blocked Cholesky whose trailing updates run through oz_gemm
+// (with b: also the forward substitution L y = b, w being n doubles of work space)
 cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t lda, double* Linv, int* flag, int S,
-                                  int* rc_out);
+                                  const double* b, double* y, double* w, int* rc_out);
 
 }  // namespace gn

@@ -436,22 +436,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // ---------------------------------------------------------------------------
 // operand preparation: exponents and slices (K-major, [S][npad][kpad] BF16)
 // ---------------------------------------------------------------------------
-// digits of one value x with exponent e into the S slice values
-template <int S>
-__device__ __forceinline__ void digits(double x, int e, __nv_bfloat16* out, int64_t stride) {
-  long long v = llrint(ldexp(x, 8 * S - e));
-  int a[S];
-#pragma unroll
-  for (int q = S - 1; q >= 1; q--) {
-    const long long d = (v + 128) >> 8;
-    a[q] = (int)(v - (d << 8));
-    v = d;
-  }
-  a[0] = (int)v;
-#pragma unroll
-  for (int q = 0; q < S; q++) out[q * stride] = __float2bfloat16_rn(ldexpf((float)a[q], -8 * (q + 1)));
-}
-
 // columns of a K x n row-major matrix (J layout): partial column maxima over 64 row chunks
 constexpr int CM_CHUNKS = 64;
 __global__ void colmax_partial(const double* __restrict__ X, int64_t ld, int64_t nrows, int64_t ncols,
@@ -492,7 +476,7 @@ __global__ void __launch_bounds__(256) split_cols_kernel(const double* __restric
     const int kk = (t >> 5) + 8 * r;
     const int64_t k = k0 + kk;
     const double x = (k < nrows && j < ncols) ? X[k * ld + j] : 0.0;
-    digits<S>(x, ex, &sl[0][jj][kk], 32 * (64 + 8));
+    oz_digits<S>(x, ex, &sl[0][jj][kk], 32 * (64 + 8));
   }
   __syncthreads();
   for (int idx = t; idx < S * 32 * 8; idx += 256) {
@@ -529,7 +513,7 @@ __global__ void split_rows_kernel(const double* __restrict__ X, int64_t ld, int6
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = idx / kpad, c = idx - row * kpad;
     const double x = (row < nrows && c < k) ? X[row * ld + c] : 0.0;
-    digits<S>(x, e[row], out + row * kpad + c, npad * kpad);
+    oz_digits<S>(x, e[row], out + row * kpad + c, npad * kpad);
   }
 }
 
@@ -563,7 +547,7 @@ int encode(const OzOperand& op, int S, CUtensorMap* map) {
     return GN_ERR_UNSUPPORTED;
   }
   memset(map, 0, sizeof(*map));
-  cuuint64_t dims[2] = {(cuuint64_t)op.kpad, (cuuint64_t)(S * op.npad)};
+  cuuint64_t dims[2] = {(cuuint64_t)op.kpad, (cuuint64_t)(op.map_rows > 0 ? op.map_rows : S * op.npad)};
   cuuint64_t strides[1] = {(cuuint64_t)(op.kpad * 2)};
   cuuint32_t box[2] = {BKS, TM};
   cuuint32_t estr[2] = {1, 1};
@@ -621,7 +605,7 @@ int launch_oz(const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, doub
   OzArgs a;
   a.rowsA = A.npad;
   a.rowsB = B.npad;
-  a.Kpad = A.kpad;
+  a.Kpad = A.kuse > 0 ? A.kuse : A.kpad;
   a.M = M;
   a.N = N;
   const int64_t mt = (M + TM - 1) / TM, nt = (N + TN - 1) / TN;
@@ -682,9 +666,17 @@ int oz_prepare_rows(int S, const double* X, int64_t ld, int64_t n, int64_t k, co
   }
 }
 
+OzOperand oz_operand_rows(const OzOperand& op, int S, int64_t row_off) {
+  OzOperand v = op;
+  v.slices = static_cast<__nv_bfloat16*>(op.slices) + row_off * op.kpad;
+  v.e = op.e + row_off;
+  v.map_rows = (op.map_rows > 0 ? op.map_rows : S * op.npad) - row_off;
+  return v;
+}
+
 int oz_gemm(int S, bool sym, const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, double* C, int64_t ldc,
             int mode, const double* rowscale, int* flag, cudaStream_t st) {
-  if (A.kpad != B.kpad) return GN_ERR_INVALID;
+  if (A.kpad != B.kpad || A.kuse != B.kuse || A.kuse % BKS != 0 || A.kuse > A.kpad) return GN_ERR_INVALID;
 #define GN_OZ_CASE(s)                                                                     \
   case s:                                                                                 \
     return sym ? launch_oz<s, true>(A, B, M, N, C, ldc, mode, rowscale, flag, st)         \
