@@ -16,6 +16,7 @@
 // remaining vector spread over all SMs.
 #include <cmath>
 #include <type_traits>
+#include <vector>
 
 #include "gn_internal.cuh"
 
@@ -751,7 +752,7 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
   const size_t lb = rup(nblk * NB * NB * sizeof(float2), 256);
   const size_t cb = rup(nblk * NB * sizeof(int), 256);
   const size_t yb = rup(NB * sizeof(float2), 256);
-  int rc = ensure_split_ws(h, ub + sb + eb + bb + lb + cb + yb + 256);
+  int rc = ensure_split_ws(h, ub + sb + eb + 2 * bb + lb + cb + yb + 256);
   if (rc) {
     *rc_out = rc;
     return cudaErrorMemoryAllocation;
@@ -760,24 +761,59 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
   float2* U = reinterpret_cast<float2*>(base);
   void* strip_slices = base + ub;
   int* ex = reinterpret_cast<int*>(base + ub + sb);
-  unsigned char* bulk_base = base + ub + sb + eb;
-  float2* LinvDF = reinterpret_cast<float2*>(base + ub + sb + eb + bb);
-  int* scales = reinterpret_cast<int*>(base + ub + sb + eb + bb + lb);
-  float2* yDF = reinterpret_cast<float2*>(base + ub + sb + eb + bb + lb + cb);
-  cudaError_t err = cudaMemsetAsync(U, 0, (size_t)n * n * sizeof(float2), st);
+  unsigned char* bulk_base = base + ub + sb + eb;   // two bulk operands of bb bytes
+  float2* LinvDF = reinterpret_cast<float2*>(base + ub + sb + eb + 2 * bb);
+  int* scales = reinterpret_cast<int*>(base + ub + sb + eb + 2 * bb + lb);
+  float2* yDF = reinterpret_cast<float2*>(base + ub + sb + eb + 2 * bb + lb + cb);
+  // look-ahead streams: the chain of each strip and the bulk update of the next strip's
+  // columns run on sh (high priority); the rest of each bulk update on sl, concurrently
+  // with the next strip's chain
+  if (!h->st_hi) {
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->st_hi, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->st_lo, cudaStreamNonBlocking, least);
+    if (e != cudaSuccess) return e;
+  }
+  cudaStream_t sh = h->st_hi, sl = h->st_lo;
+  const int64_t nstrip = (n + kStrip - 1) / kStrip;
+  std::vector<cudaEvent_t> evs(2 * nstrip + 3, nullptr);
+  cudaError_t err = cudaSuccess;
+  for (auto& e : evs)
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  struct Guard {   // events may be destroyed while work on them is pending
+    std::vector<cudaEvent_t>& v;
+    ~Guard() {
+      for (auto e : v)
+        if (e) cudaEventDestroy(e);
+    }
+  } guard{evs};
   if (err != cudaSuccess) return err;
-  if (b && (err = cudaMemcpyAsync(w, b, n * sizeof(double), cudaMemcpyDeviceToDevice, st)) != cudaSuccess) return err;
-  for (int64_t s0 = 0; s0 < n; s0 += kStrip) {
+  cudaEvent_t* evA = evs.data();            // [t]: bulk operand of strip t sliced, next strip's columns updated
+  cudaEvent_t* evB = evs.data() + nstrip;   // [t]: deferred bulk update of strip t done
+  cudaEvent_t e0 = evs[2 * nstrip], e_hi = evs[2 * nstrip + 1], e_lo = evs[2 * nstrip + 2];
+  std::vector<char> launchedB(nstrip, 0);
+  auto fail = [&](int code) {
+    *rc_out = code;
+    return cudaErrorUnknown;
+  };
+  if ((err = cudaEventRecord(e0, st)) != cudaSuccess) return err;
+  if ((err = cudaStreamWaitEvent(sh, e0, 0)) != cudaSuccess) return err;
+  if ((err = cudaStreamWaitEvent(sl, e0, 0)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(U, 0, (size_t)n * n * sizeof(float2), sh)) != cudaSuccess) return err;
+  if (b && (err = cudaMemcpyAsync(w, b, n * sizeof(double), cudaMemcpyDeviceToDevice, sh)) != cudaSuccess) return err;
+  strip_exponent_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, sh>>>(A, lda, nullptr, n, 0, n, ne, ex);
+  count_launch();
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  for (int64_t t = 0; t < nstrip; t++) {
+    const int64_t s0 = t * kStrip;
     const int64_t s1 = (s0 + kStrip < n) ? s0 + kStrip : n;
-    strip_exponent_kernel<<<(unsigned)((ne - s0 + 255) / 256), 256, 0, st>>>(A, lda, s0 > 0 ? U : nullptr, n, s0,
-                                                                             n, ne, ex);
-    count_launch();
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
     OzOperand strip;
     strip.slices = strip_slices;
     strip.e = ex + s0;
     strip.npad = rup(n - s0, 128);
     strip.kpad = kStrip;
+    // the strip's chain: in-strip updates, diagonal factors, panels
     for (int64_t k0 = s0; k0 < s1; k0 += NB) {
       const int kb = (int)((n - k0) < NB ? (n - k0) : NB);
       const int kofs = (int)(k0 - s0);
@@ -786,38 +822,57 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
         OzOperand v = oz_operand_rows(strip, S, k0 - s0);
         v.kuse = kofs;
         rc = oz_gemm(S, false, v, v, n - k0, kb, reinterpret_cast<double*>(U + k0 * n + k0), n, 3, nullptr,
-                     h->flag + 2, st);
-        if (rc) {
-          *rc_out = rc;
-          return cudaErrorUnknown;
-        }
+                     h->flag + 2, sh);
+        if (rc) return fail(rc);
       }
       const float2* Uk = (k0 > 0) ? U : nullptr;
-      err = launch_potrf<ArithDF>(A, lda, k0, kb, Uk, n, Linv, LinvDF, scales, b ? w : nullptr, y, yDF, flag, st);
+      err = launch_potrf<ArithDF>(A, lda, k0, kb, Uk, n, Linv, LinvDF, scales, b ? w : nullptr, y, yDF, flag, sh);
       if (err != cudaSuccess) return err;
       const int64_t k1 = k0 + kb;
       if (k1 >= n) break;
       err = launch_panel_split(S, A, lda, k0, kb, k1, n, Uk, n, LinvDF + (k0 / NB) * NB * NB,
-                               scales + (k0 / NB) * NB, strip, ex, s0, kofs, yDF, b ? w : nullptr, flag, st);
+                               scales + (k0 / NB) * NB, strip, ex, s0, kofs, yDF, b ? w : nullptr, flag, sh);
       if (err != cudaSuccess) return err;
     }
-    if (s1 < n) {
-      // bulk: U[s1:, s1:] += L[s1:, s0:s1] L[s1:, s0:s1]^T (lower tiles).  Its operand is
-      // sliced again from the FP64 panels with each row's own maximum over the strip's
-      // 256 columns (a tighter exponent than the Schur bound, which also covers later
-      // columns): the bulk carries most of the update, so it gets the finer scale.
-      OzOperand w = oz_operand_at(bulk_base, S, n - s1, kStrip);
-      rc = oz_prepare_rows(S, A + s1 * lda + s0, lda, n - s1, s1 - s0, w, st);
-      if (!rc)
-        rc = oz_gemm(S, true, w, w, n - s1, n - s1, reinterpret_cast<double*>(U + s1 * n + s1), n, 3, nullptr,
-                     h->flag + 2, st);
-      if (rc) {
-        *rc_out = rc;
-        return cudaErrorUnknown;
-      }
+    if (s1 >= n) break;
+    // bulk update of the trailing matrix, U[s1:, s1:] += L[s1:, s0:s1] L[s1:, s0:s1]^T.  Its
+    // operand is sliced again from the FP64 panels with each row's own maximum over the
+    // strip's 256 columns (a tighter exponent than the Schur bound, which also covers later
+    // columns).  Double buffered: buffer t % 2 was last read by the deferred update of strip
+    // t - 2, which the wait before the previous strip's next-columns update already covers.
+    OzOperand wb = oz_operand_at(bulk_base + (t & 1) * bb, S, n - s1, kStrip);
+    rc = oz_prepare_rows(S, A + s1 * lda + s0, lda, n - s1, s1 - s0, wb, sh);
+    if (rc) return fail(rc);
+    // (a) the next strip's columns now, on the critical path; the deferred update of strip
+    //     t - 1 writes those columns too, so it must be done first
+    if (t >= 1 && launchedB[t - 1] && (err = cudaStreamWaitEvent(sh, evB[t - 1], 0)) != cudaSuccess) return err;
+    const int64_t nn = (n - s1 < kStrip) ? n - s1 : kStrip;
+    rc = oz_gemm(S, false, wb, wb, n - s1, nn, reinterpret_cast<double*>(U + s1 * n + s1), n, 3, nullptr,
+                 h->flag + 2, sh);
+    if (rc) return fail(rc);
+    // the next strip's row exponents, from a fixed state of U (strip t's deferred update not yet applied:
+    // a looser but valid bound for rows past the next strip, and a reproducible one)
+    strip_exponent_kernel<<<(unsigned)((ne - s1 + 255) / 256), 256, 0, sh>>>(A, lda, U, n, s1, n, ne, ex);
+    count_launch();
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    if ((err = cudaEventRecord(evA[t], sh)) != cudaSuccess) return err;
+    // (b) the rest, U[s2:, s2:], deferred to sl: it overlaps the next strip's chain, which
+    //     touches only the next strip's columns
+    const int64_t s2 = s1 + kStrip;
+    if (s2 < n) {
+      if ((err = cudaStreamWaitEvent(sl, evA[t], 0)) != cudaSuccess) return err;
+      OzOperand wv = oz_operand_rows(wb, S, kStrip);
+      rc = oz_gemm(S, true, wv, wv, n - s2, n - s2, reinterpret_cast<double*>(U + s2 * n + s2), n, 3, nullptr,
+                   h->flag + 2, sl);
+      if (rc) return fail(rc);
+      if ((err = cudaEventRecord(evB[t], sl)) != cudaSuccess) return err;
+      launchedB[t] = 1;
     }
   }
-  return cudaSuccess;
+  if ((err = cudaEventRecord(e_hi, sh)) != cudaSuccess) return err;
+  if ((err = cudaEventRecord(e_lo, sl)) != cudaSuccess) return err;
+  if ((err = cudaStreamWaitEvent(st, e_hi, 0)) != cudaSuccess) return err;
+  return cudaStreamWaitEvent(st, e_lo, 0);
 }
 
 namespace {

@@ -404,6 +404,8 @@ int gn_init(const gn_problem* p, void* cuda_stream, gn_handle** out) {
 int gn_destroy(gn_handle* h) {
   if (!h) return GN_OK;
   cudaStreamSynchronize(h->st);
+  if (h->st_hi) cudaStreamDestroy(h->st_hi);
+  if (h->st_lo) cudaStreamDestroy(h->st_lo);
   free_all(h);
   if (h->tmaps) free(h->tmaps);
   delete h;

@@ -98,7 +98,7 @@ struct gn_handle {
   double* Linv;           // inverses of the diagonal blocks [nblk x 64 x 64]
   double* g;              // gradient [Pp]
   double* delta;          // step [Pp]
-  double* vtmp;           // scratch [max(Pp, n_rows)]
+  double* vtmp;           // scratch [64 x (max(Pp, n_rows) + 16)]
   double* red;            // reduction partials
   int* flag;              // device status word
   double* hpin;           // pinned host scalars
@@ -118,6 +118,9 @@ struct gn_handle {
   void* split_ws;
   size_t split_ws_bytes;
   void* tmaps;            // host copies of TMA descriptors
+  // streams of the split factorisation's look-ahead (created on first use)
+  cudaStream_t st_hi = nullptr;   // critical path (high priority)
+  cudaStream_t st_lo = nullptr;   // deferred bulk updates (low priority)
 };
 
 namespace gn {
