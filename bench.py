@@ -418,14 +418,18 @@ def kernel_report(prob, args, phases):
     c = cf / (chol_ms * 1e-3) / 1e12
     if args.precision == "split_all":
         out["cholesky"] = {"bound": "mixed", "fp64_equivalent_tflops": c, "ms": chol_ms,
-                           "kernel": f"potrf_diag (FP64, one SM per 64 x 64 block) + ozaki_kernel<{args.slices},0> "
-                                     f"(panel solves) + ozaki_kernel<{args.slices},1> (trailing updates, "
-                                     "double-FP32 accumulation)",
+                           "kernel": "potrf_inv_kernel<ArithDF> (double-float 64 x 64 diagonal factor and "
+                                     "inverse, one CTA) + panel_df_kernel (double-float panel solve writing the "
+                                     f"split operand) + ozaki_kernel<{args.slices},0> (in-strip updates) + "
+                                     f"ozaki_kernel<{args.slices},1> (K = 256 bulk updates, double-FP32 "
+                                     "accumulation, overlapped with the next strip on a second stream); the phase "
+                                     "includes the backward triangular solve",
                            "algorithmic_flops_per_launch": cf}
     else:
         out["cholesky"] = {"bound": "alu", "achieved": c, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                            "frac": c / FP64_NOMINAL_TFLOPS, "traffic": None, "ms": chol_ms,
-                           "kernel": "potrf_diag + dgemm_kernel<1,1> (blocked FP64 Cholesky, DFMA pipe)",
+                           "kernel": "potrf_inv_kernel<Arith64> + panel_solve_kernel + dgemm_kernel<1,1> "
+                                     "(blocked FP64 Cholesky, DFMA pipe)",
                            "peak_source": fp64_src, "algorithmic_flops_per_launch": cf}
     out["jacobian"] = {"ms": phases[0], "note": "jets + residual + J rows (FP64 pipe); CCF adds the Hilbert "
                                                 "contraction (FP64 DGEMM, or split on tcgen05 under SPLIT_ALL)"}
