@@ -53,6 +53,8 @@ extern "C" {
 #define GN_ERR_TIMEOUT       -6   /* a bounded device-side wait gave up */
 #define GN_ERR_UNSUPPORTED   -7   /* requested precision/path not available on this device */
 #define GN_ERR_TOO_LARGE     -8   /* size exceeds the fixed scratch of gn_jtr_noalloc (16384 columns) */
+#define GN_ERR_IO            -9   /* a checkpoint file could not be written or read */
+#define GN_ERR_MISMATCH     -10   /* a checkpoint belongs to another equation or architecture */
 
 /* ---- problem description ----------------------------------------------- */
 /* Equations (Results and Methods; residual operators as derived from the
@@ -227,6 +229,19 @@ int gn_batch_handle(gn_batch* b, int fit, gn_handle** out);
 int gn_batch_step(gn_batch* b, double* const* thetas, double* lambdas, double* dampings, gn_step_info* infos,
                   int* status);
 int gn_batch_destroy(gn_batch* b);
+
+/* Checkpoint and resume of a fit (the paper's fits run for many Gauss-Newton
+ * steps; resuming one needs theta, lambda and the damping).  The file holds,
+ * little-endian: the magic bytes "GNCK", a uint32 version (1), the int32
+ * equation and n_layers, int32 widths[GN_MAX_LAYERS + 1], the int64 parameter
+ * count P, the float64 lambda and damping, then theta as P float64 values.
+ * gn_save: theta is device memory [P] (read), lambda and damping host values;
+ * synchronises the handle's stream.  gn_load: checks the file against the
+ * handle's equation and widths (GN_ERR_MISMATCH otherwise), writes theta
+ * (device [P]) and *lambda, *damping (host).  Both return GN_OK, GN_ERR_INVALID,
+ * GN_ERR_IO, GN_ERR_MISMATCH (load) or GN_ERR_CUDA; the caller owns all buffers. */
+int gn_save(gn_handle* h, const char* path, const double* theta, double lambda, double damping);
+int gn_load(gn_handle* h, const char* path, double* theta, double* lambda, double* damping);
 
 /* Max |R_k| over the interior points (Methods, "Validation Metrics", max d0
  * residual) at (theta, lambda), unweighted.  *out: host.  Synchronises. */

@@ -389,15 +389,17 @@ __global__ void __launch_bounds__(128) panel_solve_kernel(double* A, int64_t lda
 // each product is the exact FP32 product of the high parts plus the cross
 // terms, its high part added exactly (TwoSum) and the low parts accumulated
 // in FP32, renormalised at the end.  Writes L21 in FP64 and its S BF16 slices
-// into the strip operand (row r at r - row_base, columns kofs + j, exponent ex[r]).
+// into the strip operand (row r at r - row_base, columns kofs + j), with each
+// row's own exponent over this panel's 64 columns in eout[r - row_base] (the
+// strip operand keeps one exponent array per panel).
 constexpr size_t kPanelDFSmem = (size_t)(kPanelRows + NB) * (NB + 1) * sizeof(float2);
 
 template <int S>
 __global__ void __launch_bounds__(128) panel_df_kernel(double* A, int64_t lda, int64_t k0, int kb, int64_t k1,
                                                        int64_t n, const float2* __restrict__ U, int64_t ldu,
                                                        const float2* __restrict__ LkDF, const int* __restrict__ sck,
-                                                       __nv_bfloat16* slices, const int* __restrict__ ex,
-                                                       int64_t row_base, int64_t npad, int64_t kpad, int kofs,
+                                                       __nv_bfloat16* slices, int* eout, int64_t row_base,
+                                                       int64_t npad, int64_t kpad, int kofs,
                                                        const float2* __restrict__ fyDF, double* fw, const int* flag) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float2 (*As)[NB + 1] = reinterpret_cast<float2 (*)[NB + 1]>(smraw);
@@ -508,42 +510,27 @@ __global__ void __launch_bounds__(128) panel_df_kernel(double* A, int64_t lda, i
 #pragma unroll
   for (int a = 0; a < 4; a++) {
     const int64_t r = rb + ty + 8 * a;
+    // row maximum over the 16 lanes holding this row (a half warp); |hi| suffices: with
+    // 2^e > max |hi| the leading digit stays <= 2^8, exact in BF16
+    float m = 0.f;
+#pragma unroll
+    for (int b = 0; b < 4; b++)
+      if (tx + 16 * b < kb) m = fmaxf(m, fabsf(ah[a][b]));
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    int e = 0;
+    if (m > 0.f && isfinite(m)) frexpf(m, &e);
     if (r >= n) continue;
+    if (tx == 0) eout[r - row_base] = e;
 #pragma unroll
     for (int b = 0; b < 4; b++) {
       const int j = tx + 16 * b;
       if (j >= kb) continue;
       const double x = (double)ah[a][b] + (double)al[a][b];
       A[r * lda + k0 + j] = x;
-      oz_digits<S>(x, ex[r], slices + (r - row_base) * kpad + kofs + j, npad * kpad);
+      oz_digits<S>(x, e, slices + (r - row_base) * kpad + kofs + j, npad * kpad);
     }
   }
-}
-
-// Row exponents of one strip of the split factor.  When the columns before s0
-// are eliminated, the rest of row r of L has squared norm equal to the Schur
-// complement's diagonal, S_rr = A[r][r] - U[r][r], so sqrt(S_rr) bounds every
-// entry of row r in this strip and in later ones.  U carries ~2^-46 relative
-// precision, so S_rr is taken with a floor of 2^-44 A[r][r] (a bound that still
-// holds when the computed difference is only rounding noise), and
-// ex[r] = floor((ilogb(S) + 3) / 2) makes 2^ex[r] exceed sqrt(S) by at least
-// sqrt(2) (a margin for rounding in the computed factor).  Rows >= n get 0.
-__global__ void strip_exponent_kernel(const double* __restrict__ A, int64_t lda, const float2* __restrict__ U,
-                                      int64_t ldu, int64_t s0, int64_t n, int64_t total, int* ex) {
-  const int64_t r = s0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= total) return;
-  int e = 0;
-  if (r < n) {
-    const double a = A[r * lda + r];
-    double d = a;
-    if (U) {
-      const float2 u = U[r * ldu + r];
-      d -= (double)u.x + (double)u.y;
-    }
-    const double m2 = fmax(d, 0.0) + ldexp(fabs(a), -44);
-    if (m2 > 0.0 && isfinite(m2)) e = (ilogb(m2) + 3) >> 1;
-  }
-  ex[r] = e;
 }
 
 // Blocked triangular solves with the stored diagonal inverses.  One launch per
@@ -654,7 +641,7 @@ cudaError_t launch_panel(double* A, int64_t lda, int64_t k0, int kb, int64_t k1,
 
 template <int S>
 cudaError_t launch_panel_df(double* A, int64_t lda, int64_t k0, int kb, int64_t k1, int64_t n, const float2* U,
-                            int64_t ldu, const float2* LkDF, const int* sck, const OzOperand& op, const int* ex,
+                            int64_t ldu, const float2* LkDF, const int* sck, const OzOperand& op, int* eout,
                             int64_t row_base, int kofs, const float2* fyDF, double* fw, const int* flag,
                             cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(panel_df_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -663,7 +650,7 @@ cudaError_t launch_panel_df(double* A, int64_t lda, int64_t k0, int kb, int64_t 
   const int64_t blocks = (n - k1 + kPanelRows - 1) / kPanelRows;
   if (blocks <= 0) return cudaSuccess;
   panel_df_kernel<S><<<(unsigned)blocks, 128, kPanelDFSmem, st>>>(A, lda, k0, kb, k1, n, U, ldu, LkDF, sck,
-                                                                  static_cast<__nv_bfloat16*>(op.slices), ex,
+                                                                  static_cast<__nv_bfloat16*>(op.slices), eout,
                                                                   row_base, op.npad, op.kpad, kofs, fyDF, fw,
                                                                   flag);
   count_launch();
@@ -672,12 +659,12 @@ cudaError_t launch_panel_df(double* A, int64_t lda, int64_t k0, int kb, int64_t 
 
 cudaError_t launch_panel_split(int S, double* A, int64_t lda, int64_t k0, int kb, int64_t k1, int64_t n,
                                const float2* U, int64_t ldu, const float2* LkDF, const int* sck, const OzOperand& op,
-                               const int* ex, int64_t row_base, int kofs, const float2* fyDF, double* fw,
+                               int* eout, int64_t row_base, int kofs, const float2* fyDF, double* fw,
                                const int* flag, cudaStream_t st) {
   switch (S) {
 #define GN_PANEL_CASE(s)                                                                                   \
   case s:                                                                                                  \
-    return launch_panel_df<s>(A, lda, k0, kb, k1, n, U, ldu, LkDF, sck, op, ex, row_base, kofs, fyDF, fw, \
+    return launch_panel_df<s>(A, lda, k0, kb, k1, n, U, ldu, LkDF, sck, op, eout, row_base, kofs, fyDF, fw, \
                               flag, st);
     GN_PANEL_CASE(1)
     GN_PANEL_CASE(2)
@@ -720,14 +707,18 @@ cudaError_t cholesky_factor(double* A, int64_t n, int64_t lda, double* Linv, int
 // O(n^2).
 //
 // Two-level blocking: the 64-wide panels are grouped in strips of kStrip = 256
-// columns, and the bulk update of the trailing matrix runs once per strip (one
-// split GEMM with K = 256), not once per panel: a quarter of the passes over U.
-// Inside the strip, each panel's own 64 columns first get the updates of the
-// strip's earlier panels (a 64-column split GEMM over the K columns already
-// written).  For those in-strip updates every row carries one exponent ex[r],
-// fixed at the strip's start from the Schur complement's diagonal
-// (strip_exponent_kernel), so the panels write their slices side by side into
-// one strip operand as they are solved.
+// columns.  Each panel writes its slices into the strip's operand with its own
+// row exponents (one exponent array per panel: the split GEMM applies them per
+// 64-column chunk), so the bulk update of the trailing matrix runs once per
+// strip (one split GEMM with K = 256, a quarter of the passes over U) at the
+// precision of per-panel updates.  Inside the strip, each panel's own 64
+// columns first get the updates of the strip's earlier panels (a 64-column
+// split GEMM over the chunks already written).
+//
+// Look-ahead: the bulk update of strip t is split into the next strip's 256
+// columns, done at once on the critical stream, and the rest, deferred to a
+// low-priority stream where it overlaps strip t + 1's chain (which touches only
+// its own columns).  Strip operands alternate between two buffers.
 //
 // The diagonal blocks and the panels are computed in double-float arithmetic
 // (about 48 significant bits, the precision U and the split GEMM carry).
@@ -744,30 +735,24 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
   auto rup = [](int64_t v, int64_t m) { return (v + m - 1) / m * m; };
   const int64_t npad0 = rup(n, 128);
   const size_t ub = rup((int64_t)n * n * sizeof(float2), 256);
-  const size_t sb = rup((int64_t)S * npad0 * kStrip * 2, 256);
-  const int64_t ne = npad0 + 1024;   // exponent rows, zero padded past n
-  const size_t bb = oz_operand_bytes(S, n, kStrip);
-  const size_t eb = rup(ne * sizeof(int), 256);
+  const size_t sb = rup((int64_t)S * npad0 * kStrip * 2, 256);      // one strip operand's slices
+  const int64_t estride = npad0 + 1024;                             // exponent rows per panel chunk, padded
+  const size_t eb = rup(4 * estride * sizeof(int), 256);            // one strip operand's 4 exponent arrays
   const int64_t nblk = (n + NB - 1) / NB;
   const size_t lb = rup(nblk * NB * NB * sizeof(float2), 256);
   const size_t cb = rup(nblk * NB * sizeof(int), 256);
   const size_t yb = rup(NB * sizeof(float2), 256);
-  int rc = ensure_split_ws(h, ub + sb + eb + 2 * bb + lb + cb + yb + 256);
+  int rc = ensure_split_ws(h, ub + 2 * (sb + eb) + lb + cb + yb + 256);
   if (rc) {
     *rc_out = rc;
     return cudaErrorMemoryAllocation;
   }
   unsigned char* base = static_cast<unsigned char*>(h->split_ws);
   float2* U = reinterpret_cast<float2*>(base);
-  void* strip_slices = base + ub;
-  int* ex = reinterpret_cast<int*>(base + ub + sb);
-  unsigned char* bulk_base = base + ub + sb + eb;   // two bulk operands of bb bytes
-  float2* LinvDF = reinterpret_cast<float2*>(base + ub + sb + eb + 2 * bb);
-  int* scales = reinterpret_cast<int*>(base + ub + sb + eb + 2 * bb + lb);
-  float2* yDF = reinterpret_cast<float2*>(base + ub + sb + eb + 2 * bb + lb + cb);
-  // look-ahead streams: the chain of each strip and the bulk update of the next strip's
-  // columns run on sh (high priority); the rest of each bulk update on sl, concurrently
-  // with the next strip's chain
+  unsigned char* strip_base = base + ub;   // two strip operands of sb + eb bytes
+  float2* LinvDF = reinterpret_cast<float2*>(base + ub + 2 * (sb + eb));
+  int* scales = reinterpret_cast<int*>(base + ub + 2 * (sb + eb) + lb);
+  float2* yDF = reinterpret_cast<float2*>(base + ub + 2 * (sb + eb) + lb + cb);
   if (!h->st_hi) {
     int least = 0, greatest = 0;
     cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
@@ -789,8 +774,8 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
     }
   } guard{evs};
   if (err != cudaSuccess) return err;
-  cudaEvent_t* evA = evs.data();            // [t]: bulk operand of strip t sliced, next strip's columns updated
-  cudaEvent_t* evB = evs.data() + nstrip;   // [t]: deferred bulk update of strip t done
+  cudaEvent_t* evA = evs.data();            // [t]: strip t's next-columns update done
+  cudaEvent_t* evB = evs.data() + nstrip;   // [t]: strip t's deferred bulk update done
   cudaEvent_t e0 = evs[2 * nstrip], e_hi = evs[2 * nstrip + 1], e_lo = evs[2 * nstrip + 2];
   std::vector<char> launchedB(nstrip, 0);
   auto fail = [&](int code) {
@@ -802,17 +787,19 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
   if ((err = cudaStreamWaitEvent(sl, e0, 0)) != cudaSuccess) return err;
   if ((err = cudaMemsetAsync(U, 0, (size_t)n * n * sizeof(float2), sh)) != cudaSuccess) return err;
   if (b && (err = cudaMemcpyAsync(w, b, n * sizeof(double), cudaMemcpyDeviceToDevice, sh)) != cudaSuccess) return err;
-  strip_exponent_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, sh>>>(A, lda, nullptr, n, 0, n, ne, ex);
-  count_launch();
-  if ((err = cudaGetLastError()) != cudaSuccess) return err;
   for (int64_t t = 0; t < nstrip; t++) {
     const int64_t s0 = t * kStrip;
     const int64_t s1 = (s0 + kStrip < n) ? s0 + kStrip : n;
+    // strip operand t % 2 (rows relative to s0); its previous user, strip t - 2's deferred
+    // update, finished before strip t - 1's next-columns update (the wait below)
+    unsigned char* sbase = strip_base + (t & 1) * (sb + eb);
     OzOperand strip;
-    strip.slices = strip_slices;
-    strip.e = ex + s0;
+    strip.slices = sbase;
+    strip.e = reinterpret_cast<int*>(sbase + sb);
     strip.npad = rup(n - s0, 128);
     strip.kpad = kStrip;
+    strip.echunk = NB;
+    strip.estride = estride;
     // the strip's chain: in-strip updates, diagonal factors, panels
     for (int64_t k0 = s0; k0 < s1; k0 += NB) {
       const int kb = (int)((n - k0) < NB ? (n - k0) : NB);
@@ -831,18 +818,13 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
       const int64_t k1 = k0 + kb;
       if (k1 >= n) break;
       err = launch_panel_split(S, A, lda, k0, kb, k1, n, Uk, n, LinvDF + (k0 / NB) * NB * NB,
-                               scales + (k0 / NB) * NB, strip, ex, s0, kofs, yDF, b ? w : nullptr, flag, sh);
+                               scales + (k0 / NB) * NB, strip, strip.e + (kofs / NB) * estride, s0, kofs, yDF,
+                               b ? w : nullptr, flag, sh);
       if (err != cudaSuccess) return err;
     }
     if (s1 >= n) break;
-    // bulk update of the trailing matrix, U[s1:, s1:] += L[s1:, s0:s1] L[s1:, s0:s1]^T.  Its
-    // operand is sliced again from the FP64 panels with each row's own maximum over the
-    // strip's 256 columns (a tighter exponent than the Schur bound, which also covers later
-    // columns).  Double buffered: buffer t % 2 was last read by the deferred update of strip
-    // t - 2, which the wait before the previous strip's next-columns update already covers.
-    OzOperand wb = oz_operand_at(bulk_base + (t & 1) * bb, S, n - s1, kStrip);
-    rc = oz_prepare_rows(S, A + s1 * lda + s0, lda, n - s1, s1 - s0, wb, sh);
-    if (rc) return fail(rc);
+    // bulk update of the trailing matrix, U[s1:, s1:] += L[s1:, s0:s1] L[s1:, s0:s1]^T
+    OzOperand wb = oz_operand_rows(strip, S, s1 - s0);
     // (a) the next strip's columns now, on the critical path; the deferred update of strip
     //     t - 1 writes those columns too, so it must be done first
     if (t >= 1 && launchedB[t - 1] && (err = cudaStreamWaitEvent(sh, evB[t - 1], 0)) != cudaSuccess) return err;
@@ -850,14 +832,9 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
     rc = oz_gemm(S, false, wb, wb, n - s1, nn, reinterpret_cast<double*>(U + s1 * n + s1), n, 3, nullptr,
                  h->flag + 2, sh);
     if (rc) return fail(rc);
-    // the next strip's row exponents, from a fixed state of U (strip t's deferred update not yet applied:
-    // a looser but valid bound for rows past the next strip, and a reproducible one)
-    strip_exponent_kernel<<<(unsigned)((ne - s1 + 255) / 256), 256, 0, sh>>>(A, lda, U, n, s1, n, ne, ex);
-    count_launch();
-    if ((err = cudaGetLastError()) != cudaSuccess) return err;
     if ((err = cudaEventRecord(evA[t], sh)) != cudaSuccess) return err;
-    // (b) the rest, U[s2:, s2:], deferred to sl: it overlaps the next strip's chain, which
-    //     touches only the next strip's columns
+    // (b) the rest, U[s2:, s2:] (lower tiles), deferred to sl: it overlaps the next strip's
+    //     chain, which touches only the next strip's columns
     const int64_t s2 = s1 + kStrip;
     if (s2 < n) {
       if ((err = cudaStreamWaitEvent(sl, evA[t], 0)) != cudaSuccess) return err;

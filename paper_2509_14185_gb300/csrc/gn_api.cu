@@ -301,6 +301,8 @@ const char* gn_error_string(int code) {
     case GN_ERR_TIMEOUT: return "bounded device wait timed out";
     case GN_ERR_UNSUPPORTED: return "unsupported on this device or build";
     case GN_ERR_TOO_LARGE: return "size exceeds the fixed scratch of the allocation-free entry point";
+    case GN_ERR_IO: return "checkpoint file could not be written or read";
+    case GN_ERR_MISMATCH: return "checkpoint belongs to another equation or architecture";
     default: return "unknown status";
   }
 }

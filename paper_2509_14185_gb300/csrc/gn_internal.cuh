@@ -180,6 +180,10 @@ struct OzOperand {
   int64_t npad, kpad;    // npad is also the row stride between slices
   int64_t kuse = 0;      // contraction length actually used (a multiple of 32; 0: kpad)
   int64_t map_rows = 0;  // rows addressable from `slices` in the 2D slice view (0: S npad)
+  // chunked exponents: echunk > 0 gives every row one exponent per echunk contraction
+  // columns, chunk c's at e[c * estride + row] (echunk a multiple of 32, at most 128)
+  int echunk = 0;
+  int64_t estride = 0;
 };
 // rows [row_off, ...) of op as an operand of its own (same slice stride; row_off % 8 == 0)
 OzOperand oz_operand_rows(const OzOperand& op, int S, int64_t row_off);

@@ -185,6 +185,8 @@ struct OzArgs {
   int nt;                 // column tiles (rectangular decode)
   const int* eA;          // exponents of A rows (padded)
   const int* eB;          // exponents of B rows (padded)
+  int64_t estride;        // chunked exponents: stride between the chunks' exponent arrays
+  int spc;                // stages per flush chunk (SPC, or the exponent chunk)
   double* C;
   int64_t ldc;
   int mode;               // 0: C = v, 1: C += rs_i v, 2: C -= v, 3: C2 += v in double-FP32 (FP32 pipe)
@@ -195,7 +197,7 @@ struct OzArgs {
 // ---------------------------------------------------------------------------
 // main kernel
 // ---------------------------------------------------------------------------
-template <int S, bool SYM>
+template <int S, bool SYM, bool CH>
 __global__ void __launch_bounds__(NTHREADS, 1)
     ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const OzArgs p) {
   constexpr int NST = n_stages(S);
@@ -209,7 +211,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* done = acc_empty + 1;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   __shared__ int abort_cta;
-  __shared__ int ecs[2][TM];   // exponents of this tile's rows (0) and columns (1)
+  __shared__ int ecs[2][TM];       // exponents of this tile's rows (0) and columns (1)
+  // chunked mode: 2^e of the rows and columns per chunk, double buffered (a stub otherwise)
+  __shared__ float eccf[CH ? 2 : 1][2][CH ? TM : 1];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t ti, tj;
@@ -224,7 +228,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tj = blockIdx.x % p.nt;
   }
   const int nk = (int)(p.Kpad / BKS);
-  const int nchunk = (nk + SPC - 1) / SPC;
+  const int spc = p.spc;
+  const int nchunk = (nk + spc - 1) / spc;
   int* flag = p.flag;
 
   if (threadIdx.x == 0) {
@@ -280,19 +285,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {
       bool ok = true;
       for (int c = 0; c < nchunk && ok; c++) {
-        const int q_end = (nk - c * SPC) < SPC ? (nk - c * SPC) : SPC;
+        const int q_end = (nk - c * spc) < spc ? (nk - c * spc) : spc;
         for (int q = 0; q < q_end && ok; q++) {
-          const int kt = c * SPC + q;
+          const int kt = c * spc + q;
           const int st = kt % NST;
           if (!mbar_wait(&full[st], (kt / NST) & 1, flag)) { ok = false; break; }
           tc_fence_after();
           const uint32_t base = smem_u32(smem + st * STAGE_BYTES);
-          // pass 0: tail levels (>= 5), which the epilogue's per-chunk flush does not
-          // read, so they overlap the flush of the previous chunk; pass 1: the exact
-          // head levels, after the flush has released their accumulators.
+          // pass 0: tail levels (>= 5); pass 1: the exact head levels.  With one exponent
+          // per row the tail accumulates over the whole K and the per-chunk flush does not
+          // read it, so pass 0 overlaps the flush of the previous chunk and only pass 1
+          // waits for it.  With chunked exponents every chunk flushes the tail too, so
+          // both passes wait.
 #pragma unroll
           for (int pass = 0; pass < 2; pass++) {
-            if (pass == 1 && q == 0 && c > 0) {
+            if (q == 0 && c > 0 && pass == (CH ? 0 : 1)) {
               if (!mbar_wait(acc_empty, (c - 1) & 1, flag)) { ok = false; break; }
               tc_fence_after();
             }
@@ -308,9 +315,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                   const uint64_t da = smem_desc(base + s * SLICE_BYTES + kk * 32);
                   const uint64_t db = smem_desc(base + (S + u) * SLICE_BYTES + kk * 32);
                   // the first pair of a level (s = 0) resets the slot: per chunk for the
-                  // exact head levels, once for the tail
-                  const bool first =
-                      (slot < 3) ? (q == 0 && kk == 0 && s == 0) : (kt == 0 && kk == 0 && s == 0 && u == 3);
+                  // exact head levels; for the tail once, or per chunk with chunked exponents
+                  const bool first = (slot < 3) ? (q == 0 && kk == 0 && s == 0)
+                                                : ((CH ? q : kt) == 0 && kk == 0 && s == 0 && u == 3);
                   mma_bf16(tmem + slot * TN, da, db, first ? 0u : 1u);
                 }
               }
@@ -332,7 +339,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const int qcol = (warp - 2) >> 2;          // column half 0..1
     const int row = quad * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(qcol * EC);
-    ecs[qcol][row] = (qcol == 0) ? p.eA[ti * TM + row] : p.eB[tj * TN + row];
+    // chunked exponents are applied at each chunk's flush, so the final scale is 2^0
+    ecs[qcol][row] = CH ? 0 : ((qcol == 0) ? p.eA[ti * TM + row] : p.eB[tj * TN + row]);
     asm volatile("bar.sync 1, 256;" ::: "memory");   // the 8 epilogue warps only
     float hi[EC], lo[EC];
 #pragma unroll
@@ -340,25 +348,52 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     constexpr int nhead = S < 3 ? S : 3;        // head levels present: 2..min(S+1, 4)
     bool ok = true;
     for (int c = 0; c < nchunk; c++) {
+      if constexpr (CH) {
+        // this chunk's exponents (double buffered: every thread has passed the previous
+        // chunk's barrier, so nobody still reads the buffer of chunk c - 2)
+        const int ev = (qcol == 0) ? p.eA[c * p.estride + ti * TM + row] : p.eB[c * p.estride + tj * TN + row];
+        eccf[c & 1][qcol][row] = pow2f(ev);
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+      }
       if (!mbar_wait(acc_full, c & 1, flag)) { ok = false; break; }
       tc_fence_after();
+      if constexpr (CH) {
+        // head levels and the tail, each scaled by this chunk's 2^e_row 2^e_col (two exact
+        // power-of-two products; the scales come from shared memory, see below)
+        const float rsc = eccf[c & 1][0][row];
 #pragma unroll
-      for (int slot = 0; slot < nhead; slot++) {
+        for (int slot = 0; slot < 4; slot++) {
+          if (slot >= nhead && slot != 3) continue;
+          if (slot == 3 && S < 4) continue;
 #pragma unroll
-        for (int part = 0; part < EC / 16; part++) {
-          float v[16];
-          tmem_ld16(lane_base + (uint32_t)(slot * TN + part * 16), v);
+          for (int part = 0; part < EC / 16; part++) {
+            float v[16];
+            tmem_ld16(lane_base + (uint32_t)(slot * TN + part * 16), v);
 #pragma unroll
-          for (int i = 0; i < 16; i++) dd_add(hi[part * 16 + i], lo[part * 16 + i], v[i]);
+            for (int i = 0; i < 16; i++)
+              dd_add(hi[part * 16 + i], lo[part * 16 + i],
+                     __fmul_rn(__fmul_rn(v[i], rsc), eccf[c & 1][1][qcol * EC + part * 16 + i]));
+          }
         }
-      }
-      if (S >= 4 && c == nchunk - 1) {
+      } else {
 #pragma unroll
-        for (int part = 0; part < EC / 16; part++) {
-          float v[16];
-          tmem_ld16(lane_base + (uint32_t)(3 * TN + part * 16), v);
+        for (int slot = 0; slot < nhead; slot++) {
 #pragma unroll
-          for (int i = 0; i < 16; i++) dd_add(hi[part * 16 + i], lo[part * 16 + i], v[i]);
+          for (int part = 0; part < EC / 16; part++) {
+            float v[16];
+            tmem_ld16(lane_base + (uint32_t)(slot * TN + part * 16), v);
+#pragma unroll
+            for (int i = 0; i < 16; i++) dd_add(hi[part * 16 + i], lo[part * 16 + i], v[i]);
+          }
+        }
+        if (S >= 4 && c == nchunk - 1) {
+#pragma unroll
+          for (int part = 0; part < EC / 16; part++) {
+            float v[16];
+            tmem_ld16(lane_base + (uint32_t)(3 * TN + part * 16), v);
+#pragma unroll
+            for (int i = 0; i < 16; i++) dd_add(hi[part * 16 + i], lo[part * 16 + i], v[i]);
+          }
         }
       }
       tc_fence_before();
@@ -599,8 +634,9 @@ int launch_oz(const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, doub
   rc = encode(B, S, &mb);
   if (rc) return rc;
   const size_t smem = (size_t)bar_offset(S) + 1024 + 256;
-  if (GN_NOTE(cudaFuncSetAttribute(ozaki_kernel<S, SYM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-      cudaSuccess)
+  const bool ch = A.echunk > 0;
+  if (GN_NOTE(cudaFuncSetAttribute(ch ? ozaki_kernel<S, SYM, true> : ozaki_kernel<S, SYM, false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
     return GN_ERR_CUDA;
   OzArgs a;
   a.rowsA = A.npad;
@@ -612,6 +648,8 @@ int launch_oz(const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, doub
   a.nt = (int)nt;
   a.eA = A.e;
   a.eB = B.e;
+  a.spc = A.echunk > 0 ? A.echunk / BKS : SPC;
+  a.estride = A.estride;
   a.C = C;
   a.ldc = ldc;
   a.mode = mode;
@@ -619,7 +657,10 @@ int launch_oz(const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, doub
   a.flag = flag;
   const int64_t tiles = SYM ? mt * (mt + 1) / 2 : mt * nt;
   if (tiles <= 0) return GN_OK;
-  ozaki_kernel<S, SYM><<<(unsigned)tiles, NTHREADS, smem, st>>>(ma, mb, a);
+  if (ch)
+    ozaki_kernel<S, SYM, true><<<(unsigned)tiles, NTHREADS, smem, st>>>(ma, mb, a);
+  else
+    ozaki_kernel<S, SYM, false><<<(unsigned)tiles, NTHREADS, smem, st>>>(ma, mb, a);
   count_launch();
   return GN_NOTE(cudaGetLastError()) == cudaSuccess ? GN_OK : GN_ERR_CUDA;
 }
@@ -677,6 +718,9 @@ OzOperand oz_operand_rows(const OzOperand& op, int S, int64_t row_off) {
 int oz_gemm(int S, bool sym, const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, double* C, int64_t ldc,
             int mode, const double* rowscale, int* flag, cudaStream_t st) {
   if (A.kpad != B.kpad || A.kuse != B.kuse || A.kuse % BKS != 0 || A.kuse > A.kpad) return GN_ERR_INVALID;
+  if (A.echunk != B.echunk || A.estride != B.estride || A.echunk % BKS != 0 || A.echunk > SPC * BKS ||
+      (A.echunk > 0 && A.estride <= 0))
+    return GN_ERR_INVALID;
 #define GN_OZ_CASE(s)                                                                     \
   case s:                                                                                 \
     return sym ? launch_oz<s, true>(A, B, M, N, C, ldc, mode, rowscale, flag, st)         \

@@ -26,6 +26,8 @@ GN_ERR_NOT_SPD = -5
 GN_ERR_TIMEOUT = -6
 GN_ERR_UNSUPPORTED = -7
 GN_ERR_TOO_LARGE = -8
+GN_ERR_IO = -9
+GN_ERR_MISMATCH = -10
 
 GN_PREC_FP64 = 0
 GN_PREC_SPLIT_BF16 = 1
@@ -92,6 +94,8 @@ EXPORTS = {
     "gn_damped_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_D), _P, ctypes.POINTER(ctypes.c_int)]),
     "gn_step": (ctypes.c_int, [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(gn_step_info)]),
     "gn_max_residual": (ctypes.c_int, [_P, _P, _D, ctypes.POINTER(_D)]),
+    "gn_save": (ctypes.c_int, [_P, ctypes.c_char_p, _P, _D, _D]),
+    "gn_load": (ctypes.c_int, [_P, ctypes.c_char_p, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "gn_jtr_noalloc": (ctypes.c_int, [_P, _I64, _I64, _I64, _P, _P, _P]),
     "gn_batch_init": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P)]),
     "gn_batch_handle": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
@@ -250,6 +254,15 @@ class GNProblem:
         out = _D()
         _check(lib().gn_max_residual(self.h, _ptr(theta), float(lam), ctypes.byref(out)), "gn_max_residual")
         return out.value
+
+    def gn_save(self, path, theta, lam, gamma):
+        _check(lib().gn_save(self.h, os.fsencode(path), _ptr(theta), float(lam), float(gamma)), "gn_save")
+
+    def gn_load(self, path, theta_out):
+        lam, gam = _D(), _D()
+        _check(lib().gn_load(self.h, os.fsencode(path), _ptr(theta_out), ctypes.byref(lam), ctypes.byref(gam)),
+               "gn_load")
+        return lam.value, gam.value
 
     # -- conveniences --------------------------------------------------------------
     def new_vec(self, n):
