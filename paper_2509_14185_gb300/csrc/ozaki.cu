@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tj = blockIdx.x % p.nt;
   }
   const int nk = (int)(p.Kpad / BKS);
-  const int spc = p.spc;
+  const int spc = CH ? p.spc : SPC;   // a compile-time constant on the single-exponent path
   const int nchunk = (nk + spc - 1) / spc;
   int* flag = p.flag;
 
