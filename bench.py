@@ -30,6 +30,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one split Gram launch,
+# ozaki_kernel<6,1,0> on the CCF 1st-unstable workload (2278 tiles, S = 6), from a single-pass
+# ncu capture of `bench.py --steps 1 --warmup 1`: 18.37 GB read + 0.29 GB written.  Valid only
+# for that kernel build and workload; re-measure when either changes.
+GRAM_TRAFFIC_BYTES_CCF_S6 = 18.37e9 + 0.29e9
+
 METRIC = "gn_steps_per_s"
 UNIT = "steps/s"
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (DFMA/DMMA) nominal; the probe measured 1.19 DFMA
@@ -406,10 +412,12 @@ def kernel_report(prob, args, phases):
         pk, src = measured_peak("bf16_tflops_sustained", 1700.0)
         executed = gram_executed_flops(rows, Pp, S)
         tens = executed / (gram_ms * 1e-3) / 1e12
+        traffic = (GRAM_TRAFFIC_BYTES_CCF_S6 if (S == 6 and getattr(args, "workload", "") == "ccf_unstable1")
+                   else None)
         out["gram"] = {"bound": "tensor", "achieved": tens, "peak": pk, "unit": "TFLOP/s", "frac": tens / pk,
-                       "traffic": None, "ms": gram_ms,
-                       "kernel": f"ozaki_kernel<{S},1> (BF16 slice products on tcgen05, TMEM accumulators; "
-                                 "the slicing pre-pass is inside the timed phase)",
+                       "traffic": traffic, "traffic_unit": "bytes per launch" if traffic else None, "ms": gram_ms,
+                       "kernel": f"ozaki_kernel<{S},1,0> (split Gram: BF16 slice products on tcgen05, TMEM "
+                                 "accumulators; the slicing pre-pass is inside the timed phase)",
                        "peak_source": src + ", sustained: the kernel runs inside a long step",
                        "executed_flops_per_launch": executed,
                        "fp64_equivalent_tflops": gram_flops / (gram_ms * 1e-3) / 1e12,
@@ -657,9 +665,9 @@ def main():
     # per-phase device times (library CUDA events on the launch stream, averaged over the timed steps)
     phases = [statistics.mean(i["ms_phase"][k] for i in infos) for k in range(7)]
     kernels = kernel_report(prob, args, phases)
-    # the roofline object describes the phase with the largest device time
-    dom = max(("gram", "cholesky"), key=lambda k: kernels[k]["ms"])
-    roof = dict(kernels[dom])
+    # the roofline object describes the largest single kernel, the Gram launch (the Cholesky
+    # phase is a chain of several kernels and is reported beside it under "kernels")
+    roof = dict(kernels["gram"])
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
