@@ -140,3 +140,96 @@ def gn_step(problem, theta, lam, gamma):
     x = np.concatenate([theta, [lam]])
     xn, gamma, info = gn_step_generic(rows_fn, jac_fn, x, gamma)
     return xn[:P].copy(), float(xn[P]), gamma, info
+
+
+# ---------------------------------------------------------------------------
+# The paper's own curvature estimate (Methods, "Second-order Optimizer"): an
+# exponential moving average over iterations of an unbiased rank-1 estimate of
+# G from one product with the Jacobian, and per-iteration learning rate and
+# momentum chosen in closed form by the quadratic-model rule of Martens &
+# Grosse (2015).  Readings (the paper gives no constants and defers to
+# kfac-jax): the sign vector v (independent +-1 entries, so E[v v^T] = I and
+# E[u u^T] = G for u = J~^T v) is an input; the average starts at the first
+# sample; the direction is Delta = -(G_ema + gamma I)^{-1} g; (alpha, mu)
+# minimise the damped model M(d) = g.d + 1/2 d.(G + gamma I).d over
+# d = alpha Delta + mu v_prev with the exact G applied through J~ products
+# (mu = 0 while v_prev = 0); the update is applied whenever the new loss is
+# finite; gamma follows the same Levenberg-Marquardt rule as the exact step,
+# with rho measured against the undamped model.
+# ---------------------------------------------------------------------------
+def rank1_estimate(J, v):
+    """u = J^T v; u u^T estimates J^T J without bias for independent +-1 signs v."""
+    return J.T @ v
+
+
+def mg_coefficients(C_dd, C_dv, C_vv, g_d, g_v, have_v):
+    """(alpha, mu) minimising g.d + 1/2 d.C.d over d = alpha Delta + mu v:
+    the 2 x 2 normal equations [C_dd C_dv; C_dv C_vv] [alpha; mu] = -[g_d; g_v]
+    (mu = 0 without a previous update, or when the 2 x 2 system is singular)."""
+    if have_v:
+        det = C_dd * C_vv - C_dv * C_dv
+        if det > 0.0 and np.isfinite(det):
+            alpha = (-g_d * C_vv + g_v * C_dv) / det
+            mu = (-g_v * C_dd + g_d * C_dv) / det
+            return alpha, mu
+    return -g_d / C_dd, 0.0
+
+
+def ema_step_generic(rows_fn, jac_fn, x, gamma, G_ema, v_prev, signs, beta, first):
+    """One step of the EMA rank-1 optimiser on the unknowns x (theta with lambda appended).
+    Returns (x_new, gamma_new, G_ema_new, v_new, info)."""
+    r = rows_fn(x)
+    J = jac_fn(x)
+    h0 = 0.5 * float(r @ r)
+    g = J.T @ r
+    u = rank1_estimate(J, signs)
+    G_new = np.outer(u, u) if first else beta * G_ema + (1.0 - beta) * np.outer(u, u)
+    info = {"loss_before": h0, "loss_after": h0, "alpha": 0.0, "mu": 0.0, "rho": 0.0,
+            "chol_retries": 0, "status": STEP_OK, "gamma_used": gamma}
+    delta, gamma, retries, ok = damped_solve(G_new, g, gamma)
+    info["chol_retries"] = retries
+    info["gamma_used"] = gamma
+    if not ok:
+        info["status"] = ERR_NOT_SPD
+        return x, gamma, G_new, v_prev, info
+    D = -delta                                   # the direction Delta
+    JD, Jv = J @ D, J @ v_prev
+    C_dd = float(JD @ JD) + gamma * float(D @ D)
+    C_dv = float(JD @ Jv) + gamma * float(D @ v_prev)
+    C_vv = float(Jv @ Jv) + gamma * float(v_prev @ v_prev)
+    g_d, g_v = float(g @ D), float(g @ v_prev)
+    have_v = (not first) and float(v_prev @ v_prev) > 0.0
+    alpha, mu = mg_coefficients(C_dd, C_dv, C_vv, g_d, g_v, have_v)
+    d = alpha * D + mu * v_prev
+    xt = x + d
+    rt = rows_fn(xt)
+    ht = 0.5 * float(rt @ rt) if np.all(np.isfinite(rt)) else np.inf
+    Jd = alpha * JD + mu * Jv
+    model = alpha * g_d + mu * g_v + 0.5 * float(Jd @ Jd)      # undamped model change M(d) - M(0)
+    info.update(alpha=alpha, mu=mu, delta=delta, g=g, G_ema=G_new)
+    if not np.isfinite(ht):
+        info["status"] = WARN_NO_DECREASE
+        return x, gamma * 10.0, G_new, np.zeros_like(v_prev), info
+    rho = (ht - h0) / model if model != 0.0 else 1.0
+    if rho < 0.25:
+        gamma *= 1.5
+    elif rho > 0.75:
+        gamma *= 2.0 / 3.0
+    info.update(rho=rho, loss_after=ht)
+    return xt, gamma, G_new, d, info
+
+
+def ema_step(problem, theta, lam, gamma, G_ema, v_prev, signs, beta, first):
+    """EMA rank-1 step of a profile fit: returns (theta, lambda, gamma, G_ema, v_prev, info)."""
+    P = problem.P
+
+    def rows_fn(x):
+        return problem.rows(x[:P], x[P])
+
+    def jac_fn(x):
+        return jacobian(problem, x[:P], x[P])
+
+    x = np.concatenate([theta, [lam]])
+    xn, gamma, G_new, v_new, info = ema_step_generic(rows_fn, jac_fn, x, gamma, G_ema, v_prev, signs, beta,
+                                                     first)
+    return xn[:P].copy(), float(xn[P]), gamma, G_new, v_new, info

@@ -56,6 +56,12 @@ def uniform(seed: int, n: int, offset: int = 0) -> np.ndarray:
     return ((z >> np.uint64(11)).astype(np.float64) + 1.0) * (1.0 / 9007199254740992.0)
 
 
+def signs(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Independent +-1 values (the top bit of each SplitMix64 draw), as doubles."""
+    z = splitmix64(seed, n, offset)
+    return np.where((z >> np.uint64(63)) == np.uint64(1), 1.0, -1.0)
+
+
 def normal(seed: int, n: int, offset: int = 0) -> np.ndarray:
     """Standard normal deviates by Box-Muller (one deviate per pair of uniforms)."""
     u = uniform(seed, 2 * n, 2 * offset)

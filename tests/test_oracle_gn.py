@@ -171,3 +171,103 @@ def test_planted_transposed_jacobian_breaks_linear_step():
     b = rng.standard_normal(6)
     x1, _, _ = gn.gn_step_generic(lambda x: A @ x - b, lambda x: A.T, np.zeros(6), 1e-14)
     assert np.max(np.abs(x1 - np.linalg.solve(A, b))) > 1e-3
+
+
+# ---------------------------------------------------------------------------
+# the paper's EMA rank-1 optimiser (Methods, "Second-order Optimizer")
+# ---------------------------------------------------------------------------
+def test_rank1_estimate_is_unbiased_exactly():
+    """E[u u^T] = J^T J for u = J^T v with independent +-1 signs: averaging over all 2^R
+    sign vectors of a small J gives J^T J to rounding."""
+    import itertools
+    rng = np.random.default_rng(3)
+    J = rng.standard_normal((6, 4))
+    acc = np.zeros((4, 4))
+    for bits in itertools.product([-1.0, 1.0], repeat=6):
+        u = gn.rank1_estimate(J, np.array(bits))
+        acc += np.outer(u, u)
+    acc /= 2 ** 6
+    assert np.max(np.abs(acc - J.T @ J)) <= 1e-13 * np.max(np.abs(J.T @ J))
+
+
+def test_mg_coefficients_minimise_the_model():
+    """(alpha, mu) from the 2 x 2 normal equations is the minimiser of the quadratic
+    g.d + 1/2 d.C.d over the plane spanned by Delta and v (checked against a dense grid
+    refinement and by the zero gradient)."""
+    rng = np.random.default_rng(5)
+    B = rng.standard_normal((7, 7))
+    C = B.T @ B + 0.1 * np.eye(7)
+    g = rng.standard_normal(7)
+    D, v = rng.standard_normal(7), rng.standard_normal(7)
+    a, m = gn.mg_coefficients(D @ C @ D, D @ C @ v, v @ C @ v, g @ D, g @ v, True)
+
+    def model(a, m):
+        d = a * D + m * v
+        return g @ d + 0.5 * d @ C @ d
+
+    f0 = model(a, m)
+    for da, dm in [(1e-3, 0), (-1e-3, 0), (0, 1e-3), (0, -1e-3), (1e-3, 1e-3), (-1e-3, 1e-3)]:
+        assert model(a + da, m + dm) > f0
+    h = 1e-6
+    assert abs((model(a + h, m) - model(a - h, m)) / (2 * h)) < 1e-6
+    assert abs((model(a, m + h) - model(a, m - h)) / (2 * h)) < 1e-6
+    a1, m1 = gn.mg_coefficients(D @ C @ D, 0.0, 1.0, g @ D, 0.0, False)
+    assert m1 == 0.0 and abs(a1 + (g @ D) / (D @ C @ D)) < 1e-15
+
+
+def test_ema_step_with_exact_curvature_is_the_damped_gn_step():
+    """Special case: when the average already equals the exact G (beta = 1 keeps it) and there
+    is no previous update, Delta = -(G + gamma I)^{-1} g and the closed-form alpha is exactly 1
+    (Delta.C.Delta = -g.Delta for C = G + gamma I), so the step is the plain damped GN step."""
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((12, 5))
+    b = rng.standard_normal(12)
+
+    def rows_fn(x):
+        return A @ x - b
+
+    def jac_fn(x):
+        return A
+
+    x0 = np.zeros(5)
+    G = A.T @ A
+    gamma = 1e-3
+    xn, gam, Gn, vn, info = gn.ema_step_generic(rows_fn, jac_fn, x0, gamma, G, np.zeros(5), np.ones(12), 1.0,
+                                                 False)
+    assert abs(info["alpha"] - 1.0) < 1e-12 and info["mu"] == 0.0
+    step = -np.linalg.solve(G + gamma * np.eye(5), A.T @ (A @ x0 - b))
+    assert np.max(np.abs(xn - (x0 + step))) <= 1e-12 * np.max(np.abs(step))
+    assert np.array_equal(Gn, G) and np.max(np.abs(vn - step)) <= 1e-12 * np.max(np.abs(step))
+
+
+def test_ema_step_first_step_uses_the_rank1_sample_and_reaches_least_squares():
+    """On a linear least-squares problem the EMA optimiser starts its average from the first
+    rank-1 sample, never increases the objective (the closed-form step minimises the model,
+    which is exact for a linear residual) and reaches the least-squares minimum (closed form)."""
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((30, 6))
+    b = rng.standard_normal(30)
+
+    def rows_fn(x):
+        return A @ x - b
+
+    def jac_fn(x):
+        return A
+
+    s = I.signs(4, 30)
+    assert set(np.unique(s)) == {-1.0, 1.0}
+    xs = np.linalg.lstsq(A, b, rcond=None)[0]
+    hmin = 0.5 * float((A @ xs - b) @ (A @ xs - b))
+    x = np.zeros(6)
+    G = np.zeros((6, 6))
+    v = np.zeros(6)
+    gamma = 1.0
+    for k in range(40):
+        sk = I.signs(4, 30, 30 * k)
+        x, gamma, Gn, v, info = gn.ema_step_generic(rows_fn, jac_fn, x, gamma, G, v, sk, 0.9, k == 0)
+        u = A.T @ sk
+        expect = np.outer(u, u) if k == 0 else 0.9 * G + (1.0 - 0.9) * np.outer(u, u)
+        assert np.array_equal(Gn, expect)
+        G = Gn
+        assert info["loss_after"] <= info["loss_before"] * (1 + 1e-12)
+    assert abs(info["loss_after"] - hmin) <= 1e-9 * hmin
