@@ -82,8 +82,9 @@ enum gn_precision {
                               combined in double-FP32 and returned as FP64 */
   GN_PREC_SPLIT_ALL = 2    /* as GN_PREC_SPLIT_BF16, and the other two dense contractions too:
                               the CCF Hilbert contraction J_U = K J_g and the trailing updates
-                              of the blocked Cholesky factorisation (diagonal blocks, panel
-                              solves and the triangular solves stay FP64).  Entrywise error of
+                              of the blocked Cholesky factorisation (accumulated in double-FP32;
+                              diagonal blocks and panels in double-float arithmetic, ~48 bits;
+                              triangular solves FP64; backward error ~2e-13).  Entrywise error of
                               each split product, in units of 2^(e_i+e_j) with |x| < 1 the
                               power-of-two scaled operands and K the contraction length:
                               2^(-8S-1)(|x_i|_1+|x_j|_1) + K 2^(-16S-2) + K S(S-1) 2^(-8S-3)
@@ -126,6 +127,7 @@ typedef struct gn_step_info {
   int status;                /* same value as the return code */
   double ms_phase[8];        /* device time per phase: jacobian, gram, gradient, factor,
                                 solve, line search, total, unused */
+  double momentum;           /* gn_step_ema: the closed-form momentum coefficient mu (0 in gn_step) */
 } gn_step_info;
 
 typedef struct gn_handle gn_handle;
@@ -229,6 +231,25 @@ int gn_batch_handle(gn_batch* b, int fit, gn_handle** out);
 int gn_batch_step(gn_batch* b, double* const* thetas, double* lambdas, double* dampings, gn_step_info* infos,
                   int* status);
 int gn_batch_destroy(gn_batch* b);
+
+/* One step of the paper's own optimiser (Methods, "Second-order Optimizer"): G is
+ * estimated by an exponential moving average over iterations of the unbiased rank-1
+ * estimate u u^T, u = J~^T v (v independent +-1 signs, E[v v^T] = I), and the step
+ * d = alpha Delta + mu v_prev uses the learning rate and momentum that minimise the
+ * quadratic model g.d + 1/2 d.(G + gamma I).d with the exact G applied through J~
+ * products (Martens & Grosse 2015), Delta = -(G_ema + gamma I)^{-1} g.
+ * G_ema: device [P' x P'] row-major, in/out (input ignored when first != 0: the average
+ * starts at the first sample); v_prev: device [P'], the previous update d, in/out
+ * (treated as 0 when first != 0); signs: device [rows] of +-1 values (caller-drawn);
+ * beta: weight of the old average, in [0, 1).  theta, lambda, damping as gn_step; the
+ * update is applied whenever the new loss is finite, and damping follows the same
+ * Levenberg-Marquardt rule as gn_step (rho against the undamped model).  Needs the whole
+ * Jacobian in the handle's J~ buffer (rows x P' x 8 bytes <= 32 GiB), else
+ * GN_ERR_UNSUPPORTED.  Returns GN_OK, GN_WARN_NO_DECREASE (non-finite new loss: theta,
+ * lambda kept, v_prev zeroed, damping x10), GN_ERR_NOT_SPD, GN_ERR_NONFINITE, GN_ERR_INVALID
+ * or GN_ERR_CUDA.  Synchronises. */
+int gn_step_ema(gn_handle* h, double* theta, double* lambda, double* damping, double* G_ema, double* v_prev,
+                const double* signs, double beta, int first, gn_step_info* info);
 
 /* Checkpoint and resume of a fit (the paper's fits run for many Gauss-Newton
  * steps; resuming one needs theta, lambda and the damping).  The file holds,

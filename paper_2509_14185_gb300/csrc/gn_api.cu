@@ -67,7 +67,7 @@ cudaError_t dalloc(T** p, size_t count) {
 }
 
 void free_all(gn_handle* h) {
-  void* ptrs[] = {h->wt, h->theta_t, h->r, h->J, h->G, h->A, h->Linv, h->g, h->delta, h->vtmp, h->red,
+  void* ptrs[] = {h->ema_ws, h->wt, h->theta_t, h->r, h->J, h->G, h->A, h->Linv, h->g, h->delta, h->vtmp, h->red,
                   h->flag, h->gpart, h->kf, h->dcoef, h->snode, h->gnode, h->Jg, h->ug, h->sU, h->tnode,
                   h->split_ws};
   for (void* p : ptrs)
@@ -654,6 +654,133 @@ int gn_step(gn_handle* h, double* theta, double* lambda, double* damping, gn_ste
   inf.ms_phase[4] = tm.ms(5, 6);
   inf.ms_phase[5] = tm.ms(6, 7);
   inf.ms_phase[6] = tm.ms(0, 8);
+  if (info) *info = inf;
+  return inf.status;
+}
+
+// The paper's own optimiser: EMA of rank-1 curvature estimates, closed-form learning rate
+// and momentum (Methods, "Second-order Optimizer"; the readings are listed with the
+// declaration in gn.h).
+int gn_step_ema(gn_handle* h, double* theta, double* lambda, double* damping, double* G_ema, double* v_prev,
+                const double* signs, double beta, int first, gn_step_info* info) {
+  if (!h || !theta || !lambda || !damping || !G_ema || !v_prev || !signs || !(beta >= 0.0 && beta < 1.0))
+    return GN_ERR_INVALID;
+  if (h->jrows < h->n_rows) {
+    set_detail(__FILE__, __LINE__, "gn_step_ema needs the whole Jacobian in one block");
+    return GN_ERR_UNSUPPORTED;
+  }
+  gn_step_info inf;
+  memset(&inf, 0, sizeof(inf));
+  cudaStream_t st = h->st;
+  const int64_t Pp = h->Pp, P = h->P, R = h->n_rows;
+  const double lam = *lambda;
+  double gamma = *damping;
+  if (h->ema_len < Pp + 2 * R) {
+    if (h->ema_ws) cudaFree(h->ema_ws);
+    h->ema_ws = nullptr;
+    h->ema_len = 0;
+    if (GN_NOTE(dalloc(&h->ema_ws, (size_t)(Pp + 2 * R))) != cudaSuccess) return GN_ERR_OOM;
+    h->ema_len = Pp + 2 * R;
+  }
+  double* u = h->ema_ws;
+  double* JD = u + Pp;   // J~ delta
+  double* Jv = JD + R;   // J~ v_prev
+  Timer tm(st);
+  GN_TRY_CUDA(cudaMemsetAsync(h->flag + 2, 0, sizeof(int), st));
+  tm.mark(0);
+  // 1. rows and the Jacobian
+  Pass ps = {MODE_JACOBIAN, h->r, h->J, h->ldJ, 0, R, nullptr};
+  int rc = run_pass(h, theta, lam, ps, nullptr);
+  if (rc) return rc;
+  tm.mark(1);
+  // 2. g = J~^T r~, the rank-1 sample u = J~^T v, its average, h0
+  GN_TRY_CUDA(dgemv_t_scratch(h->J, h->ldJ, R, Pp, h->r, h->g, 0.0, h->vtmp, st));
+  GN_TRY_CUDA(dgemv_t_scratch(h->J, h->ldJ, R, Pp, signs, u, 0.0, h->vtmp, st));
+  rc = loss_of(h, h->r, 0);
+  if (rc) return rc;
+  GN_TRY_CUDA(ema_rank1(G_ema, Pp, Pp, u, beta, first ? 1 : 0, st));
+  if (first) GN_TRY_CUDA(cudaMemsetAsync(v_prev, 0, Pp * sizeof(double), st));
+  GN_TRY_CUDA(cudaMemcpyAsync(h->hpin + 16, h->red + 256, sizeof(double), cudaMemcpyDeviceToHost, st));
+  tm.mark(2);
+  // 3. Delta = -(G_ema + gamma I)^{-1} g  (h->delta holds -Delta)
+  int retries = 0;
+  rc = gn_damped_solve(h, G_ema, h->g, &gamma, h->delta, &retries);
+  tm.mark(3);
+  inf.chol_retries = retries;
+  inf.gamma_used = gamma;
+  const double h0 = 0.5 * h->hpin[16];
+  inf.loss_before = inf.loss_after = h0;
+  if (rc) {
+    inf.status = rc;
+    if (info) *info = inf;
+    return rc;
+  }
+  if (!std::isfinite(h0)) {
+    inf.status = GN_ERR_NONFINITE;
+    if (info) *info = inf;
+    return GN_ERR_NONFINITE;
+  }
+  // 4. exact curvature through J~ products, and the scalars of the 2 x 2 model
+  GN_TRY_CUDA(dgemv_n(h->J, h->ldJ, R, Pp, h->delta, JD, 0.0, st));
+  GN_TRY_CUDA(dgemv_n(h->J, h->ldJ, R, Pp, v_prev, Jv, 0.0, st));
+  const double* xs[8] = {JD, JD, Jv, h->delta, h->delta, v_prev, h->g, h->g};
+  const double* ys[8] = {JD, Jv, Jv, h->delta, v_prev, v_prev, h->delta, v_prev};
+  const int64_t ns[8] = {R, R, R, Pp, Pp, Pp, Pp, Pp};
+  for (int k = 0; k < 8; k++) {
+    GN_TRY_CUDA(dot_partial(xs[k], ys[k], ns[k], h->red, st));
+    GN_TRY_CUDA(finish_sum(h->red, h->red + 260 + k, st));
+  }
+  GN_TRY_CUDA(cudaMemcpyAsync(h->red + 268, h->delta + P, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  GN_TRY_CUDA(cudaMemcpyAsync(h->red + 269, v_prev + P, sizeof(double), cudaMemcpyDeviceToDevice, st));
+  GN_TRY_CUDA(cudaMemcpyAsync(h->hpin + 20, h->red + 260, 10 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  GN_TRY_CUDA(cudaStreamSynchronize(st));
+  const double* s = h->hpin + 20;   // with Delta = -delta:
+  const double C_dd = s[0] + gamma * s[3];
+  const double C_dv = -(s[1] + gamma * s[4]);
+  const double C_vv = s[2] + gamma * s[5];
+  const double g_d = -s[6], g_v = s[7];
+  double alpha = -g_d / C_dd, mu = 0.0;
+  if (!first && s[5] > 0.0) {
+    const double det = C_dd * C_vv - C_dv * C_dv;
+    if (det > 0.0 && std::isfinite(det)) {
+      alpha = (-g_d * C_vv + g_v * C_dv) / det;
+      mu = (-g_v * C_dd + g_d * C_dv) / det;
+    }
+  }
+  const double lam_t = lam - alpha * s[8] + mu * s[9];
+  // 5. the update d = alpha Delta + mu v_prev (v_prev <- d), and the loss at the new point
+  GN_TRY_CUDA(ema_update(theta, h->delta, v_prev, alpha, mu, P, Pp, h->theta_t, st));
+  double ht = 0.0;
+  rc = residual_loss(h, h->theta_t, lam_t, h->r, &ht);
+  if (rc) return rc;
+  tm.mark(4);
+  const double Jd2 = alpha * alpha * s[0] - 2.0 * alpha * mu * s[1] + mu * mu * s[2];
+  const double model = alpha * g_d + mu * g_v + 0.5 * Jd2;   // undamped model change
+  inf.alpha = alpha;
+  inf.momentum = mu;
+  if (!std::isfinite(ht)) {
+    gamma *= 10.0;
+    GN_TRY_CUDA(cudaMemsetAsync(v_prev, 0, Pp * sizeof(double), st));
+    inf.status = GN_WARN_NO_DECREASE;
+  } else {
+    const double rho = model != 0.0 ? (ht - h0) / model : 1.0;
+    if (rho < 0.25) gamma *= 1.5;
+    else if (rho > 0.75) gamma *= 2.0 / 3.0;
+    GN_TRY_CUDA(cudaMemcpyAsync(theta, h->theta_t, P * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    *lambda = lam_t;
+    inf.rho = rho;
+    inf.loss_after = ht;
+    inf.status = GN_OK;
+  }
+  inf.n_trials = 1;
+  *damping = gamma;
+  tm.mark(5);
+  GN_TRY_CUDA(cudaEventSynchronize(tm.ev[5]));
+  inf.ms_phase[0] = tm.ms(0, 1);
+  inf.ms_phase[1] = tm.ms(1, 2);
+  inf.ms_phase[3] = tm.ms(2, 3);
+  inf.ms_phase[5] = tm.ms(3, 4);
+  inf.ms_phase[6] = tm.ms(0, 5);
   if (info) *info = inf;
   return inf.status;
 }

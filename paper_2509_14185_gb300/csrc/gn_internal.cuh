@@ -118,6 +118,9 @@ struct gn_handle {
   void* split_ws;
   size_t split_ws_bytes;
   void* tmaps;            // host copies of TMA descriptors
+  // EMA rank-1 optimiser scratch: u [Pp], J~ Delta [rows], J~ v [rows] (allocated on first use)
+  double* ema_ws = nullptr;
+  int64_t ema_len = 0;
   // streams of the split factorisation's look-ahead (created on first use)
   cudaStream_t st_hi = nullptr;   // critical path (high priority)
   cudaStream_t st_lo = nullptr;   // deferred bulk updates (low priority)
@@ -142,6 +145,10 @@ cudaError_t dgemm(int64_t m, int64_t n, int64_t k, double alpha, const double* A
 
 // Vector helpers (deterministic reductions).
 cudaError_t dot_partial(const double* x, const double* y, int64_t n, double* red, cudaStream_t st);
+// EMA rank-1 optimiser: G = u u^T (first) or beta G + (1 - beta) u u^T; the two-term update
+cudaError_t ema_rank1(double* G, int64_t n, int64_t ld, const double* u, double beta, int first, cudaStream_t st);
+cudaError_t ema_update(const double* theta, const double* delta, double* v, double alpha, double mu, int64_t P,
+                       int64_t n, double* theta_t, cudaStream_t st);
 cudaError_t sumsq_and_flag(const double* x, int64_t n, double* red, cudaStream_t st);
 cudaError_t finish_sum(double* red, double* out_dev, cudaStream_t st);
 cudaError_t axpy_trial(const double* theta, const double* delta, double alpha, int64_t P, double* out,

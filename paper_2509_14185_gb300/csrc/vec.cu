@@ -129,7 +129,47 @@ __global__ void copy_add_diag_kernel(const double* __restrict__ G, double* A, in
   }
 }
 
+// G = u u^T (first) or beta G + (1 - beta) u u^T, the whole n x n matrix (row-major, ld)
+__global__ void ema_rank1_kernel(double* G, int64_t n, int64_t ld, const double* __restrict__ u, double beta,
+                                 int first) {
+  const int64_t total = n * n;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / n, j = idx - i * n;
+    const double p = u[i] * u[j];
+    G[i * ld + j] = first ? p : beta * G[i * ld + j] + (1.0 - beta) * p;
+  }
+}
+
+// d = alpha D + mu v (D = -delta); theta_t = theta + d[0:P); v = d (all n = P + 1 entries)
+__global__ void ema_update_kernel(const double* __restrict__ theta, const double* __restrict__ delta, double* v,
+                                  double alpha, double mu, int64_t P, int64_t n, double* theta_t) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double d = -alpha * delta[i] + mu * v[i];
+    if (i < P) theta_t[i] = theta[i] + d;
+    v[i] = d;
+  }
+}
+
 }  // namespace
+
+cudaError_t ema_rank1(double* G, int64_t n, int64_t ld, const double* u, double beta, int first, cudaStream_t st) {
+  const int64_t total = n * n;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  ema_rank1_kernel<<<(unsigned)blocks, 256, 0, st>>>(G, n, ld, u, beta, first);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t ema_update(const double* theta, const double* delta, double* v, double alpha, double mu, int64_t P,
+                       int64_t n, double* theta_t, cudaStream_t st) {
+  int64_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 4) blocks = 152 * 4;
+  ema_update_kernel<<<(unsigned)blocks, 256, 0, st>>>(theta, delta, v, alpha, mu, P, n, theta_t);
+  count_launch();
+  return cudaGetLastError();
+}
 
 cudaError_t dot_partial(const double* x, const double* y, int64_t n, double* red, cudaStream_t st) {
   reduce_kernel<0><<<RB, RT, 0, st>>>(x, y, n, red);

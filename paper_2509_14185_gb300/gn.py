@@ -68,6 +68,7 @@ class gn_step_info(ctypes.Structure):
         ("n_trials", ctypes.c_int),
         ("status", ctypes.c_int),
         ("ms_phase", ctypes.c_double * 8),
+        ("momentum", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -94,6 +95,8 @@ EXPORTS = {
     "gn_damped_solve": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(_D), _P, ctypes.POINTER(ctypes.c_int)]),
     "gn_step": (ctypes.c_int, [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(gn_step_info)]),
     "gn_max_residual": (ctypes.c_int, [_P, _P, _D, ctypes.POINTER(_D)]),
+    "gn_step_ema": (ctypes.c_int, [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), _P, _P, _P, _D, ctypes.c_int,
+                                   ctypes.POINTER(gn_step_info)]),
     "gn_save": (ctypes.c_int, [_P, ctypes.c_char_p, _P, _D, _D]),
     "gn_load": (ctypes.c_int, [_P, ctypes.c_char_p, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "gn_jtr_noalloc": (ctypes.c_int, [_P, _I64, _I64, _I64, _P, _P, _P]),
@@ -248,6 +251,17 @@ class GNProblem:
         rc = lib().gn_step(self.h, _ptr(theta), ctypes.byref(lam_), ctypes.byref(gam_), ctypes.byref(info))
         if rc < 0 and rc not in (GN_ERR_NOT_SPD, GN_ERR_NONFINITE):
             _check(rc, "gn_step")
+        return rc, lam_.value, gam_.value, info.as_dict()
+
+    def gn_step_ema(self, theta, lam, gamma, G_ema, v_prev, signs, beta, first):
+        """The paper's EMA rank-1 optimiser: theta, G_ema, v_prev updated in place."""
+        lam_ = _D(lam)
+        gam_ = _D(gamma)
+        info = gn_step_info()
+        rc = lib().gn_step_ema(self.h, _ptr(theta), ctypes.byref(lam_), ctypes.byref(gam_), _ptr(G_ema),
+                               _ptr(v_prev), _ptr(signs), float(beta), int(bool(first)), ctypes.byref(info))
+        if rc < 0 and rc not in (GN_ERR_NOT_SPD, GN_ERR_NONFINITE):
+            _check(rc, "gn_step_ema")
         return rc, lam_.value, gam_.value, info.as_dict()
 
     def gn_max_residual(self, theta, lam):
