@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--equal-residual", action="store_true",
                     help="FP64 path for --er-steps steps vs split path to the same max residual (own JSON line)")
     ap.add_argument("--er-steps", type=int, default=50)
+    ap.add_argument("--ema-vs-exact", action="store_true",
+                    help="head-to-head on the same kernels: exact-G damped GN vs the paper's EMA rank-1 "
+                         "optimiser, loss against device time (own JSON line)")
+    ap.add_argument("--ema-beta", type=float, default=0.95)
     ap.add_argument("--workload", default="ccf_unstable1",
                     choices=["ccf_unstable1", "ccf_stable", "ipm", "boussinesq", "batched"],
                     help="ccf_unstable1 is the headline line; the others print their own line")
@@ -128,6 +132,59 @@ def equal_residual(args):
            "split_curve": [(h["step"], h["loss"], h["max_res"]) for h in hs[::5]]}
     print(json.dumps(out))
     val.close()
+    return 0
+
+
+def ema_vs_exact(args):
+    """Exact-G damped GN (gn_step) against the paper's optimiser (gn_step_ema: EMA of rank-1
+    curvature samples, closed-form learning rate and momentum) from the same initialisation,
+    both in the chosen precision, for the same device-time budget: the exact path's --er-steps
+    steps.  Reports the training loss against device time for both."""
+    import numpy as np
+    import torch
+    from paper_2509_14185_gb300 import build as B
+    B.build()
+    from paper_2509_14185_gb300 import gn, inputs
+    w = inputs.ccf_unstable_1d()
+    prec = {"fp64": gn.GN_PREC_FP64, "split": gn.GN_PREC_SPLIT_BF16, "split_all": gn.GN_PREC_SPLIT_ALL}[args.precision]
+    prob = gn.GNProblem.from_workload(w, precision=prec, n_slices=args.slices)
+    Pp, R = prob.P + 1, prob.n_rows
+
+    def curve_exact(n):
+        th = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
+        lam, gam, t, out = w.lam, w.gamma, 0.0, []
+        for k in range(n):
+            rc, lam, gam, info = prob.gn_step(th, lam, gam)
+            t += info["ms_phase"][6] * 1e-3
+            out.append([k + 1, t, info["loss_after"]])
+        return out, t
+
+    def curve_ema(budget):
+        th = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
+        G = torch.zeros((Pp, Pp), dtype=torch.float64, device="cuda")
+        v = torch.zeros(Pp, dtype=torch.float64, device="cuda")
+        lam, gam, t, out, k = w.lam, w.gamma, 0.0, [], 0
+        while t < budget and k < 100000:
+            s = torch.tensor(inputs.signs(1234, R, R * k), dtype=torch.float64, device="cuda")
+            rc, lam, gam, info = prob.gn_step_ema(th, lam, gam, G, v, s, args.ema_beta, k == 0)
+            t += info["ms_phase"][6] * 1e-3
+            k += 1
+            out.append([k, t, info["loss_after"]])
+        return out, t
+
+    exact, budget = curve_exact(args.er_steps)
+    ema, t_ema = curve_ema(budget)
+    best_exact = min(c[2] for c in exact)
+    best_ema = min(c[2] for c in ema)
+    thin = lambda c: c[:: max(1, len(c) // 25)] + [c[-1]]
+    print(json.dumps({"mode": "ema_vs_exact", "workload": w.name, "precision": args.precision,
+                      "beta": args.ema_beta, "budget_device_s": budget,
+                      "exact": {"steps": len(exact), "device_s": budget, "best_loss": best_exact,
+                                "ms_per_step": 1e3 * budget / len(exact)},
+                      "ema": {"steps": len(ema), "device_s": t_ema, "best_loss": best_ema,
+                              "ms_per_step": 1e3 * t_ema / len(ema)},
+                      "exact_curve": thin(exact), "ema_curve": thin(ema)}))
+    prob.close()
     return 0
 
 
@@ -591,6 +648,8 @@ def main():
         return equal_residual(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.ema_vs_exact:
+        return ema_vs_exact(args)
     import numpy as np
     import torch
 
