@@ -164,7 +164,9 @@ struct ArithDF {
   static __device__ __forceinline__ double store_scaled(T v, int k) { return f2d_scaled(v.h, k) + f2d_scaled(v.l, k); }
 };
 
-constexpr int kPotrfThreads = 512;
+constexpr int kPotrfTPR = 16;                       // threads per row of the diagonal block
+constexpr int kPotrfEPT = NB / kPotrfTPR;             // elements (columns) per thread
+constexpr int kPotrfThreads = NB * kPotrfTPR;         // 1024
 constexpr size_t kPotrfSmem = (size_t)(NB * (NB + 1) + 4 * NB) * 8;   // final columns + 2 x 2 broadcast rows
 
 // Factor and invert the diagonal block B = A[k0:k0+kb, k0:k0+kb] (minus U, the
@@ -180,7 +182,8 @@ constexpr size_t kPotrfSmem = (size_t)(NB * (NB + 1) + 4 * NB) * 8;   // final c
 // so no value is rescaled inside the chain.  S[i][c] and Y[i][c] share one
 // register: column c of S is final (and published) at step c, exactly when
 // Y[i][c] starts to accumulate.  Thread (i, g) holds row i's elements
-// c = g + 8m (m = 0..7) in registers: eight independent chains per thread.
+// c = g + 16m (m = 0..3) in registers: four independent chains per thread,
+// 32 warps to hide the FP32 latency of the double-float arithmetic.
 // Each step publishes column j of S and row j of Y to shared memory (double
 // buffered, so one barrier per column suffices).  At the end
 // L'[i][j] = S[i][j] / sqrt(d_j) and L'^{-1}[i][c] = Y[i][c] / sqrt(d_i);
@@ -198,7 +201,7 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_inv_kernel(double* A, int
   T* rowbuf = colbuf + 2 * NB;                                 // [2][NB]: row j of Y; reused for 1/sqrt(d)
   __shared__ int sc[NB];
   if (*flag) return;
-  const int t = threadIdx.x, i = t >> 3, g = t & 7;
+  const int t = threadIdx.x, i = t / kPotrfTPR, g = t % kPotrfTPR;
   if (t < NB) {
     int e = 0;
     if (t < kb) {
@@ -212,10 +215,10 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_inv_kernel(double* A, int
     sc[t] = e;
   }
   __syncthreads();
-  T X[8];
+  T X[kPotrfEPT];
 #pragma unroll
-  for (int m = 0; m < 8; m++) {
-    const int c = g + 8 * m;
+  for (int m = 0; m < kPotrfEPT; m++) {
+    const int c = g + kPotrfTPR * m;
     X[m] = AR::zero();
     if (i < kb && c <= i) {
       float2 u;
@@ -228,18 +231,15 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_inv_kernel(double* A, int
     T* cb = colbuf + (j & 1) * NB;
     T* rb = rowbuf + (j & 1) * NB;
     if (i < kb) {
-      if (g == (j & 7) && i >= j) {
+      if (g == j % kPotrfTPR && i >= j) {
         // the owner of column j: constant register indices only (no indexed registers)
+        static_assert(kPotrfEPT == 4, "one case per register below");
         T v;
-        switch (j >> 3) {
+        switch (j / kPotrfTPR) {
           case 0: v = X[0]; X[0] = AR::zero(); break;
           case 1: v = X[1]; X[1] = AR::zero(); break;
           case 2: v = X[2]; X[2] = AR::zero(); break;
-          case 3: v = X[3]; X[3] = AR::zero(); break;
-          case 4: v = X[4]; X[4] = AR::zero(); break;
-          case 5: v = X[5]; X[5] = AR::zero(); break;
-          case 6: v = X[6]; X[6] = AR::zero(); break;
-          default: v = X[7]; X[7] = AR::zero(); break;
+          default: v = X[3]; X[3] = AR::zero(); break;
         }
         // from here on the register accumulates Y[i][j] (0 below the diagonal of I)
         cb[i] = v;
@@ -247,8 +247,8 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_inv_kernel(double* A, int
       }
       if (i == j) {
 #pragma unroll
-        for (int m = 0; m < 8; m++)
-          if (g + 8 * m < j) rb[g + 8 * m] = X[m];
+        for (int m = 0; m < kPotrfEPT; m++)
+          if (g + kPotrfTPR * m < j) rb[g + kPotrfTPR * m] = X[m];
       }
     }
     __syncthreads();
@@ -259,11 +259,11 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_inv_kernel(double* A, int
     }
     if (i > j && i < kb) {
       const T a = AR::mul(cb[i], AR::rcp(d));
-      const int mmax = (i - g) >> 3;   // columns c = g + 8m <= i (floor division: none when i < g)
+      const int mmax = (i - g) >= 0 ? (i - g) / kPotrfTPR : -1;   // columns c = g + TPR m <= i
 #pragma unroll
-      for (int m = 0; m < 8; m++) {
+      for (int m = 0; m < kPotrfEPT; m++) {
         if (m > mmax) break;
-        const int c = g + 8 * m;
+        const int c = g + kPotrfTPR * m;
         // trailing: S[c][j] (column j); inverse: Y[j][c] (row j), with Y[j][j] = 1
         const T* src = (c > j) ? &cb[c] : &rb[c];
         const T v = (c == j) ? AR::one() : *src;
@@ -282,8 +282,8 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_inv_kernel(double* A, int
   double* Lk = Linv + (k0 / NB) * NB * NB;
   float2* Lf2 = LinvDF ? LinvDF + (k0 / NB) * NB * NB : nullptr;
 #pragma unroll
-  for (int m = 0; m < 8; m++) {
-    const int c = g + 8 * m;
+  for (int m = 0; m < kPotrfEPT; m++) {
+    const int c = g + kPotrfTPR * m;
     T v = AR::zero();
     if (i < kb && c <= i) v = (c == i) ? rs[i] : AR::mul(X[m], rs[i]);   // L'^{-1}[i][c] = Y[i][c] / sqrt(d_i)
     Lk[i * NB + c] = (i < kb && c <= i) ? AR::store_scaled(v, -sc[c]) : 0.0;
@@ -298,15 +298,15 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_inv_kernel(double* A, int
     if (fw) {
       T acc = AR::zero();
 #pragma unroll
-      for (int m = 0; m < 8; m++) {
-        const int c = g + 8 * m;
+      for (int m = 0; m < kPotrfEPT; m++) {
+        const int c = g + kPotrfTPR * m;
         if (i < kb && c <= i) {
           const T v = (c == i) ? rs[i] : AR::mul(X[m], rs[i]);
           acc = AR::add(acc, AR::mul(v, AR::load_scaled(fw[k0 + c], nullptr, -sc[c])));
         }
       }
 #pragma unroll
-      for (int o = 1; o < 8; o <<= 1) {
+      for (int o = 1; o < kPotrfTPR; o <<= 1) {
         const T other = {__shfl_xor_sync(0xffffffffu, acc.h, o), __shfl_xor_sync(0xffffffffu, acc.l, o)};
         acc = AR::add(acc, other);
       }
@@ -385,7 +385,8 @@ __global__ void __launch_bounds__(128) panel_solve_kernel(double* A, int64_t lda
 // The split path's panel solve in double-float arithmetic on the FP32 pipe
 // (about 48 significant bits, the precision of U and of the split GEMM):
 // L21 = (A21 - U21) D L'^{-T}, with L'^{-1} (LkDF) and the power-of-two scales
-// D = diag(2^-sc) from the diagonal factor.  Same tiling as the FP64 kernel;
+// D = diag(2^-sc) from the diagonal factor.  32 rows per CTA, 256 threads, 2 x 4 outputs
+// per thread (rows ty + 16a, columns tx + 16b), the same K segments as the FP64 kernel;
 // each product is the exact FP32 product of the high parts plus the cross
 // terms, its high part added exactly (TwoSum) and the low parts accumulated
 // in FP32, renormalised at the end.  Writes L21 in FP64 and its S BF16 slices
@@ -393,9 +394,12 @@ __global__ void __launch_bounds__(128) panel_solve_kernel(double* A, int64_t lda
 // row's own exponent over this panel's 64 columns in eout[r - row_base] (the
 // strip operand keeps one exponent array per panel).
 constexpr size_t kPanelDFSmem = (size_t)(kPanelRows + NB) * (NB + 1) * sizeof(float2);
+constexpr int kPanelDFThreads = 256;                       // 16 x 16: 2 rows x 4 columns per thread
+constexpr int kPanelDFRowStride = kPanelDFThreads / 16;    // rows ty + 16 a
+constexpr int kPanelDFRows = kPanelRows / kPanelDFRowStride;
 
 template <int S>
-__global__ void __launch_bounds__(128) panel_df_kernel(double* A, int64_t lda, int64_t k0, int kb, int64_t k1,
+__global__ void __launch_bounds__(kPanelDFThreads) panel_df_kernel(double* A, int64_t lda, int64_t k0, int kb, int64_t k1,
                                                        int64_t n, const float2* __restrict__ U, int64_t ldu,
                                                        const float2* __restrict__ LkDF, const int* __restrict__ sck,
                                                        __nv_bfloat16* slices, int* eout, int64_t row_base,
@@ -447,9 +451,9 @@ __global__ void __launch_bounds__(128) panel_df_kernel(double* A, int64_t lda, i
     As[rr][q] = make_float2(h, l);
   }
   __syncthreads();
-  float ah[4][4], al[4][4];
+  float ah[kPanelDFRows][4], al[kPanelDFRows][4];
 #pragma unroll
-  for (int a = 0; a < 4; a++)
+  for (int a = 0; a < kPanelDFRows; a++)
 #pragma unroll
     for (int b = 0; b < 4; b++) ah[a][b] = al[a][b] = 0.f;
 #pragma unroll
@@ -457,13 +461,13 @@ __global__ void __launch_bounds__(128) panel_df_kernel(double* A, int64_t lda, i
 #pragma unroll 2
     for (int tt = 0; tt < 16; tt++) {
       const int q = 16 * seg + tt;
-      float2 av[4], lv[4];
+      float2 av[kPanelDFRows], lv[4];
 #pragma unroll
-      for (int a = 0; a < 4; a++) av[a] = As[ty + 8 * a][q];
+      for (int a = 0; a < kPanelDFRows; a++) av[a] = As[ty + kPanelDFRowStride * a][q];
 #pragma unroll
       for (int b = seg; b < 4; b++) lv[b] = Lt[q][tx + 16 * b];
 #pragma unroll
-      for (int a = 0; a < 4; a++)
+      for (int a = 0; a < kPanelDFRows; a++)
 #pragma unroll
         for (int b = seg; b < 4; b++) {
           const float p = __fmul_rn(av[a].x, lv[b].x);
@@ -478,7 +482,7 @@ __global__ void __launch_bounds__(128) panel_df_kernel(double* A, int64_t lda, i
     }
   }
 #pragma unroll
-  for (int a = 0; a < 4; a++)
+  for (int a = 0; a < kPanelDFRows; a++)
 #pragma unroll
     for (int b = 0; b < 4; b++) {   // renormalise (Fast2Sum)
       const float hi = __fadd_rn(ah[a][b], al[a][b]);
@@ -488,7 +492,7 @@ __global__ void __launch_bounds__(128) panel_df_kernel(double* A, int64_t lda, i
   if (fw) {
     // forward substitution: w[r] -= L21[r][:] y_k, the 16 lanes of a row (a half warp) combining
 #pragma unroll
-    for (int a = 0; a < 4; a++) {
+    for (int a = 0; a < kPanelDFRows; a++) {
       DF acc = {0.f, 0.f};
 #pragma unroll
       for (int b = 0; b < 4; b++) {
@@ -503,13 +507,13 @@ __global__ void __launch_bounds__(128) panel_df_kernel(double* A, int64_t lda, i
         const DF other = {__shfl_xor_sync(0xffffffffu, acc.h, o), __shfl_xor_sync(0xffffffffu, acc.l, o)};
         acc = ArithDF::add(acc, other);
       }
-      const int64_t r = rb + ty + 8 * a;
+      const int64_t r = rb + ty + kPanelDFRowStride * a;
       if (tx == 0 && r < n) fw[r] = (fw[r] - (double)acc.h) - (double)acc.l;
     }
   }
 #pragma unroll
-  for (int a = 0; a < 4; a++) {
-    const int64_t r = rb + ty + 8 * a;
+  for (int a = 0; a < kPanelDFRows; a++) {
+    const int64_t r = rb + ty + kPanelDFRowStride * a;
     // row maximum over the 16 lanes holding this row (a half warp); |hi| suffices: with
     // 2^e > max |hi| the leading digit stays <= 2^8, exact in BF16
     float m = 0.f;
@@ -649,7 +653,7 @@ cudaError_t launch_panel_df(double* A, int64_t lda, int64_t k0, int kb, int64_t 
   if (e != cudaSuccess) return e;
   const int64_t blocks = (n - k1 + kPanelRows - 1) / kPanelRows;
   if (blocks <= 0) return cudaSuccess;
-  panel_df_kernel<S><<<(unsigned)blocks, 128, kPanelDFSmem, st>>>(A, lda, k0, kb, k1, n, U, ldu, LkDF, sck,
+  panel_df_kernel<S><<<(unsigned)blocks, kPanelDFThreads, kPanelDFSmem, st>>>(A, lda, k0, kb, k1, n, U, ldu, LkDF, sck,
                                                                   static_cast<__nv_bfloat16*>(op.slices), eout,
                                                                   row_base, op.npad, op.kpad, kofs, fyDF, fw,
                                                                   flag);
