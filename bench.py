@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--slices", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--micro", default=None, choices=[None, "gram", "chol"],
+    ap.add_argument("--micro", default=None, choices=[None, "gram", "chol", "jacobian"],
                     help="time one kernel family alone instead of the GN step (not the bench contract line)")
     ap.add_argument("--width", type=int, default=None,
                     help="--micro: hidden width w of a 1-w-w-1 CCF net (gram: default 44; chol: default the "
@@ -67,6 +67,8 @@ def parse():
                     choices=["ccf_unstable1", "ccf_stable", "ipm", "boussinesq", "batched"],
                     help="ccf_unstable1 is the headline line; the others print their own line")
     ap.add_argument("--streams", type=int, default=8, help="--workload batched: CUDA streams (host workers)")
+    ap.add_argument("--radii", type=int, default=None,
+                    help="--micro jacobian on a 2D workload: radii x angles of a smaller point set (default: full)")
     return ap.parse_args()
 
 
@@ -235,6 +237,69 @@ def micro_gram(args):
         out["tensor_tflops_incl_prepass"] = executed / (ms * 1e-3) / 1e12
     print(json.dumps(out))
     prob.close()
+    return 0
+
+
+def micro_jacobian(args):
+    """The fused jet -> residual -> Jacobian-row kernel alone (gn_jacobian over all rows) and
+    the residual-only pass of the line search (gn_residual), timed with CUDA events on the
+    handle's stream.  Algorithmic bytes of the Jacobian pass: rows * P' * 8 written (the
+    J~ rows; inputs and weights are O(N + P)).  For CCF the pass also holds the Hilbert node
+    jets and the J_U contraction, so a Burgers problem on the same network and points (no
+    nonlocal term) is timed beside it: that line is the jet kernel alone.  Prints one JSON
+    line (not the bench contract line); with --steps 1 --warmup 0 it is the small case of
+    the jet-kernel ncu captures."""
+    import torch
+    from paper_2509_14185_gb300 import build as B
+    B.build()
+    from paper_2509_14185_gb300 import gn, inputs
+    w = inputs.WORKLOADS[args.workload]()
+    if args.radii and w.d == 2:
+        seed = inputs.WORKLOADS[args.workload].__defaults__[0]
+        w.y = inputs.points_2d_polar(args.radii, args.radii, 1e-3, 1e3, seed)
+        w.y_bnd = inputs.wall_points(max(1, args.radii * args.radii // 16), 1e-3, 1e3, seed)
+        w.name = w.name + f"_reduced_{args.radii}x{args.radii}"
+    hbm, hsrc = measured_peak("hbm_gbs", 6800.0)
+    cases = [(w.name, w.equation)]
+    if w.equation == inputs.CCF:
+        cases.append((w.name.replace("ccf", "burgers_same_net_and_points"), inputs.BURGERS))
+    prec = {"fp64": gn.GN_PREC_FP64, "split": gn.GN_PREC_SPLIT_BF16, "split_all": gn.GN_PREC_SPLIT_ALL}[args.precision]
+    out = {"micro": "jacobian", "hbm_peak_gbs": hbm, "peak_source": hsrc, "precision": args.precision, "cases": []}
+    for name, eq in cases:
+        prob = gn.GNProblem(eq, w.widths, w.y, w.y_bnd if w.y_bnd.size else None, w.rho, y_norm=w.y_norm,
+                            c_norm=w.c_norm, hilbert_m=w.hilbert_m, precision=prec, n_slices=args.slices)
+        Pp = prob.P + 1
+        theta = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
+        J = torch.empty((prob.n_rows, Pp), dtype=torch.float64, device="cuda")
+        r = prob.new_vec(prob.n_rows)
+        stream = torch.cuda.current_stream()
+
+        def timed(fn):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(max(1, args.steps)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            return statistics.median(ts)
+
+        ms_j = timed(lambda: prob.gn_jacobian(theta, w.lam, J))
+        ms_r = timed(lambda: prob.gn_residual(theta, w.lam, r, want_loss=False))
+        jbytes = prob.n_rows * Pp * 8.0
+        gbs = jbytes / (ms_j * 1e-3) / 1e9
+        out["cases"].append({"case": name, "rows": prob.n_rows, "cols": Pp, "n_pts": prob.n_pts,
+                             "jacobian_ms": ms_j, "jacobian_bytes_written": jbytes, "jacobian_gbs": gbs,
+                             "jacobian_frac_hbm": gbs / hbm, "residual_ms": ms_r,
+                             "residual_points_per_s": prob.n_pts / (ms_r * 1e-3),
+                             "includes_hilbert": eq == inputs.CCF})
+        del J
+        prob.close()
+    print(json.dumps(out))
     return 0
 
 
@@ -644,6 +709,8 @@ def main():
         return micro_gram(args)
     if args.micro == "chol":
         return micro_chol(args)
+    if args.micro == "jacobian":
+        return micro_jacobian(args)
     if args.equal_residual:
         return equal_residual(args)
     if args.workload == "batched":
