@@ -67,6 +67,9 @@ def parse():
                     choices=["ccf_unstable1", "ccf_stable", "ipm", "boussinesq", "batched"],
                     help="ccf_unstable1 is the headline line; the others print their own line")
     ap.add_argument("--streams", type=int, default=8, help="--workload batched: CUDA streams (host workers)")
+    ap.add_argument("--graph", action="store_true",
+                    help="step through the captured CUDA graphs (gn_step_graph; batched: one graph launch per "
+                         "batched step, gn_batch_graph_step)")
     ap.add_argument("--radii", type=int, default=None,
                     help="--micro jacobian on a 2D workload: radii x angles of a smaller point set (default: full)")
     return ap.parse_args()
@@ -635,8 +638,13 @@ def run_batched(args):
     thetas = [torch.tensor(w.theta, dtype=torch.float64, device="cuda") for w in fits]
     lams = [w.lam for w in fits]
     gams = [w.gamma for w in fits]
+    if args.graph:
+        batch.gn_batch_capture_graph(thetas)
+        step = lambda l, g: batch.gn_batch_graph_step(l, g)
+    else:
+        step = lambda l, g: batch.gn_batch_step(thetas, l, g)
     for _ in range(args.warmup):
-        lams, gams, infos, st = batch.gn_batch_step(thetas, lams, gams)
+        lams, gams, infos, st = step(lams, gams)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -649,7 +657,7 @@ def run_batched(args):
     statuses = []
     ev0.record(stream)
     for _ in range(args.steps):
-        lams, gams, infos, st = batch.gn_batch_step(thetas, lams, gams)
+        lams, gams, infos, st = step(lams, gams)
         statuses.append(st)
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -681,7 +689,9 @@ def run_batched(args):
         line = {"metric": "gn_fit_steps_per_s", "value": value, "unit": "fit-steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"batched_ccf_sweep_{n}_fits", "fits": n, "streams": args.streams,
+                "config": {"workload": f"batched_ccf_sweep_{n}_fits", "fits": n,
+                           "launch": "one CUDA graph launch per batched step (every fit a branch)" if args.graph
+                           else f"{args.streams} streams, one host worker thread each",
                            "params_range": [min(Pps), max(Pps)], "n_pts_range": [min(rows) - 1, max(rows) - 1],
                            "gram_precision": args.precision if args.precision == "fp64"
                            else f"split_bf16_s{args.slices}",
@@ -736,8 +746,9 @@ def main():
     stream = torch.cuda.current_stream()
     theta = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
     lam, gam = w.lam, w.gamma
+    gn_step = prob.gn_step_graph if args.graph else prob.gn_step
     for _ in range(args.warmup):
-        rc, lam, gam, info = prob.gn_step(theta, lam, gam)
+        rc, lam, gam, info = gn_step(theta, lam, gam)
         if rc < 0:
             raise RuntimeError(f"gn_step failed in warm-up: {rc}")
     torch.cuda.synchronize()
@@ -757,7 +768,7 @@ def main():
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         for _ in range(args.steps):
-            rc, lam, gam, info = prob.gn_step(theta, lam, gam)
+            rc, lam, gam, info = gn_step(theta, lam, gam)
             if rc < 0:
                 raise RuntimeError(f"gn_step failed: {rc}")
             infos.append(info)
@@ -773,7 +784,7 @@ def main():
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             l0 = L.gn_kernel_launches()
             ev0.record(stream)
-            rc, lam, gam, info = prob.gn_step(theta, lam, gam)
+            rc, lam, gam, info = gn_step(theta, lam, gam)
             ev1.record(stream)
             launches += L.gn_kernel_launches() - l0
             if rc < 0:
@@ -788,8 +799,20 @@ def main():
         dist.barrier()
     value = world * 1000.0 / ms
 
-    # per-phase device times (library CUDA events on the launch stream, averaged over the timed steps)
-    phases = [statistics.mean(i["ms_phase"][k] for i in infos) for k in range(7)]
+    # per-phase device times (library CUDA events on the launch stream, averaged over the timed steps);
+    # a captured graph is timed as a whole, so its phases come from eager steps of the same kernels
+    # on a copy of the parameters, after the timed region
+    phase_src = "timed steps"
+    if args.graph:
+        th2 = theta.clone()
+        l2, g2, pinfos = lam, gam, []
+        for _ in range(max(2, min(args.steps, 5))):
+            rc2, l2, g2, i2 = prob.gn_step(th2, l2, g2)
+            pinfos.append(i2)
+        phases = [statistics.mean(i["ms_phase"][k] for i in pinfos) for k in range(7)]
+        phase_src = f"{len(pinfos)} eager gn_step calls after the timed region (same kernels as the graph)"
+    else:
+        phases = [statistics.mean(i["ms_phase"][k] for i in infos) for k in range(7)]
     kernels = kernel_report(prob, args, phases)
     # the roofline object describes the largest single kernel, the Gram launch (the Cholesky
     # phase is a chain of several kernels and is reported beside it under "kernels")
@@ -806,7 +829,7 @@ def main():
         lam2, gam2 = lam, gam
         for _ in range(args.steps):
             theta.copy_(th_host, non_blocking=True)
-            rc, lam2, gam2, info2 = prob.gn_step(theta, lam2, gam2)
+            rc, lam2, gam2, info2 = gn_step(theta, lam2, gam2)
             out_host.copy_(theta, non_blocking=True)
             th_host.copy_(out_host)
         e1.record(stream)
@@ -836,7 +859,8 @@ def main():
                 "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches),
                 "phase_ms": {"jacobian": phases[0], "gram": phases[1], "factor": phases[3], "solve": phases[4],
-                             "line_search": phases[5], "total": phases[6]},
+                             "line_search": phases[5], "total": phases[6], "source": phase_src},
+                "step_call": "gn_step_graph (captured CUDA graphs)" if args.graph else "gn_step",
                 "final": {"loss": infos[-1]["loss_after"], "lambda": lam, "damping": gam,
                           "trials": [i["n_trials"] for i in infos]}}
         print(json.dumps(line))

@@ -211,6 +211,22 @@ int gn_damped_solve(gn_handle* h, const double* G, const double* g, double* gamm
  * library's choice because the paper gives none. */
 int gn_step(gn_handle* h, double* theta, double* lambda, double* damping, gn_step_info* info);
 
+/* The step of gn_step with every host decision moved onto the device, captured
+ * once as CUDA graphs and replayed: the factorisation check, the Armijo
+ * backtracking (eight conditional IF nodes, one residual-only trial each) and
+ * the Levenberg-Marquardt update read and write a device-resident state holding
+ * lambda and the damping, so one step is one graph launch plus one small copy
+ * each way and one synchronisation.  Same arguments, results, constants and
+ * return codes as gn_step (a failed factorisation replays the solve part with
+ * damping x10, at most 5 times).  The first call for a given theta address (or
+ * after gn_set_precision or a change of the lambda setting) captures the
+ * graphs: it grows the handle's workspace to its final size and synchronises;
+ * make that first call before any stream capture of your own.  The graphs run
+ * on a stream of the handle's own, after the work already queued on the
+ * handle's stream.  info->ms_phase[6] is the step's device time; the other
+ * phases are not timed.  Cites: Methods, "Second-order Optimizer". */
+int gn_step_graph(gn_handle* h, double* theta, double* lambda, double* damping, gn_step_info* info);
+
 /* ---- batched fits ---------------------------------------------------------- */
 /* Many independent profile fits of uneven size (lambda seeds, widths, depths,
  * point counts), as in the paper's sweeps over lambda and seeds (Methods,
@@ -231,6 +247,24 @@ int gn_batch_handle(gn_batch* b, int fit, gn_handle** out);
 int gn_batch_step(gn_batch* b, double* const* thetas, double* lambdas, double* dampings, gn_step_info* infos,
                   int* status);
 int gn_batch_destroy(gn_batch* b);
+
+/* Graph mode of a batch: one CUDA graph holds every fit's whole damped GN step
+ * (gn_step_graph's device-resident step, each fit an independent branch), so a
+ * batched step is a single cudaGraphLaunch.  gn_batch_capture_graph captures it
+ * for the parameter buffers thetas (host array of n_fits device pointers, in
+ * place like gn_step; the addresses are part of the graph, so capture again
+ * after changing any of them or any fit's precision or lambda setting) and
+ * allocates the per-fit device states, capture streams and each fit's
+ * workspace; it synchronises the device and must not be called while the
+ * batch's fits have work in flight.  gn_batch_graph_step then runs one step of
+ * every fit from the host values lambdas, dampings (in/out, as gn_batch_step);
+ * a fit whose factorisation fails is retried with damping x10 by replaying its
+ * own solve graph (at most 5 times).  infos, status as gn_batch_step (ms_phase
+ * is not filled).  Returns GN_ERR_INVALID when no graph was captured.  Cites:
+ * the paper's sweeps over lambda seeds and architectures (Methods,
+ * "Identifying Admissible lambda Values"). */
+int gn_batch_capture_graph(gn_batch* b, double* const* thetas);
+int gn_batch_graph_step(gn_batch* b, double* lambdas, double* dampings, gn_step_info* infos, int* status);
 
 /* One step of the paper's own optimiser (Methods, "Second-order Optimizer"): G is
  * estimated by an exponential moving average over iterations of the unbiased rank-1

@@ -732,6 +732,33 @@ cudaError_t cholesky_factor(double* A, int64_t n, int64_t lda, double* Linv, int
 // *rc_out receives a GN_ERR_* code on failure.
 constexpr int64_t kStrip = 4 * NB;
 
+// Split workspace of cholesky_factor_split: U (n x n double-FP32), two strip operands
+// (slices and four exponent arrays each), the double-float diagonal inverses, their
+// scales and the double-float forward-solve block.
+size_t chol_split_ws_bytes(int64_t n, int S) {
+  auto rup = [](int64_t v, int64_t m) { return (v + m - 1) / m * m; };
+  const int64_t npad0 = rup(n, 128);
+  const size_t ub = rup((int64_t)n * n * sizeof(float2), 256);
+  const size_t sb = rup((int64_t)S * npad0 * kStrip * 2, 256);
+  const int64_t estride = npad0 + 1024;
+  const size_t eb = rup(4 * estride * sizeof(int), 256);
+  const int64_t nblk = (n + NB - 1) / NB;
+  const size_t lb = rup(nblk * NB * NB * sizeof(float2), 256);
+  const size_t cb = rup(nblk * NB * sizeof(int), 256);
+  const size_t yb = rup(NB * sizeof(float2), 256);
+  return ub + 2 * (sb + eb) + lb + cb + yb + 256;
+}
+
+// The look-ahead's two streams (critical path at high priority, deferred bulk updates at low).
+cudaError_t ensure_chol_streams(gn_handle* h) {
+  if (h->st_hi) return cudaSuccess;
+  int least = 0, greatest = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->st_hi, cudaStreamNonBlocking, greatest);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->st_lo, cudaStreamNonBlocking, least);
+  return e;
+}
+
 cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t lda, double* Linv, int* flag, int S,
                                   const double* b, double* y, double* w, int* rc_out) {
   cudaStream_t st = h->st;
@@ -745,8 +772,7 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
   const int64_t nblk = (n + NB - 1) / NB;
   const size_t lb = rup(nblk * NB * NB * sizeof(float2), 256);
   const size_t cb = rup(nblk * NB * sizeof(int), 256);
-  const size_t yb = rup(NB * sizeof(float2), 256);
-  int rc = ensure_split_ws(h, ub + 2 * (sb + eb) + lb + cb + yb + 256);
+  int rc = ensure_split_ws(h, chol_split_ws_bytes(n, S));
   if (rc) {
     *rc_out = rc;
     return cudaErrorMemoryAllocation;
@@ -757,11 +783,8 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
   float2* LinvDF = reinterpret_cast<float2*>(base + ub + 2 * (sb + eb));
   int* scales = reinterpret_cast<int*>(base + ub + 2 * (sb + eb) + lb);
   float2* yDF = reinterpret_cast<float2*>(base + ub + 2 * (sb + eb) + lb + cb);
-  if (!h->st_hi) {
-    int least = 0, greatest = 0;
-    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->st_hi, cudaStreamNonBlocking, greatest);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->st_lo, cudaStreamNonBlocking, least);
+  {
+    const cudaError_t e = ensure_chol_streams(h);
     if (e != cudaSuccess) return e;
   }
   cudaStream_t sh = h->st_hi, sl = h->st_lo;

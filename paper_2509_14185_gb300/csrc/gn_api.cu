@@ -76,15 +76,11 @@ void free_all(gn_handle* h) {
 }
 
 // Device copy of the normalisation point: red[512 .. 513].
-struct Pass {
-  int mode;
-  double* r;        // r~ destination (may be null)
-  double* J;        // Jacobian block destination
-  int64_t ldJ, jlo, jhi;
-  const double* seed;
-};
-
 double* norm_point(gn_handle* h) { return h->red + 512; }
+
+}  // namespace
+
+namespace gn {
 
 // Evaluate rows (all kinds) at (theta, lambda) in one mode.  In gradient mode
 // the per-warp partials are reduced into grad (P+1 entries).
@@ -98,6 +94,7 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
   a.theta = theta;
   a.wt = h->wt;
   a.lam = lam;
+  a.lamp = ps.lamp;
   a.flag = h->flag;
   a.ldg = round_up(h->Pp, 16);
   a.gpart = h->gpart;
@@ -263,6 +260,10 @@ int gram_into(gn_handle* h, const double* J, int64_t ld, int64_t nrows, const do
   return GN_OK;
 }
 
+}  // namespace gn
+
+namespace {
+
 struct Timer {
   cudaEvent_t ev[9];
   int n = 0;
@@ -406,6 +407,7 @@ int gn_init(const gn_problem* p, void* cuda_stream, gn_handle** out) {
 int gn_destroy(gn_handle* h) {
   if (!h) return GN_OK;
   cudaStreamSynchronize(h->st);
+  graph_release(h);
   if (h->st_hi) cudaStreamDestroy(h->st_hi);
   if (h->st_lo) cudaStreamDestroy(h->st_lo);
   free_all(h);

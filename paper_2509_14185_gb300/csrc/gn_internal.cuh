@@ -53,6 +53,7 @@ struct JetArgs {
   const double* theta;   // [P]
   const double* wt;      // transposed weights
   double lam;
+  const double* lamp;    // device copy of lambda (null: use lam); graph-captured steps read it here
   int64_t n;             // points of this kind
   const double* y;       // SoA [d][ystride]
   int64_t ystride;
@@ -74,6 +75,7 @@ struct JetArgs {
 };
 
 struct Workspace;
+struct GraphState;     // CUDA graphs of the device-resident step (graph.cu)
 
 }  // namespace gn
 
@@ -124,9 +126,34 @@ struct gn_handle {
   // streams of the split factorisation's look-ahead (created on first use)
   cudaStream_t st_hi = nullptr;   // critical path (high priority)
   cudaStream_t st_lo = nullptr;   // deferred bulk updates (low priority)
+  // graph-captured step (created on first use of gn_step_graph or by a batch capture)
+  gn::GraphState* gs = nullptr;
+  int capturing = 0;              // a stream capture is in progress: no workspace may grow
+  int lam_frozen = 0;             // lambda held fixed (funnel inference trains at fixed lambda)
 };
 
 namespace gn {
+
+// One evaluation pass over all point kinds (gn_api.cu).
+struct Pass {
+  int mode;
+  double* r;        // r~ destination (may be null)
+  double* J;        // Jacobian block destination
+  int64_t ldJ, jlo, jhi;
+  const double* seed;
+  const double* lamp = nullptr;   // device lambda (null: the host value passed to run_pass)
+};
+int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, double* grad);
+// 1/2 |r|^2 reduction: the sum of squares lands in red[256 + slot] (device)
+int loss_of(gn_handle* h, const double* r, int slot);
+int gram_into(gn_handle* h, const double* J, int64_t ld, int64_t nrows, const double* r, double* G, double* g,
+              int precision, int accumulate);
+// grow the split workspace to what every split contraction of a step needs, and create the
+// factorisation's streams, so that a captured step allocates nothing
+int prepare_for_capture(gn_handle* h);
+size_t chol_split_ws_bytes(int64_t n, int S);
+cudaError_t ensure_chol_streams(gn_handle* h);
+void graph_release(gn_handle* h);
 
 // ---- launchers (host functions implemented in the .cu files) -----------
 cudaError_t launch_transpose_weights(const NetDesc& net, const double* theta, double* wt, cudaStream_t st);

@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
   const int64_t gw = (int64_t)blockIdx.x * wpb + warp;
   const int64_t nw = (int64_t)gridDim.x * wpb;
   double* gp = (MODE == MODE_GRADIENT) ? A.gpart + gw * A.ldg : nullptr;
-  const double lam = A.lam;
+  const double lam = A.lamp ? *A.lamp : A.lam;
   const int K = 1 + NF * CR;                  // tangent directions in use
   const int dir = (lane < K) ? lane : 0;      // this lane's direction
 

@@ -739,12 +739,37 @@ int oz_gemm(int S, bool sym, const OzOperand& A, const OzOperand& B, int64_t M, 
 
 int ensure_split_ws(gn_handle* h, size_t need) {
   if (h->split_ws_bytes >= need) return GN_OK;
+  if (h->capturing) {   // prepare_for_capture sized it; growing now would allocate inside a capture
+    set_detail(__FILE__, __LINE__, "split workspace would grow during a graph capture");
+    return GN_ERR_UNSUPPORTED;
+  }
   if (h->split_ws) cudaFree(h->split_ws);   // synchronises: no kernel still reads it
   h->split_ws = nullptr;
   h->split_ws_bytes = 0;
   if (GN_NOTE(cudaMalloc(&h->split_ws, need)) != cudaSuccess) return GN_ERR_OOM;
   h->split_ws_bytes = need;
   return GN_OK;
+}
+
+// Everything a step's split contractions need, allocated up front: the Gram operand of the
+// largest row block, the CCF Hilbert contraction's operands (SPLIT_ALL) and the split
+// factorisation's workspace and streams (SPLIT_ALL).
+int prepare_for_capture(gn_handle* h) {
+  if (h->precision == GN_PREC_FP64) return GN_OK;
+  const int S = h->n_slices;
+  size_t need = oz_operand_bytes(S, h->Pp, h->jrows) + (size_t)CM_CHUNKS * rup(h->Pp, TM) * 8 + 256;
+  if (h->precision == GN_PREC_SPLIT_ALL) {
+    if (h->eq == GN_CCF && h->p.n_pts > 0) {
+      const int64_t rows = h->p.n_pts < h->jrows ? h->p.n_pts : h->jrows;
+      const size_t hil = oz_operand_bytes(S, rows, h->Mh) + oz_operand_bytes(S, h->Pp, h->Mh) +
+                         (size_t)64 * rup(h->Pp, 128) * 8 + 512;
+      if (hil > need) need = hil;
+    }
+    const size_t ch = chol_split_ws_bytes(h->Pp, S);
+    if (ch > need) need = ch;
+    if (GN_NOTE(ensure_chol_streams(h)) != cudaSuccess) return GN_ERR_CUDA;
+  }
+  return ensure_split_ws(h, need);
 }
 
 // Gram through the split GEMM: G (lower tiles) = J^T J or += (accumulate).

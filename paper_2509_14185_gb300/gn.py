@@ -104,6 +104,9 @@ EXPORTS = {
     "gn_batch_handle": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
     "gn_batch_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "gn_batch_destroy": (ctypes.c_int, [_P]),
+    "gn_step_graph": (ctypes.c_int, [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(gn_step_info)]),
+    "gn_batch_capture_graph": (ctypes.c_int, [_P, _P]),
+    "gn_batch_graph_step": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "gn_kernel_launches": (ctypes.c_int64, []),
     "gn_last_error_detail": (ctypes.c_char_p, []),
     "gn_error_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -253,6 +256,16 @@ class GNProblem:
             _check(rc, "gn_step")
         return rc, lam_.value, gam_.value, info.as_dict()
 
+    def gn_step_graph(self, theta, lam, gamma):
+        """gn_step through the handle's captured CUDA graphs (captured on the first call for theta)."""
+        lam_ = _D(lam)
+        gam_ = _D(gamma)
+        info = gn_step_info()
+        rc = lib().gn_step_graph(self.h, _ptr(theta), ctypes.byref(lam_), ctypes.byref(gam_), ctypes.byref(info))
+        if rc < 0 and rc not in (GN_ERR_NOT_SPD, GN_ERR_NONFINITE):
+            _check(rc, "gn_step_graph")
+        return rc, lam_.value, gam_.value, info.as_dict()
+
     def gn_step_ema(self, theta, lam, gamma, G_ema, v_prev, signs, beta, first):
         """The paper's EMA rank-1 optimiser: theta, G_ema, v_prev updated in place."""
         lam_ = _D(lam)
@@ -383,6 +396,24 @@ class GNBatch:
         torch.cuda.synchronize(self.device)     # the batch's streams do not wait on torch's
         rc = lib().gn_batch_step(self.b, ptrs, lam, gam, infos, st)
         _check(rc if rc < 0 and rc not in (GN_ERR_NOT_SPD, GN_ERR_NONFINITE) else 0, "gn_batch_step")
+        return list(lam), list(gam), [infos[i].as_dict() for i in range(self.n)], list(st)
+
+    def gn_batch_capture_graph(self, thetas):
+        """Capture every fit's step into one CUDA graph for these parameter tensors."""
+        self._graph_thetas = list(thetas)
+        ptrs = (ctypes.c_void_p * self.n)(*[t.data_ptr() for t in thetas])
+        torch.cuda.synchronize(self.device)
+        _check(lib().gn_batch_capture_graph(self.b, ptrs), "gn_batch_capture_graph")
+
+    def gn_batch_graph_step(self, lambdas, dampings):
+        """One step of every fit as one graph launch (on the tensors given to gn_batch_capture_graph)."""
+        lam = (ctypes.c_double * self.n)(*lambdas)
+        gam = (ctypes.c_double * self.n)(*dampings)
+        infos = (gn_step_info * self.n)()
+        st = (ctypes.c_int * self.n)()
+        torch.cuda.synchronize(self.device)
+        rc = lib().gn_batch_graph_step(self.b, lam, gam, infos, st)
+        _check(rc if rc < 0 and rc not in (GN_ERR_NOT_SPD, GN_ERR_NONFINITE) else 0, "gn_batch_graph_step")
         return list(lam), list(gam), [infos[i].as_dict() for i in range(self.n)], list(st)
 
     def close(self):
