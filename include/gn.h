@@ -152,6 +152,18 @@ int gn_row_count(const gn_handle* h, int64_t* n_rows);
 /* Change the Gram precision used by gn_step and gn_gram. */
 int gn_set_precision(gn_handle* h, int precision, int n_slices);
 
+/* Split-K factor of the split-precision Gram (the contraction over rows cut into ksplit
+ * parts over ksplit times more CTAs, partial tiles summed in a fixed order by a second
+ * launch).  ksplit = 0 (default): autotuned: on the first split Gram of a shape (slices,
+ * column tiles, contraction chunks) in the process, every candidate (1 and the splits that
+ * keep the launch within four waves of the 152 SMs and at least 256 rows per part) is
+ * timed with CUDA events on the handle's stream and the fastest kept for every handle of
+ * that shape; the tuning launch synchronises the stream.  ksplit = 1..8 forces a factor.
+ * The split changes only the order of the final FP64 additions.  GN_ERR_INVALID otherwise.
+ * gn_gram_split_choice reports the factor a Gram over nrows rows uses (0: not tuned yet). */
+int gn_set_gram_split(gn_handle* h, int ksplit);
+int gn_gram_split_choice(const gn_handle* h, int64_t nrows, int* ksplit);
+
 /* ---- evaluation --------------------------------------------------------- */
 
 /* r_out[0..n_rows) = r~(theta, lambda); *loss_out (host, may be NULL) = h = |r~|^2/2.

@@ -437,6 +437,18 @@ int gn_set_precision(gn_handle* h, int precision, int n_slices) {
   return GN_OK;
 }
 
+int gn_set_gram_split(gn_handle* h, int ksplit) {
+  if (!h || ksplit < 0 || ksplit > 8) return GN_ERR_INVALID;
+  h->gram_ksplit = ksplit;
+  return GN_OK;
+}
+
+int gn_gram_split_choice(const gn_handle* h, int64_t nrows, int* ksplit) {
+  if (!h || !ksplit || nrows < 0) return GN_ERR_INVALID;
+  *ksplit = h->gram_ksplit > 0 ? h->gram_ksplit : gram_split_choice(h->n_slices, h->Pp, nrows);
+  return GN_OK;
+}
+
 int gn_residual(gn_handle* h, const double* theta, double lambda, double* r_out, double* loss_out) {
   if (!h || !theta) return GN_ERR_INVALID;
   double* r = r_out ? r_out : h->r;

@@ -130,6 +130,7 @@ struct gn_handle {
   gn::GraphState* gs = nullptr;
   int capturing = 0;              // a stream capture is in progress: no workspace may grow
   int lam_frozen = 0;             // lambda held fixed (funnel inference trains at fixed lambda)
+  int gram_ksplit = 0;            // split-K factor of the split Gram (0: autotuned per shape)
 };
 
 namespace gn {
@@ -152,6 +153,8 @@ int gram_into(gn_handle* h, const double* J, int64_t ld, int64_t nrows, const do
 // factorisation's streams, so that a captured step allocates nothing
 int prepare_for_capture(gn_handle* h);
 size_t chol_split_ws_bytes(int64_t n, int S);
+// split-K factor the Gram autotuner recorded for this shape (0: not tuned yet)
+int gram_split_choice(int S, int64_t Pp, int64_t nrows);
 cudaError_t ensure_chol_streams(gn_handle* h);
 void graph_release(gn_handle* h);
 
@@ -249,8 +252,11 @@ int oz_prepare_rows(int S, const double* X, int64_t ld, int64_t n, int64_t k, co
                     cudaStream_t st);
 // C (M x N, ldc) op= A B^T; sym: only tiles with row tile >= column tile (A must equal B);
 // mode 0: C = v, 1: C += rowscale[i] v (rowscale may be null), 2: C -= v.  flag: bit 1 on timeout.
+// ksplit > 1 (modes 0-2, single exponents only): the contraction is cut into ksplit parts
+// over that many more CTAs, whose partial tiles (part: tiles * ksplit * 128 * 128 float2)
+// are summed by a second launch.
 int oz_gemm(int S, bool sym, const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, double* C, int64_t ldc,
-            int mode, const double* rowscale, int* flag, cudaStream_t st);
+            int mode, const double* rowscale, int* flag, cudaStream_t st, int ksplit = 1, void* part = nullptr);
 // Gram through oz_gemm (lower tiles); returns GN_ERR_* codes.
 int split_gram(gn_handle* h, const double* J, int64_t ld, int64_t nrows, double* G, int accumulate);
 // grow the handle's split workspace to at least `need` bytes

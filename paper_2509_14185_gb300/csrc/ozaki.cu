@@ -42,6 +42,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "gn_internal.cuh"
 
@@ -192,6 +196,11 @@ struct OzArgs {
   int mode;               // 0: C = v, 1: C += rs_i v, 2: C -= v, 3: C2 += v in double-FP32 (FP32 pipe)
   const double* rowscale; // mode 1 (may be null: 1)
   int* flag;
+  // split-K: CTA b works on tile b / ksplit, flush chunks [(b % ksplit) cps, + cps) of the
+  // contraction, and writes its unscaled (hi, lo) tile to part (null: no split, epilogue in place)
+  int ksplit;
+  int cps;
+  float2* part;
 };
 
 // ---------------------------------------------------------------------------
@@ -217,19 +226,27 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t ti, tj;
+  const int64_t tb = blockIdx.x / p.ksplit;   // output tile
+  const int ksp = (int)(blockIdx.x % p.ksplit);
   if (SYM) {  // lower-triangular tile ti >= tj
-    const int64_t t = blockIdx.x;
+    const int64_t t = tb;
     ti = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
     while ((ti + 1) * (ti + 2) / 2 <= t) ti++;
     while (ti * (ti + 1) / 2 > t) ti--;
     tj = t - ti * (ti + 1) / 2;
   } else {
-    ti = blockIdx.x / p.nt;
-    tj = blockIdx.x % p.nt;
+    ti = tb / p.nt;
+    tj = tb % p.nt;
   }
-  const int nk = (int)(p.Kpad / BKS);
   const int spc = CH ? p.spc : SPC;   // a compile-time constant on the single-exponent path
-  const int nchunk = (nk + spc - 1) / spc;
+  // this CTA's part of the contraction: flush chunks [c0, c0 + nchunk), stages [kt0, kt0 + nk)
+  const int nk_all = (int)(p.Kpad / BKS);
+  const int nchunk_all = (nk_all + spc - 1) / spc;
+  const int c0 = ksp * p.cps;
+  const int c1 = (c0 + p.cps < nchunk_all) ? c0 + p.cps : nchunk_all;
+  const int kt0 = c0 * spc;
+  const int nk = ((c1 * spc < nk_all) ? c1 * spc : nk_all) - kt0;
+  const int nchunk = c1 - c0;
   int* flag = p.flag;
 
   if (threadIdx.x == 0) {
@@ -271,8 +288,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         mbar_expect_tx(&full[st], STAGE_BYTES);
 #pragma unroll
         for (int s = 0; s < S; s++) {
-          tma_load_2d(base + s * SLICE_BYTES, &tmA, kt * BKS, (int)(s * p.rowsA) + rowA, &full[st]);
-          tma_load_2d(base + (S + s) * SLICE_BYTES, &tmB, kt * BKS, (int)(s * p.rowsB) + rowB, &full[st]);
+          tma_load_2d(base + s * SLICE_BYTES, &tmA, (kt0 + kt) * BKS, (int)(s * p.rowsA) + rowA, &full[st]);
+          tma_load_2d(base + (S + s) * SLICE_BYTES, &tmB, (kt0 + kt) * BKS, (int)(s * p.rowsB) + rowB, &full[st]);
         }
         issued = kt + 1;
       }
@@ -351,7 +368,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if constexpr (CH) {
         // this chunk's exponents (double buffered: every thread has passed the previous
         // chunk's barrier, so nobody still reads the buffer of chunk c - 2)
-        const int ev = (qcol == 0) ? p.eA[c * p.estride + ti * TM + row] : p.eB[c * p.estride + tj * TN + row];
+        const int ev = (qcol == 0) ? p.eA[(c0 + c) * p.estride + ti * TM + row]
+                                   : p.eB[(c0 + c) * p.estride + tj * TN + row];
         eccf[c & 1][qcol][row] = pow2f(ev);
         asm volatile("bar.sync 1, 256;" ::: "memory");
       }
@@ -409,7 +427,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int i = 0; i < EC; i++) park[row * (TN + 1) + qcol * EC + i] = make_float2(hi[i], lo[i]);
     }
     asm volatile("bar.sync 1, 256;" ::: "memory");
-    if (ok) {
+    if (ok && p.part) {
+      // split-K partial: the unscaled (hi, lo) tile, coalesced; oz_splitk_reduce finishes it
+      const int et = (warp - 2) * 32 + lane;
+      float2* dst = p.part + (size_t)blockIdx.x * (TM * TN);
+      for (int idx = et; idx < TM * TN; idx += 256) dst[idx] = park[(idx / TN) * (TN + 1) + (idx % TN)];
+    } else if (ok) {
       // 64 elements per thread, in batches of 8 whose global loads are issued
       // together (a load-modify-store loop would expose one memory latency per element)
       const int et = (warp - 2) * 32 + lane;
@@ -465,6 +488,39 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
+// Split-K epilogue: C_ij op= 2^(e_i + e_j) sum_ks (hi + lo)_ks, the partial tiles summed in
+// split order (deterministic), then the same store / add / subtract as the fused epilogue.
+template <bool SYM>
+__global__ void __launch_bounds__(256) oz_splitk_reduce(const float2* __restrict__ part, int ksplit, OzArgs p) {
+  const int64_t tb = blockIdx.x;
+  int64_t ti, tj;
+  if (SYM) {
+    ti = (int64_t)((sqrt(8.0 * (double)tb + 1.0) - 1.0) * 0.5);
+    while ((ti + 1) * (ti + 2) / 2 <= tb) ti++;
+    while (ti * (ti + 1) / 2 > tb) ti--;
+    tj = tb - ti * (ti + 1) / 2;
+  } else {
+    ti = tb / p.nt;
+    tj = tb % p.nt;
+  }
+  const float2* src = part + (size_t)tb * ksplit * (TM * TN);
+  for (int idx = threadIdx.x; idx < TM * TN; idx += 256) {
+    const int r = idx / TN, cc = idx % TN;
+    const int64_t gi = ti * TM + r, gj = tj * TN + cc;
+    if (gi >= p.M || gj >= p.N) continue;
+    double v = 0.0;
+    for (int k = 0; k < ksplit; k++) {
+      const float2 hl = src[(size_t)k * (TM * TN) + idx];
+      v += (double)hl.x + (double)hl.y;
+    }
+    const double cv = v * pow2(p.eA[gi] + p.eB[gj]);
+    const int64_t off = gi * p.ldc + gj;
+    if (p.mode == 0) p.C[off] = cv;
+    else if (p.mode == 1) p.C[off] = fma(p.rowscale ? p.rowscale[gi] : 1.0, cv, p.C[off]);
+    else p.C[off] = p.C[off] - cv;
   }
 }
 
@@ -627,7 +683,7 @@ int prep_rows(const double* X, int64_t ld, int64_t n, int64_t k, const OzOperand
 
 template <int S, bool SYM>
 int launch_oz(const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, double* C, int64_t ldc, int mode,
-              const double* rowscale, int* flag, cudaStream_t st) {
+              const double* rowscale, int* flag, cudaStream_t st, int ksplit, void* part) {
   CUtensorMap ma, mb;
   int rc = encode(A, S, &ma);
   if (rc) return rc;
@@ -657,11 +713,24 @@ int launch_oz(const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, doub
   a.flag = flag;
   const int64_t tiles = SYM ? mt * (mt + 1) / 2 : mt * nt;
   if (tiles <= 0) return GN_OK;
+  const int nchunk_all = (int)((a.Kpad / BKS + a.spc - 1) / a.spc);
+  if (ksplit < 1 || ch || mode == 3 || !part) ksplit = 1;   // split-K: single-exponent modes 0-2 only
+  a.cps = (nchunk_all + ksplit - 1) / ksplit;
+  if (a.cps < 1) a.cps = 1;
+  ksplit = (nchunk_all + a.cps - 1) / a.cps;   // no empty splits
+  if (ksplit < 1) ksplit = 1;
+  a.ksplit = ksplit;
+  a.part = ksplit > 1 ? static_cast<float2*>(part) : nullptr;
+  const unsigned grid = (unsigned)(tiles * ksplit);
   if (ch)
-    ozaki_kernel<S, SYM, true><<<(unsigned)tiles, NTHREADS, smem, st>>>(ma, mb, a);
+    ozaki_kernel<S, SYM, true><<<grid, NTHREADS, smem, st>>>(ma, mb, a);
   else
-    ozaki_kernel<S, SYM, false><<<(unsigned)tiles, NTHREADS, smem, st>>>(ma, mb, a);
+    ozaki_kernel<S, SYM, false><<<grid, NTHREADS, smem, st>>>(ma, mb, a);
   count_launch();
+  if (ksplit > 1) {
+    oz_splitk_reduce<SYM><<<(unsigned)tiles, 256, 0, st>>>(a.part, ksplit, a);
+    count_launch();
+  }
   return GN_NOTE(cudaGetLastError()) == cudaSuccess ? GN_OK : GN_ERR_CUDA;
 }
 
@@ -716,15 +785,15 @@ OzOperand oz_operand_rows(const OzOperand& op, int S, int64_t row_off) {
 }
 
 int oz_gemm(int S, bool sym, const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, double* C, int64_t ldc,
-            int mode, const double* rowscale, int* flag, cudaStream_t st) {
+            int mode, const double* rowscale, int* flag, cudaStream_t st, int ksplit, void* part) {
   if (A.kpad != B.kpad || A.kuse != B.kuse || A.kuse % BKS != 0 || A.kuse > A.kpad) return GN_ERR_INVALID;
   if (A.echunk != B.echunk || A.estride != B.estride || A.echunk % BKS != 0 || A.echunk > SPC * BKS ||
       (A.echunk > 0 && A.estride <= 0))
     return GN_ERR_INVALID;
 #define GN_OZ_CASE(s)                                                                     \
   case s:                                                                                 \
-    return sym ? launch_oz<s, true>(A, B, M, N, C, ldc, mode, rowscale, flag, st)         \
-               : launch_oz<s, false>(A, B, M, N, C, ldc, mode, rowscale, flag, st);
+    return sym ? launch_oz<s, true>(A, B, M, N, C, ldc, mode, rowscale, flag, st, ksplit, part)   \
+               : launch_oz<s, false>(A, B, M, N, C, ldc, mode, rowscale, flag, st, ksplit, part);
   switch (S) {
     GN_OZ_CASE(1)
     GN_OZ_CASE(2)
@@ -751,13 +820,127 @@ int ensure_split_ws(gn_handle* h, size_t need) {
   return GN_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Gram split-K autotuner.  A Gram of few 128 x 128 tiles (small P') leaves most of the 152
+// SMs idle; cutting the contraction into ksplit parts multiplies the CTAs.  The best ksplit
+// depends on the tile count, the contraction length and S, so it is measured: on the first
+// split Gram of a shape (S, tile rows, flush chunks) every candidate is launched and timed
+// with CUDA events, and the fastest is kept in a process-wide table (so every handle of that
+// shape in the process takes the same, deterministic path).  gn_set_gram_split forces one.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int64_t kSplitMaxCtas = 4 * 152;   // candidates keep tiles * ksplit within 4 waves
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int64_t, int64_t>, int> g_tune;
+
+int64_t gram_chunks(int64_t nrows) { return (rup(nrows > 0 ? nrows : 1, BKS) / BKS + SPC - 1) / SPC; }
+int64_t gram_tiles(int64_t Pp) {
+  const int64_t mt = (Pp + TM - 1) / TM;
+  return mt * (mt + 1) / 2;
+}
+std::vector<int> gram_candidates(int64_t Pp, int64_t nrows) {
+  std::vector<int> c = {1};
+  const int64_t tiles = gram_tiles(Pp), nch = gram_chunks(nrows);
+  int last = 1;
+  for (int ks : {2, 3, 4, 6, 8}) {
+    const int64_t cps = (nch + ks - 1) / ks;
+    const int eff = (int)((nch + cps - 1) / cps);   // splits actually made
+    if (tiles * eff > kSplitMaxCtas || cps < 2 || eff <= last) continue;
+    c.push_back(eff);
+    last = eff;
+  }
+  return c;
+}
+int gram_max_split(gn_handle* h, int64_t nrows) {
+  if (h->gram_ksplit > 0) return h->gram_ksplit;
+  int m = 1;
+  for (int k : gram_candidates(h->Pp, nrows)) m = k > m ? k : m;
+  return m;
+}
+size_t gram_part_bytes(int64_t Pp, int ksplit) {
+  return ksplit > 1 ? (size_t)gram_tiles(Pp) * ksplit * TM * TN * sizeof(float2) : 0;
+}
+bool lookup(int S, int64_t Pp, int64_t nrows, int* ks) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  auto it = g_tune.find(std::make_tuple(S, (Pp + TM - 1) / TM, gram_chunks(nrows)));
+  if (it == g_tune.end()) return false;
+  *ks = it->second;
+  return true;
+}
+// Time every candidate on the prepared operand (mode 0 into C, which the caller overwrites
+// afterwards) and record the fastest.  Synchronises the stream.
+int tune(gn_handle* h, int S, const OzOperand& op, int64_t nrows, double* C, void* part, int* best_out) {
+  const std::vector<int> cand = gram_candidates(h->Pp, nrows);
+  int best = 1;
+  if (cand.size() > 1) {
+    cudaEvent_t e0, e1;
+    if (GN_NOTE(cudaEventCreate(&e0)) != cudaSuccess) return GN_ERR_CUDA;
+    if (GN_NOTE(cudaEventCreate(&e1)) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      return GN_ERR_CUDA;
+    }
+    float best_ms = 0.f;
+    int rc = GN_OK;
+    for (int ks : cand) {
+      rc = oz_gemm(S, true, op, op, h->Pp, h->Pp, C, h->Pp, 0, nullptr, h->flag + 2, h->st, ks, part);   // warm
+      if (rc) break;
+      cudaEventRecord(e0, h->st);
+      for (int r = 0; r < 3 && !rc; r++)
+        rc = oz_gemm(S, true, op, op, h->Pp, h->Pp, C, h->Pp, 0, nullptr, h->flag + 2, h->st, ks, part);
+      cudaEventRecord(e1, h->st);
+      if (rc || GN_NOTE(cudaEventSynchronize(e1)) != cudaSuccess) {
+        rc = rc ? rc : GN_ERR_CUDA;
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ks == cand[0] || ms < 0.97f * best_ms) {   // a larger split must win by 3%
+        best_ms = ms;
+        best = ks;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+  }
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[std::make_tuple(S, (h->Pp + TM - 1) / TM, gram_chunks(nrows))] = best;
+  }
+  *best_out = best;
+  return GN_OK;
+}
+}  // namespace
+
+int gram_split_choice(int S, int64_t Pp, int64_t nrows) {
+  int ks = 0;
+  return lookup(S, Pp, nrows, &ks) ? ks : 0;
+}
+
+// Tune the Gram of the handle's largest row block ahead of a capture, on a zeroed operand
+// (tensor-core time does not depend on the values).
+int pretune_gram(gn_handle* h) {
+  if (h->precision == GN_PREC_FP64 || h->gram_ksplit > 0 || h->n_rows <= 0) return GN_OK;
+  const int S = h->n_slices;
+  const int64_t nrows = h->jrows;
+  int ks = 0;
+  if (lookup(S, h->Pp, nrows, &ks)) return GN_OK;
+  const size_t opb = oz_operand_bytes(S, h->Pp, nrows);
+  unsigned char* base = static_cast<unsigned char*>(h->split_ws);
+  OzOperand op = oz_operand_at(base, S, h->Pp, nrows);
+  if (GN_NOTE(cudaMemsetAsync(base, 0, opb, h->st)) != cudaSuccess) return GN_ERR_CUDA;
+  void* part = base + opb + (size_t)CM_CHUNKS * rup(h->Pp, TM) * 8 + 256;
+  return tune(h, S, op, nrows, h->G, part, &ks);
+}
+
 // Everything a step's split contractions need, allocated up front: the Gram operand of the
 // largest row block, the CCF Hilbert contraction's operands (SPLIT_ALL) and the split
 // factorisation's workspace and streams (SPLIT_ALL).
 int prepare_for_capture(gn_handle* h) {
   if (h->precision == GN_PREC_FP64) return GN_OK;
   const int S = h->n_slices;
-  size_t need = oz_operand_bytes(S, h->Pp, h->jrows) + (size_t)CM_CHUNKS * rup(h->Pp, TM) * 8 + 256;
+  size_t need = oz_operand_bytes(S, h->Pp, h->jrows) + (size_t)CM_CHUNKS * rup(h->Pp, TM) * 8 + 256 +
+                gram_part_bytes(h->Pp, gram_max_split(h, h->jrows));
   if (h->precision == GN_PREC_SPLIT_ALL) {
     if (h->eq == GN_CCF && h->p.n_pts > 0) {
       const int64_t rows = h->p.n_pts < h->jrows ? h->p.n_pts : h->jrows;
@@ -769,7 +952,9 @@ int prepare_for_capture(gn_handle* h) {
     if (ch > need) need = ch;
     if (GN_NOTE(ensure_chol_streams(h)) != cudaSuccess) return GN_ERR_CUDA;
   }
-  return ensure_split_ws(h, need);
+  const int rc = ensure_split_ws(h, need);
+  if (rc) return rc;
+  return pretune_gram(h);
 }
 
 // Gram through the split GEMM: G (lower tiles) = J^T J or += (accumulate).
@@ -778,13 +963,24 @@ int split_gram(gn_handle* h, const double* J, int64_t ld, int64_t nrows, double*
   if (S < 1 || S > kOzMaxSlices) return GN_ERR_UNSUPPORTED;
   if (nrows <= 0) return GN_OK;
   const size_t opb = oz_operand_bytes(S, h->Pp, nrows);
-  int rc = ensure_split_ws(h, opb + (size_t)CM_CHUNKS * rup(h->Pp, TM) * 8 + 256);
+  const size_t cmb = (size_t)CM_CHUNKS * rup(h->Pp, TM) * 8 + 256;
+  int rc = ensure_split_ws(h, opb + cmb + gram_part_bytes(h->Pp, gram_max_split(h, nrows)));
   if (rc) return rc;
   OzOperand op = oz_operand_at(h->split_ws, S, h->Pp, nrows);
   double* part = reinterpret_cast<double*>(static_cast<unsigned char*>(h->split_ws) + opb);
+  void* kpart = static_cast<unsigned char*>(h->split_ws) + opb + cmb;
   rc = oz_prepare_cols(S, J, ld, nrows, h->Pp, op, part, h->st);
   if (rc) return rc;
-  rc = oz_gemm(S, true, op, op, h->Pp, h->Pp, G, h->Pp, accumulate ? 1 : 0, nullptr, h->flag + 2, h->st);
+  // split-K factor: forced, tuned earlier for this shape, tuned now, or none
+  int ks = h->gram_ksplit;
+  if (ks <= 0 && !lookup(S, h->Pp, nrows, &ks)) {
+    ks = 1;
+    if (!accumulate && !h->capturing) {
+      rc = tune(h, S, op, nrows, G, kpart, &ks);
+      if (rc) return rc;
+    }
+  }
+  rc = oz_gemm(S, true, op, op, h->Pp, h->Pp, G, h->Pp, accumulate ? 1 : 0, nullptr, h->flag + 2, h->st, ks, kpart);
   if (rc) return rc;
   return GN_OK;
 }

@@ -104,6 +104,8 @@ EXPORTS = {
     "gn_batch_handle": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_P)]),
     "gn_batch_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "gn_batch_destroy": (ctypes.c_int, [_P]),
+    "gn_set_gram_split": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gn_gram_split_choice": (ctypes.c_int, [_P, _I64, ctypes.POINTER(ctypes.c_int)]),
     "gn_step_graph": (ctypes.c_int, [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(gn_step_info)]),
     "gn_batch_capture_graph": (ctypes.c_int, [_P, _P]),
     "gn_batch_graph_step": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -219,6 +221,15 @@ class GNProblem:
     # -- calls with the C names ------------------------------------------------
     def gn_set_precision(self, precision, n_slices=0):
         _check(lib().gn_set_precision(self.h, int(precision), int(n_slices)), "gn_set_precision")
+
+    def gn_set_gram_split(self, ksplit):
+        _check(lib().gn_set_gram_split(self.h, int(ksplit)), "gn_set_gram_split")
+
+    def gn_gram_split_choice(self, nrows=None):
+        k = ctypes.c_int(0)
+        _check(lib().gn_gram_split_choice(self.h, self.n_rows if nrows is None else int(nrows), ctypes.byref(k)),
+               "gn_gram_split_choice")
+        return k.value
 
     def gn_residual(self, theta, lam, r_out=None, want_loss=True):
         loss = _D()

@@ -161,3 +161,61 @@ def test_split_all_gn_step_matches_oracle(name):
     # G, J_U and the factorisation each carry ~1e-13 relative error at S = 6
     # (FP32 tail accumulator); the step amplifies it by cond(G + gamma I)
     assert np.max(np.abs(d_gpu - d_o)) / np.max(np.abs(d_o)) <= max(1e-12, 2e-13 * cond)
+
+
+# --- split-K (the contraction over rows cut into parts summed by a second launch) ---------
+
+@pytest.mark.parametrize("ksplit", [2, 3, 5, 8])
+def test_split_gram_splitk_bit_exact_on_8bit_integers(ksplit):
+    """Integer J (8-bit entries): every partial tile is an exact integer sum and the final
+    FP64 sum of the parts is exact too, so any split must give the exact Gram bit for bit
+    (this pins the partial-tile layout, the chunk ranges of each part and the reduction)."""
+    w = small("ccf")
+    prob = gpu_problem(w)
+    Pp = prob.P + 1
+    rng = np.random.default_rng(11)
+    Jh = rng.integers(-200, 201, size=(2000, Pp)).astype(np.float64)
+    Jh[:, 3] = 0.0
+    Jh[:, 9] *= 2.0 ** -30
+    prob.gn_set_gram_split(ksplit)
+    G = host(_split_gram(prob, dev(Jh), 1))
+    assert np.array_equal(np.tril(G), np.tril(Jh.T @ Jh))
+
+
+@pytest.mark.parametrize("ksplit", [1, 2, 4, 7])
+def test_split_gram_splitk_error_bound(ksplit):
+    w = small("ccf")
+    p = oracle_problem(w)
+    J1 = ogn.jacobian(p, w.theta, w.lam)
+    J = np.concatenate([J1] * 7)          # 2114 rows: 17 flush chunks, ragged
+    prob = gpu_problem(w)
+    prob.gn_set_gram_split(ksplit)
+    G = np.tril(host(_split_gram(prob, dev(J), 6)))
+    Gx = np.tril(J.T @ J)
+    bound = np.tril(split_bound(J, 6))
+    err = np.abs(G - Gx)
+    assert np.all(err <= 2.0 * bound + 1e-300), float(np.max(err / (bound + 1e-300)))
+    # accumulate (mode 1) through the split path as well
+    G2 = _split_gram(prob, dev(J), 6)
+    G2 = host(_split_gram(prob, dev(J), 6, accumulate=True, G=G2))
+    assert np.all(np.tril(np.abs(G2 - 2 * (J.T @ J))) <= 4.0 * bound + 1e-300)
+
+
+def test_gram_autotuner_records_a_choice_per_shape():
+    """The first split Gram of a shape times the candidates and records the fastest; a second
+    handle of the same shape reuses it; forcing a factor overrides the table."""
+    w = small("ccf")
+    prob = gpu_problem(w)
+    Pp = prob.P + 1
+    rng = np.random.default_rng(3)
+    J = dev(rng.standard_normal((4000, Pp)))
+    _split_gram(prob, J, 6)
+    k = prob.gn_gram_split_choice(4000)
+    assert 1 <= k <= 8
+    prob2 = gpu_problem(w)
+    prob2.gn_set_precision(SPLIT, 6)          # the table is keyed by the slice count too
+    assert prob2.gn_gram_split_choice(4000) == k
+    prob2.gn_set_gram_split(3)
+    assert prob2.gn_gram_split_choice(4000) == 3
+    with pytest.raises(Exception):
+        prob2.gn_set_gram_split(9)
