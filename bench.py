@@ -67,6 +67,13 @@ def parse():
                     choices=["ccf_unstable1", "ccf_stable", "ipm", "boussinesq", "batched"],
                     help="ccf_unstable1 is the headline line; the others print their own line")
     ap.add_argument("--streams", type=int, default=8, help="--workload batched: CUDA streams (host workers)")
+    ap.add_argument("--funnel", action="store_true",
+                    help="funnel inference of lambda over a batch of fits at fixed lambda (own JSON line)")
+    ap.add_argument("--funnel-fits", type=int, default=16)
+    ap.add_argument("--funnel-iters", type=int, default=6)
+    ap.add_argument("--funnel-steps", type=int, default=20)
+    ap.add_argument("--funnel-radius", type=float, default=0.1)
+    ap.add_argument("--funnel-dlam", type=float, default=0.01)
     ap.add_argument("--graph", action="store_true",
                     help="step through the captured CUDA graphs (gn_step_graph; batched: one graph launch per "
                          "batched step, gn_batch_graph_step)")
@@ -303,6 +310,70 @@ def micro_jacobian(args):
         del J
         prob.close()
     print(json.dumps(out))
+    return 0
+
+
+def run_funnel(args):
+    """Funnel inference of lambda (Methods, "Identifying Admissible lambda Values", item 3)
+    over a batch of fits: --funnel-fits copies of the workload with different seeded point
+    sets and initialisations and lambda seeds spread by 2 % around the workload's seed, each
+    held at a fixed lambda (gn_set_lambda_trainable(0)) and trained --funnel-steps damped GN
+    steps per iteration (one batched CUDA-graph launch per step); then r_hat(lambda), the
+    signed residual of largest magnitude within --funnel-radius of the origin, is read for
+    every fit and each fit's lambda moves by the secant update (gn_funnel_next).  Prints one
+    JSON line with the lambda and r_hat histories and the device time per funnel iteration."""
+    import torch
+    from paper_2509_14185_gb300 import build as B
+    B.build()
+    from paper_2509_14185_gb300 import gn, inputs
+    name = args.workload if args.workload != "batched" else "ccf_stable"
+    make = inputs.WORKLOADS[name]
+    seed0 = make.__defaults__[0]
+    fits = []
+    for f in range(args.funnel_fits):
+        w = make(seed=seed0 + 100 + f)
+        w.lam = w.lam * (1.0 + 0.02 * (f / max(1, args.funnel_fits - 1) - 0.5))
+        fits.append(w)
+    prec = {"fp64": gn.GN_PREC_FP64, "split": gn.GN_PREC_SPLIT_BF16, "split_all": gn.GN_PREC_SPLIT_ALL}[args.precision]
+    batch = gn.GNBatch(fits, n_streams=min(8, len(fits)), precision=prec, n_slices=args.slices)
+    batch.gn_set_lambda_trainable(False)
+    thetas = [torch.tensor(w.theta, dtype=torch.float64, device="cuda") for w in fits]
+    batch.gn_batch_capture_graph(thetas)
+    lams = [w.lam for w in fits]
+    gams = [w.gamma for w in fits]
+    hist_l = [[l] for l in lams]
+    hist_r = [[] for _ in fits]
+    iter_ms, losses = [], []
+    for it in range(args.funnel_iters):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.funnel_steps):
+            lams2, gams, infos, st = batch.gn_batch_graph_step(lams, gams)
+            assert lams2 == lams          # lambda is held fixed during the relaxation
+        r = [batch.gn_signed_max_residual(f, thetas[f], lams[f], args.funnel_radius)[0] for f in range(len(fits))]
+        e1.record()
+        torch.cuda.synchronize()
+        iter_ms.append(e0.elapsed_time(e1))
+        losses.append(statistics.median(i["loss_after"] for i in infos))
+        for f in range(len(fits)):
+            hist_r[f].append(r[f])
+            try:
+                nxt = gn.gn_funnel_next(hist_l[f], hist_r[f], args.funnel_dlam)
+            except gn.GNError:
+                nxt = lams[f]
+            lams[f] = nxt
+            hist_l[f].append(nxt)
+    batch.close()
+    final = [h[-1] for h in hist_l]
+    print(json.dumps({"mode": "funnel_inference", "workload": fits[0].name, "fits": len(fits),
+                      "precision": args.precision, "steps_per_iteration": args.funnel_steps,
+                      "radius": args.funnel_radius, "dlambda": args.funnel_dlam,
+                      "ms_per_iteration": statistics.median(iter_ms),
+                      "fit_steps_per_s": len(fits) * args.funnel_steps / (statistics.median(iter_ms) * 1e-3),
+                      "median_loss_per_iteration": losses,
+                      "lambda_final": {"median": statistics.median(final), "min": min(final), "max": max(final)},
+                      "lambda_history": hist_l[:4], "r_hat_history": hist_r[:4]}))
     return 0
 
 
@@ -723,6 +794,8 @@ def main():
         return micro_jacobian(args)
     if args.equal_residual:
         return equal_residual(args)
+    if args.funnel:
+        return run_funnel(args)
     if args.workload == "batched":
         return run_batched(args)
     if args.ema_vs_exact:

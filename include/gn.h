@@ -297,6 +297,43 @@ int gn_batch_graph_step(gn_batch* b, double* lambdas, double* dampings, gn_step_
 int gn_step_ema(gn_handle* h, double* theta, double* lambda, double* damping, double* G_ema, double* v_prev,
                 const double* signs, double beta, int first, gn_step_info* info);
 
+/* ---- the blow-up rate lambda (Methods, "Identifying Admissible lambda Values") ---- */
+
+/* trainable = 1 (default): lambda is an unknown of every step (column P of J~, entry P of
+ * the gradients).  trainable = 0: lambda is held fixed, as funnel inference trains the
+ * network at a constant lambda: column P of J~ and entry P of every gradient are zero, so
+ * gn_step, gn_step_graph and gn_step_ema leave lambda unchanged (delta_P = 0 exactly).
+ * Captured graphs are recaptured on the next gn_step_graph call; a batch graph keeps the
+ * setting it was captured with.  GN_ERR_INVALID for other values. */
+int gn_set_lambda_trainable(gn_handle* h, int trainable);
+
+/* The lambda-inference rule (item 2): the self-similar equation differentiated at the
+ * origin gives lambda from the current fields.  Boussinesq lambda = -3 - 2 d1 U1(0, 0)
+ * (the rule the paper prints), IPM lambda = -2 - 2 d1 U1(0, 0) (U1 = d2 Psi, so d1 U1 =
+ * d12 Psi), CCF lambda = -2 - 2 U'(0) with U'(0) = H[Theta/x](0) by the library's discrete
+ * Hilbert operator; the IPM and CCF rules follow from the same steps on this library's
+ * residual operators.  theta: device [P]; lambda: the value the network is evaluated at
+ * (it enters q and the envelopes); *lambda_out: host.  Synchronises.  Returns
+ * GN_ERR_UNSUPPORTED for Burgers (U'(0) = -1 for every lambda: the rule is empty),
+ * GN_ERR_NONFINITE for a non-finite result. */
+int gn_lambda_inference(gn_handle* h, const double* theta, double lambda, double* lambda_out);
+
+/* The funnel-inference signal r_hat(lambda) (item 3): over the interior points with
+ * |y| <= radius and all equations, the residual R_k (unweighted) of largest magnitude,
+ * with its sign; ties go to the first point, then the first equation.  *r_hat (host) = 0
+ * and *point = -1 when no point lies within radius; point (host, may be NULL) receives the
+ * point index.  Overwrites the handle's residual buffer.  Synchronises. */
+int gn_signed_max_residual(gn_handle* h, const double* theta, double lambda, double radius, double* r_hat,
+                           int64_t* point);
+
+/* The funnel-inference update (item 3): n = 1: lambda_0 + dlambda; n >= 2: the secant zero
+ * through the last two pairs, lambda_n - r_n (lambda_n - lambda_{n-1}) / (r_n - r_{n-1}).
+ * The paper's printed update puts lambda_n in front of the correction anchored at
+ * lambda_{n-1}; its text calls the update the secant formula, which is what this computes.
+ * lambdas, r_hats: host [n]; *lambda_next: host.  Host arithmetic only (no GPU work).
+ * GN_ERR_INVALID when n < 1 or r_n == r_{n-1}. */
+int gn_funnel_next(const double* lambdas, const double* r_hats, int n, double dlambda, double* lambda_next);
+
 /* Checkpoint and resume of a fit (the paper's fits run for many Gauss-Newton
  * steps; resuming one needs theta, lambda and the damping).  The file holds,
  * little-endian: the magic bytes "GNCK", a uint32 version (1), the int32

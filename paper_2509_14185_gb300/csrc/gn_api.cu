@@ -96,6 +96,7 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
   a.lam = lam;
   a.lamp = ps.lamp;
   a.flag = h->flag;
+  a.lam_frozen = h->lam_frozen;
   a.ldg = round_up(h->Pp, 16);
   a.gpart = h->gpart;
   const int64_t n = h->p.n_pts;
@@ -127,8 +128,8 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
     b.n = n;
     b.y = h->p.y;
     b.ystride = n;
-    b.rho = h->p.rho;
-    b.wscale = n > 0 ? sqrt(2.0 / ((double)n * h->ne)) : 0.0;
+    b.rho = ps.unweighted ? nullptr : h->p.rho;
+    b.wscale = ps.unweighted ? 1.0 : (n > 0 ? sqrt(2.0 / ((double)n * h->ne)) : 0.0);
     b.row0 = 0;
     b.r = ps.r;
     b.J = ps.J;

@@ -29,7 +29,8 @@ enum PointKind : int {
   KIND_INTERIOR = 0,  // interior collocation point: N_E residual rows
   KIND_WALL = 1,      // wall point (2D): one row, the stream function value
   KIND_NORM = 2,      // normalisation point: one row
-  KIND_NODE = 3       // CCF Hilbert node: one row, g = Theta / y at the node
+  KIND_NODE = 3,      // CCF Hilbert node: one row, g = Theta / y at the node
+  KIND_PROBE = 4      // field jets at a point: per field value, gradient, Hessian (2D) into r
 };
 
 enum JetMode : int { MODE_RESIDUAL = 0, MODE_JACOBIAN = 1, MODE_GRADIENT = 2 };
@@ -72,6 +73,7 @@ struct JetArgs {
   const double* dcoef;   // CCF: diagonal coefficient D_i per interior point
   double* sU;            // CCF out: w_i dR/dU per interior point (times the seed in gradient mode)
   int* flag;             // bit 0: non-finite residual seen
+  int lam_frozen;        // lambda held fixed: its Jacobian column and gradient entry are zero
 };
 
 struct Workspace;
@@ -144,6 +146,7 @@ struct Pass {
   int64_t ldJ, jlo, jhi;
   const double* seed;
   const double* lamp = nullptr;   // device lambda (null: the host value passed to run_pass)
+  bool unweighted = false;        // interior rows carry R itself (no loss weights)
 };
 int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, double* grad);
 // 1/2 |r|^2 reduction: the sum of squares lands in red[256 + slot] (device)

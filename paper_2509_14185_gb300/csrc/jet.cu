@@ -323,6 +323,24 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
       F[f] = ymul<D>(envelope<D>(y, u, m, e), N);
     }
 
+    if (kind == KIND_PROBE) {
+      // field jets at the point: value, gradient and (2D) Hessian (d11, d12, d22) per field;
+      // the 1D kernels carry no second y-derivative of the fields, so 1D writes 0 there
+      if (lane == 0 && A.r) {
+        constexpr int NJ = 1 + D + (D == 1 ? 1 : 3);
+        double* o = A.r + pt * (NF * NJ);
+#pragma unroll
+        for (int f = 0; f < NF; f++) {
+          o[f * NJ] = F[f].v.v;
+#pragma unroll
+          for (int i = 0; i < D; i++) o[f * NJ + 1 + i] = F[f].g[i].v;
+#pragma unroll
+          for (int k = 0; k < (D == 1 ? 1 : 3); k++) o[f * NJ + 1 + D + k] = (D == 1) ? 0.0 : F[f].h[k].v;
+        }
+      }
+      continue;
+    }
+
     // residuals (or the single value of a wall/node/norm row)
     Dl R[NE];
     double sUv = 0.0;
@@ -405,9 +423,9 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
       } else {
         sd = w * R[e].d;
       }
-      if (lane == 0) {
-        if (MODE == MODE_JACOBIAN) Jrow[net.P] = sd;
-        else gp[net.P] += sd;
+      if (lane == 0) {   // the lambda column (zero while lambda is held fixed)
+        if (MODE == MODE_JACOBIAN) Jrow[net.P] = A.lam_frozen ? 0.0 : sd;
+        else if (!A.lam_frozen) gp[net.P] += sd;
       }
       if (lane >= 1 && lane < K) {
         const int f = (lane - 1) / CR, c = (lane - 1) % CR;

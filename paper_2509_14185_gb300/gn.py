@@ -105,6 +105,10 @@ EXPORTS = {
     "gn_batch_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "gn_batch_destroy": (ctypes.c_int, [_P]),
     "gn_set_gram_split": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gn_set_lambda_trainable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gn_lambda_inference": (ctypes.c_int, [_P, _P, _D, ctypes.POINTER(_D)]),
+    "gn_signed_max_residual": (ctypes.c_int, [_P, _P, _D, _D, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
+    "gn_funnel_next": (ctypes.c_int, [_P, _P, ctypes.c_int, _D, ctypes.POINTER(_D)]),
     "gn_gram_split_choice": (ctypes.c_int, [_P, _I64, ctypes.POINTER(ctypes.c_int)]),
     "gn_step_graph": (ctypes.c_int, [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(gn_step_info)]),
     "gn_batch_capture_graph": (ctypes.c_int, [_P, _P]),
@@ -231,6 +235,21 @@ class GNProblem:
                "gn_gram_split_choice")
         return k.value
 
+    def gn_set_lambda_trainable(self, trainable):
+        _check(lib().gn_set_lambda_trainable(self.h, int(bool(trainable))), "gn_set_lambda_trainable")
+
+    def gn_lambda_inference(self, theta, lam):
+        out = _D()
+        _check(lib().gn_lambda_inference(self.h, _ptr(theta), float(lam), ctypes.byref(out)), "gn_lambda_inference")
+        return out.value
+
+    def gn_signed_max_residual(self, theta, lam, radius):
+        out = _D()
+        idx = _I64()
+        _check(lib().gn_signed_max_residual(self.h, _ptr(theta), float(lam), float(radius), ctypes.byref(out),
+                                            ctypes.byref(idx)), "gn_signed_max_residual")
+        return out.value, idx.value
+
     def gn_residual(self, theta, lam, r_out=None, want_loss=True):
         loss = _D()
         rc = lib().gn_residual(self.h, _ptr(theta), float(lam), _ptr(r_out),
@@ -324,6 +343,16 @@ class GNProblem:
         return g
 
 
+def gn_funnel_next(lambdas, r_hats, dlambda):
+    """Next lambda of funnel inference (secant on the last two (lambda, r_hat) pairs)."""
+    n = len(lambdas)
+    la = (ctypes.c_double * max(1, n))(*lambdas)
+    ra = (ctypes.c_double * max(1, n))(*r_hats)
+    out = _D()
+    _check(lib().gn_funnel_next(la, ra, int(n), float(dlambda), ctypes.byref(out)), "gn_funnel_next")
+    return out.value
+
+
 class ResidualFn(torch.autograd.Function):
     """r~(theta, lambda) as a differentiable torch op: forward calls gn_residual, backward
     calls the adjoint kernel gn_gradient seeded by the incoming gradient (the same
@@ -408,6 +437,24 @@ class GNBatch:
         rc = lib().gn_batch_step(self.b, ptrs, lam, gam, infos, st)
         _check(rc if rc < 0 and rc not in (GN_ERR_NOT_SPD, GN_ERR_NONFINITE) else 0, "gn_batch_step")
         return list(lam), list(gam), [infos[i].as_dict() for i in range(self.n)], list(st)
+
+    def handle(self, f):
+        h = ctypes.c_void_p()
+        _check(lib().gn_batch_handle(self.b, int(f), ctypes.byref(h)), "gn_batch_handle")
+        return h
+
+    def gn_set_lambda_trainable(self, trainable):
+        """Hold lambda fixed (False) or train it (True) in every fit (capture graphs after this)."""
+        for f in range(self.n):
+            _check(lib().gn_set_lambda_trainable(self.handle(f), int(bool(trainable))), "gn_set_lambda_trainable")
+
+    def gn_signed_max_residual(self, f, theta, lam, radius):
+        out = _D()
+        idx = _I64()
+        torch.cuda.synchronize(self.device)
+        _check(lib().gn_signed_max_residual(self.handle(f), _ptr(theta), float(lam), float(radius),
+                                            ctypes.byref(out), ctypes.byref(idx)), "gn_signed_max_residual")
+        return out.value, idx.value
 
     def gn_batch_capture_graph(self, thetas):
         """Capture every fit's step into one CUDA graph for these parameter tensors."""
