@@ -108,7 +108,7 @@ class Problem:
     """One profile fit: equation, MLP widths, collocation and wall points, loss weights."""
 
     def __init__(self, equation, widths, y, y_bnd=None, rho=None, c_bnd=1.0,
-                 y_norm=(1.0, 0.0), c_norm=1.0, c_norm_w=1.0, hilbert_m=1024):
+                 y_norm=(1.0, 0.0), c_norm=1.0, c_norm_w=1.0, hilbert_m=1024, stage1=None):
         self.eq = int(equation)
         self.widths = list(widths)
         self.d = DIM[self.eq]
@@ -130,24 +130,35 @@ class Problem:
         self.P = sum(self.widths[i] * self.widths[i + 1] + self.widths[i + 1]
                      for i in range(len(self.widths) - 1))
         self.n_rows = self.n * self.ne + self.nb + 1
+        # Multi-stage training (Methods, "Multi-stage Training"): stage1 = (widths1, theta1, eps)
+        # makes every field Phi = Phi_1 + eps Phi_2 with Phi_1 the frozen stage-1 network and
+        # Phi_2 this problem's network, and divides every row by eps (the normalised stage-2
+        # equation: R(Phi_1 + eps Phi_2) / eps = R_1 / eps + D[Phi_1] Phi_2 + O(eps)).
+        self.stage1 = None
+        if stage1 is not None:
+            w1, th1, eps = stage1
+            w1 = list(w1)
+            assert w1[0] == self.d and w1[-1] == N_FIELDS[self.eq] and eps > 0
+            self.stage1 = (w1, np.asarray(th1, dtype=np.float64), float(eps))
 
     # -- network ----------------------------------------------------------
-    def layers(self, theta):
+    def layers(self, theta, widths=None):
+        widths = self.widths if widths is None else widths
         out, off = [], 0
-        for i in range(len(self.widths) - 1):
-            fi, fo = self.widths[i], self.widths[i + 1]
+        for i in range(len(widths) - 1):
+            fi, fo = widths[i], widths[i + 1]
             W = theta[off:off + fi * fo].reshape(fo, fi)
             off += fi * fo
             b = theta[off:off + fo]
             off += fo
             out.append((W, b))
-        assert off == self.P
+        assert off == len(theta)
         return out
 
-    def mlp(self, theta, z):
+    def mlp(self, theta, z, widths=None):
         """tanh MLP with linear last layer applied to the input jet z (components (d_in, n))."""
         h = z
-        L = self.layers(theta)
+        L = self.layers(theta, widths)
         for i, (W, b) in enumerate(L):
             a = h.matvec(W, b)
             h = a if i == len(L) - 1 else a.tanh()
@@ -155,7 +166,17 @@ class Problem:
 
     # -- ansatz -------------------------------------------------------------
     def fields(self, theta, lam, ys, extra_g=False):
-        """Field jets Phi_A at points ys (d, n); for CCF optionally also g = Theta / y."""
+        """Field jets Phi_A at points ys (d, n); for CCF optionally also g = Theta / y.
+        In a stage-2 problem: Phi_1 + eps Phi_2 (and g_1 + eps g_2)."""
+        out = self.network_fields(theta, lam, ys, extra_g)
+        if self.stage1 is None:
+            return out
+        w1, th1, eps = self.stage1
+        base = self.network_fields(th1, lam, ys, extra_g, widths=w1)
+        return [b + f * eps for b, f in zip(base, out)]
+
+    def network_fields(self, theta, lam, ys, extra_g=False, widths=None):
+        """The ansatz fields of one network (widths, theta) at points ys."""
         d = self.d
         yj = [Jet.variable(ys[i], i, d) for i in range(d)]
         u = Jet.const(np.ones(ys.shape[1]), d)
@@ -167,7 +188,7 @@ class Problem:
         else:
             beta = yj[1] / u.sqrt()
             z = Jet.stack([q, beta])
-        nn = self.mlp(theta, z)
+        nn = self.mlp(theta, z, widths)
         out = []
         for a, (kind, k) in enumerate(field_specs(self.eq, lam)):
             out.append(_prefactor(kind, yj, u) * nn[a] * q.pow(-k))
@@ -223,7 +244,8 @@ class Problem:
         if self.nb:
             parts.append(np.sqrt(2.0 * self.c_bnd / self.nb) * self.wall_values(theta, lam))
         parts.append(np.array([np.sqrt(2.0 * self.c_norm_w) * (self.norm_value(theta, lam) - self.c_norm)]))
-        return np.concatenate(parts)
+        r = np.concatenate(parts)
+        return r / self.stage1[2] if self.stage1 is not None else r
 
     def loss(self, theta, lam):
         r = self.rows(theta, lam)
