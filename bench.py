@@ -67,6 +67,9 @@ def parse():
                     choices=["ccf_unstable1", "ccf_stable", "ipm", "boussinesq", "batched"],
                     help="ccf_unstable1 is the headline line; the others print their own line")
     ap.add_argument("--streams", type=int, default=8, help="--workload batched: CUDA streams (host workers)")
+    ap.add_argument("--multistage", action="store_true",
+                    help="two-stage training (stage 2 learns the error of stage 1; own JSON line)")
+    ap.add_argument("--stage-steps", type=int, nargs=2, default=[200, 200])
     ap.add_argument("--funnel", action="store_true",
                     help="funnel inference of lambda over a batch of fits at fixed lambda (own JSON line)")
     ap.add_argument("--funnel-fits", type=int, default=16)
@@ -310,6 +313,60 @@ def micro_jacobian(args):
         del J
         prob.close()
     print(json.dumps(out))
+    return 0
+
+
+def run_multistage(args):
+    """Two-stage training (Methods, "Multi-stage Training") on the GPU: stage 1 trains the
+    workload's network for --stage-steps[0] damped GN steps (lambda trainable, captured
+    graphs); stage 2 freezes it and trains a second network of the same shape on the
+    stage-2 problem (fields Phi_1 + eps Phi_2, rows / eps, lambda fixed, eps = the stage-1
+    max residual on the collocation points) for --stage-steps[1] steps.  Reports the max d0
+    residual on a dense validation grid after each stage and the device time of each."""
+    import torch
+    from paper_2509_14185_gb300 import build as B
+    B.build()
+    from paper_2509_14185_gb300 import gn, inputs
+    name = args.workload if args.workload in ("ccf_stable", "ccf_unstable1") else "ccf_stable"
+    w = inputs.WORKLOADS[name]()
+    prec = {"fp64": gn.GN_PREC_FP64, "split": gn.GN_PREC_SPLIT_BF16, "split_all": gn.GN_PREC_SPLIT_ALL}[args.precision]
+    grid = validation_grid_1d()
+
+    def steps(prob, theta, lam, gam, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        hist = []
+        for k in range(n):
+            rc, lam, gam, info = prob.gn_step_graph(theta, lam, gam)
+            hist.append(info["loss_after"])
+        e1.record()
+        torch.cuda.synchronize()
+        return lam, gam, e0.elapsed_time(e1), hist
+
+    p1 = gn.GNProblem.from_workload(w, precision=prec, n_slices=args.slices)
+    th1 = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
+    lam, gam, ms1, h1 = steps(p1, th1, w.lam, w.gamma, args.stage_steps[0])
+    eps = p1.gn_max_residual(th1, lam)
+    val1 = gn.GNProblem(w.equation, w.widths, grid, y_norm=w.y_norm, c_norm=w.c_norm, hilbert_m=w.hilbert_m)
+    res1 = val1.gn_max_residual(th1, lam)
+    p2 = gn.GNProblem.from_workload(w, precision=prec, n_slices=args.slices)
+    p2.gn_set_stage1(w.widths, th1, lam, eps)
+    th2 = torch.tensor(inputs.xavier_init(w.widths, 777), dtype=torch.float64, device="cuda")
+    lam2, gam2, ms2, h2 = steps(p2, th2, lam, w.gamma, args.stage_steps[1])
+    val2 = gn.GNProblem(w.equation, w.widths, grid, y_norm=w.y_norm, c_norm=w.c_norm, hilbert_m=w.hilbert_m)
+    val2.gn_set_stage1(w.widths, th1, lam, eps)
+    res2 = val2.gn_max_residual(th2, lam)
+    print(json.dumps({"mode": "multistage", "workload": w.name, "precision": args.precision,
+                      "grid_points": int(grid.shape[1]), "lambda": lam, "eps": eps,
+                      "stage1": {"steps": len(h1), "device_s": ms1 * 1e-3, "loss": h1[-1],
+                                 "max_res_train": eps, "max_res_grid": res1},
+                      "stage2": {"steps": len(h2), "device_s": ms2 * 1e-3, "loss": h2[-1],
+                                 "max_res_train": p2.gn_max_residual(th2, lam), "max_res_grid": res2},
+                      "gain_grid": res1 / res2 if res2 > 0 else None,
+                      "stage2_loss_curve": h2[:: max(1, len(h2) // 10)]}))
+    for q in (p1, p2, val1, val2):
+        q.close()
     return 0
 
 
@@ -796,6 +853,8 @@ def main():
         return equal_residual(args)
     if args.funnel:
         return run_funnel(args)
+    if args.multistage:
+        return run_multistage(args)
     if args.workload == "batched":
         return run_batched(args)
     if args.ema_vs_exact:

@@ -334,6 +334,21 @@ int gn_signed_max_residual(gn_handle* h, const double* theta, double lambda, dou
  * GN_ERR_INVALID when n < 1 or r_n == r_{n-1}. */
 int gn_funnel_next(const double* lambdas, const double* r_hats, int n, double dlambda, double* lambda_next);
 
+/* Multi-stage training (Methods, "Multi-stage Training"): turn the handle into the
+ * second stage of a fit whose first stage is the network (n_layers1, widths1, theta1) at
+ * the fixed blow-up rate lambda.  From then on every field is Phi_1 + eps Phi_2, Phi_1
+ * the frozen stage-1 network and Phi_2 the handle's own network (its own widths and
+ * parameters), every row of r~ and J~ is divided by eps (the normalised stage-2 equation
+ * R(Phi_1 + eps Phi_2) / eps = R_1 / eps + D[Phi_1] Phi_2 + O(eps), the paper's linearised
+ * equation with its O(eps^2) part kept), lambda is held fixed (gn_set_lambda_trainable(0))
+ * and gn_max_residual reports max |R_k| of the composed field.  Pass the same lambda to
+ * every later call.  widths1: host [n_layers1 + 1] with widths1[0] = d and
+ * widths1[n_layers1] = the number of fields; theta1: device [P1], read during the call only
+ * (the stage-1 field jets at every point are evaluated once and kept, so later calls do not
+ * read it); eps > 0, typically the stage-1 maximum residual.  Calling it again replaces
+ * the first stage.  Synchronises.  GN_ERR_INVALID, GN_ERR_OOM or GN_ERR_CUDA. */
+int gn_set_stage1(gn_handle* h, int n_layers1, const int* widths1, const double* theta1, double lambda, double eps);
+
 /* Checkpoint and resume of a fit (the paper's fits run for many Gauss-Newton
  * steps; resuming one needs theta, lambda and the damping).  The file holds,
  * little-endian: the magic bytes "GNCK", a uint32 version (1), the int32

@@ -69,7 +69,7 @@ cudaError_t dalloc(T** p, size_t count) {
 void free_all(gn_handle* h) {
   void* ptrs[] = {h->ema_ws, h->wt, h->theta_t, h->r, h->J, h->G, h->A, h->Linv, h->g, h->delta, h->vtmp, h->red,
                   h->flag, h->gpart, h->kf, h->dcoef, h->snode, h->gnode, h->Jg, h->ug, h->sU, h->tnode,
-                  h->split_ws};
+                  h->split_ws, h->base_int, h->base_wall, h->base_norm, h->base_node};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->hpin) cudaFreeHost(h->hpin);
@@ -97,6 +97,10 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
   a.lamp = ps.lamp;
   a.flag = h->flag;
   a.lam_frozen = h->lam_frozen;
+  a.eps = h->stage_eps;
+  a.base_ld = h->base_ld;
+  // stage 2: rows are R(Phi_1 + eps Phi_2) / eps (unless the caller wants R itself)
+  const double rs = (h->staged && !ps.unweighted) ? 1.0 / h->stage_eps : 1.0;
   a.ldg = round_up(h->Pp, 16);
   a.gpart = h->gpart;
   const int64_t n = h->p.n_pts;
@@ -117,6 +121,8 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
     b.ldJ = h->ldJ;
     b.jrow_lo = 0;
     b.jrow_hi = h->Mh;
+    b.base = h->staged ? h->base_node : nullptr;
+    b.base_ld = 1;
     GN_TRY_CUDA(launch_jet(b, st, nullptr));
     GN_TRY_CUDA(dgemv_n(h->kf, h->Mh, n, h->Mh, h->gnode, h->ug, 0.0, st));
   }
@@ -129,7 +135,8 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
     b.y = h->p.y;
     b.ystride = n;
     b.rho = ps.unweighted ? nullptr : h->p.rho;
-    b.wscale = ps.unweighted ? 1.0 : (n > 0 ? sqrt(2.0 / ((double)n * h->ne)) : 0.0);
+    b.wscale = ps.unweighted ? 1.0 : rs * (n > 0 ? sqrt(2.0 / ((double)n * h->ne)) : 0.0);
+    b.base = h->staged ? h->base_int : nullptr;
     b.row0 = 0;
     b.r = ps.r;
     b.J = ps.J;
@@ -150,7 +157,8 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
     b.n = h->p.n_bnd;
     b.y = h->p.y_bnd;
     b.ystride = h->p.n_bnd;
-    b.wscale = sqrt(2.0 * h->p.c_bnd / (double)h->p.n_bnd);
+    b.wscale = rs * sqrt(2.0 * h->p.c_bnd / (double)h->p.n_bnd);
+    b.base = h->staged ? h->base_wall : nullptr;
     b.row0 = n * h->ne;
     b.r = ps.r;
     b.J = ps.J;
@@ -168,7 +176,8 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
     b.n = 1;
     b.y = norm_point(h);
     b.ystride = 1;
-    b.wscale = sqrt(2.0 * h->p.c_norm_w);
+    b.wscale = rs * sqrt(2.0 * h->p.c_norm_w);
+    b.base = h->staged ? h->base_norm : nullptr;
     b.c_norm = h->p.c_norm;
     b.row0 = h->n_rows - 1;
     b.r = ps.r;
@@ -220,6 +229,8 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
       b.row0 = 0;
       b.r = nullptr;
       b.seed = h->tnode;
+      b.base = h->staged ? h->base_node : nullptr;
+      b.base_ld = 1;
       GN_TRY_CUDA(launch_jet(b, st, nullptr));
     }
     GN_TRY_CUDA(launch_gpart_reduce(h->gpart, h->gpart_warps, a.ldg, h->Pp, grad, 0, st));
@@ -550,7 +561,7 @@ int gn_max_residual(gn_handle* h, const double* theta, double lambda, double* ou
   GN_TRY_CUDA(cudaMemcpyAsync(h->hpin, h->red + 300, sizeof(double), cudaMemcpyDeviceToHost, h->st));
   GN_TRY_CUDA(cudaStreamSynchronize(h->st));
   const double w = nint > 0 ? sqrt(2.0 / ((double)h->p.n_pts * h->ne)) : 1.0;
-  *out = h->hpin[0] / w;
+  *out = h->hpin[0] / w * (h->staged ? h->stage_eps : 1.0);   // stage 2: max |R| of Phi_1 + eps Phi_2
   return GN_OK;
 }
 

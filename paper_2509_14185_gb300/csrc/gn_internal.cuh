@@ -35,6 +35,10 @@ enum PointKind : int {
 
 enum JetMode : int { MODE_RESIDUAL = 0, MODE_JACOBIAN = 1, MODE_GRADIENT = 2 };
 
+// Values the probe kind writes per point: per field value, gradient and Hessian (1D: one
+// zero in place of the Hessian), then for CCF the value of g = Theta / y.
+inline int probe_ld(int eq, int d, int nf) { return nf * (1 + d + (d == 1 ? 1 : 3)) + (eq == GN_CCF ? 1 : 0); }
+
 struct NetDesc {
   int L;                            // linear layers
   int w[GN_MAX_LAYERS + 1];         // widths
@@ -74,6 +78,12 @@ struct JetArgs {
   double* sU;            // CCF out: w_i dR/dU per interior point (times the seed in gradient mode)
   int* flag;             // bit 0: non-finite residual seen
   int lam_frozen;        // lambda held fixed: its Jacobian column and gradient entry are zero
+  // stage 2 of multi-stage training: fields Phi_1 + eps Phi_2 with Phi_1's jets precomputed
+  // per point (null: single stage).  Interior/wall/norm: base_ld values per point (the probe
+  // layout); CCF nodes: g_1 per node.
+  const double* base;
+  int64_t base_ld;
+  double eps;
 };
 
 struct Workspace;
@@ -134,6 +144,14 @@ struct gn_handle {
   int capturing = 0;              // a stream capture is in progress: no workspace may grow
   int lam_frozen = 0;             // lambda held fixed (funnel inference trains at fixed lambda)
   int gram_ksplit = 0;            // split-K factor of the split Gram (0: autotuned per shape)
+  // stage 2 of multi-stage training (gn_set_stage1): the stage-1 field jets at every point
+  int staged = 0;
+  double stage_eps = 1.0;
+  int64_t base_ld = 0;
+  double* base_int = nullptr;     // [n_pts][base_ld]
+  double* base_wall = nullptr;    // [n_bnd][base_ld]
+  double* base_norm = nullptr;    // [base_ld]
+  double* base_node = nullptr;    // [Mh] (CCF)
 };
 
 namespace gn {

@@ -57,7 +57,8 @@ struct GraphState {
                                   // handle's own stream may be the legacy default stream,
                                   // which cannot be captured)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_in = nullptr;
-  int precision = -1, n_slices = -1, lam_frozen = -1;   // of the handle when the graphs were captured
+  int precision = -1, n_slices = -1, lam_frozen = -1, staged = -1;   // of the handle when captured
+  double stage_eps = 0.0;
   // kernels per replay, for gn_kernel_launches: outside the trial bodies (step graph, solve
   // graph, a batch's step branch) and per line-search trial that runs
   long long k_step = 0, k_solve = 0, k_branch = 0, k_trial = 0;
@@ -353,6 +354,8 @@ int build_graphs(gn_handle* h, double* theta, bool with_step) {
   gs->precision = h->precision;
   gs->n_slices = h->n_slices;
   gs->lam_frozen = h->lam_frozen;
+  gs->staged = h->staged;
+  gs->stage_eps = h->stage_eps;
   return GN_OK;
 }
 
@@ -464,7 +467,7 @@ int gn_step_graph(gn_handle* h, double* theta, double* lambda, double* damping, 
   if (rc) return rc;
   GraphState* gs = h->gs;
   if (gs->theta != theta || !gs->x_step || gs->precision != h->precision || gs->n_slices != h->n_slices ||
-      gs->lam_frozen != h->lam_frozen) {
+      gs->lam_frozen != h->lam_frozen || gs->staged != h->staged || gs->stage_eps != h->stage_eps) {
     rc = build_graphs(h, theta, true);
     if (rc) return rc;
   }

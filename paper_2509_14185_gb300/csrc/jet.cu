@@ -322,13 +322,14 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
       const Dl e = dconst(e0) + 0.5 * (kf * a);
       F[f] = ymul<D>(envelope<D>(y, u, m, e), N);
     }
+    constexpr int NJ = 1 + D + (D == 1 ? 1 : 3);   // probe values per field
 
     if (kind == KIND_PROBE) {
       // field jets at the point: value, gradient and (2D) Hessian (d11, d12, d22) per field;
-      // the 1D kernels carry no second y-derivative of the fields, so 1D writes 0 there
+      // the 1D kernels carry no second y-derivative of the fields, so 1D writes 0 there;
+      // CCF adds g = Theta / y (the Hilbert operator's integrand)
       if (lane == 0 && A.r) {
-        constexpr int NJ = 1 + D + (D == 1 ? 1 : 3);
-        double* o = A.r + pt * (NF * NJ);
+        double* o = A.r + pt * (NF * NJ + (EQ == GN_CCF ? 1 : 0));
 #pragma unroll
         for (int f = 0; f < NF; f++) {
           o[f * NJ] = F[f].v.v;
@@ -337,8 +338,27 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
 #pragma unroll
           for (int k = 0; k < (D == 1 ? 1 : 3); k++) o[f * NJ + 1 + D + k] = (D == 1) ? 0.0 : F[f].h[k].v;
         }
+        if (EQ == GN_CCF) {
+          const YJ<D> Eg = envelope<D>(y, u, 1, dconst(-1.0) + 0.5 * (lamd * a));
+          o[NF * NJ] = (Eg.v * nn[0][0]).v;
+        }
       }
       continue;
+    }
+
+    // stage 2: Phi = Phi_1 + eps Phi_2, Phi_1 a constant (its jets precomputed at this point)
+    if (A.base && kind != KIND_NODE) {
+      const double* b = A.base + pt * A.base_ld;
+      const double ep = A.eps;
+#pragma unroll
+      for (int f = 0; f < NF; f++) {
+        F[f].v = Dl{b[f * NJ] + ep * F[f].v.v, ep * F[f].v.d};
+#pragma unroll
+        for (int i = 0; i < D; i++) F[f].g[i] = Dl{b[f * NJ + 1 + i] + ep * F[f].g[i].v, ep * F[f].g[i].d};
+#pragma unroll
+        for (int k = 0; k < (D == 1 ? 1 : 3); k++)
+          F[f].h[k] = Dl{b[f * NJ + 1 + D + k] + ep * F[f].h[k].v, ep * F[f].h[k].d};
+      }
     }
 
     // residuals (or the single value of a wall/node/norm row)
@@ -353,7 +373,8 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
         // U = sum_j K_ij g_j + D_i g(y_i); the K part's d/dlambda is added by
         // the Hilbert contraction (it carries the lambda column of J_g).
         const YJ<D> Eg = envelope<D>(y, u, 1, dconst(-1.0) + 0.5 * (lamd * a));
-        const Dl gi = Eg.v * nn[0][0];
+        Dl gi = Eg.v * nn[0][0];
+        if (A.base) gi = Dl{A.base[pt * A.base_ld + NF * NJ] + A.eps * gi.v, A.eps * gi.d};
         const Dl Uv = dconst(A.ug[pt]) + A.dcoef[pt] * gi;
         const YJ<D>& T = F[0];
         R[0] = (-1.0) * (lamd * T.v) + (y[0] * opl + Uv) * T.g[0];
@@ -383,6 +404,7 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
     } else {  // KIND_NODE (CCF): g = y/u * NN * q^{-lambda}
       const YJ<D> Eg = envelope<D>(y, u, 1, dconst(-1.0) + 0.5 * (lamd * a));
       R[0] = Eg.v * nn[0][0];
+      if (A.base) R[0] = Dl{A.base[pt] + A.eps * R[0].v, A.eps * R[0].d};
     }
 
     // ---- 4. rows ------------------------------------------------------------

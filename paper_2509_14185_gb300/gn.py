@@ -106,6 +106,7 @@ EXPORTS = {
     "gn_batch_destroy": (ctypes.c_int, [_P]),
     "gn_set_gram_split": (ctypes.c_int, [_P, ctypes.c_int]),
     "gn_set_lambda_trainable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gn_set_stage1": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _D, _D]),
     "gn_lambda_inference": (ctypes.c_int, [_P, _P, _D, ctypes.POINTER(_D)]),
     "gn_signed_max_residual": (ctypes.c_int, [_P, _P, _D, _D, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
     "gn_funnel_next": (ctypes.c_int, [_P, _P, ctypes.c_int, _D, ctypes.POINTER(_D)]),
@@ -237,6 +238,12 @@ class GNProblem:
 
     def gn_set_lambda_trainable(self, trainable):
         _check(lib().gn_set_lambda_trainable(self.h, int(bool(trainable))), "gn_set_lambda_trainable")
+
+    def gn_set_stage1(self, widths1, theta1, lam, eps):
+        """Make this problem the second stage of a fit whose first stage is (widths1, theta1)."""
+        w = (ctypes.c_int * len(widths1))(*[int(v) for v in widths1])
+        _check(lib().gn_set_stage1(self.h, len(widths1) - 1, w, _ptr(theta1), float(lam), float(eps)),
+               "gn_set_stage1")
 
     def gn_lambda_inference(self, theta, lam):
         out = _D()
