@@ -756,7 +756,6 @@ cudaError_t ensure_chol_streams(gn_handle* h) {
   cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
   if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->st_hi, cudaStreamNonBlocking, greatest);
   if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->st_lo, cudaStreamNonBlocking, least);
-  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->st_mid, cudaStreamNonBlocking, greatest);
   return e;
 }
 
@@ -788,9 +787,9 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
     const cudaError_t e = ensure_chol_streams(h);
     if (e != cudaSuccess) return e;
   }
-  cudaStream_t sh = h->st_hi, sl = h->st_lo, sm = h->st_mid;
+  cudaStream_t sh = h->st_hi, sl = h->st_lo;
   const int64_t nstrip = (n + kStrip - 1) / kStrip;
-  std::vector<cudaEvent_t> evs(2 * nstrip + 5, nullptr);
+  std::vector<cudaEvent_t> evs(2 * nstrip + 3, nullptr);
   cudaError_t err = cudaSuccess;
   for (auto& e : evs)
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
@@ -805,10 +804,6 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
   cudaEvent_t* evA = evs.data();            // [t]: strip t's next-columns update done
   cudaEvent_t* evB = evs.data() + nstrip;   // [t]: strip t's deferred bulk update done
   cudaEvent_t e0 = evs[2 * nstrip], e_hi = evs[2 * nstrip + 1], e_lo = evs[2 * nstrip + 2];
-  // in-strip updates: the rows below the diagonal block run on sm beside the diagonal factor
-  // (ev_ready: the strip operand rows they read are written; ev_mid: they are done).  Each
-  // wait is enqueued before the event is recorded again, so two events serve every panel.
-  cudaEvent_t ev_ready = evs[2 * nstrip + 3], ev_mid = evs[2 * nstrip + 4];
   std::vector<char> launchedB(nstrip, 0);
   auto fail = [&](int code) {
     *rc_out = code;
@@ -836,26 +831,11 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
     for (int64_t k0 = s0; k0 < s1; k0 += NB) {
       const int kb = (int)((n - k0) < NB ? (n - k0) : NB);
       const int kofs = (int)(k0 - s0);
-      bool mid = false;
       if (kofs > 0) {
-        // U[k0:, k0:k0+kb] += L[k0:, s0:k0] L[k0:k0+kb, s0:k0]^T, split by rows: the diagonal
-        // block (all the diagonal factor needs) on the critical path, the rows below on sm,
-        // overlapping the factor; the panel solve waits for both.  Each output element is the
-        // same product either way, so the split changes no bit of the result.
+        // U[k0:, k0:k0+kb] += L[k0:, s0:k0] L[k0:k0+kb, s0:k0]^T
         OzOperand v = oz_operand_rows(strip, S, k0 - s0);
         v.kuse = kofs;
-        const int64_t below = n - k0 - kb;
-        if (below > 0) {
-          if ((err = cudaEventRecord(ev_ready, sh)) != cudaSuccess) return err;
-          if ((err = cudaStreamWaitEvent(sm, ev_ready, 0)) != cudaSuccess) return err;
-          OzOperand vb = oz_operand_rows(v, S, kb);
-          rc = oz_gemm(S, false, vb, v, below, kb, reinterpret_cast<double*>(U + (k0 + kb) * n + k0), n, 3, nullptr,
-                       h->flag + 2, sm);
-          if (rc) return fail(rc);
-          if ((err = cudaEventRecord(ev_mid, sm)) != cudaSuccess) return err;
-          mid = true;
-        }
-        rc = oz_gemm(S, false, v, v, kb, kb, reinterpret_cast<double*>(U + k0 * n + k0), n, 3, nullptr,
+        rc = oz_gemm(S, false, v, v, n - k0, kb, reinterpret_cast<double*>(U + k0 * n + k0), n, 3, nullptr,
                      h->flag + 2, sh);
         if (rc) return fail(rc);
       }
@@ -864,7 +844,6 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
       if (err != cudaSuccess) return err;
       const int64_t k1 = k0 + kb;
       if (k1 >= n) break;
-      if (mid && (err = cudaStreamWaitEvent(sh, ev_mid, 0)) != cudaSuccess) return err;
       err = launch_panel_split(S, A, lda, k0, kb, k1, n, Uk, n, LinvDF + (k0 / NB) * NB * NB,
                                scales + (k0 / NB) * NB, strip, strip.e + (kofs / NB) * estride, s0, kofs, yDF,
                                b ? w : nullptr, flag, sh);
