@@ -73,10 +73,15 @@ def parse():
     ap.add_argument("--funnel", action="store_true",
                     help="funnel inference of lambda over a batch of fits at fixed lambda (own JSON line)")
     ap.add_argument("--funnel-fits", type=int, default=16)
+    ap.add_argument("--funnel-workload", default="ccf_stable", choices=["ccf_stable", "ccf_unstable1", "ipm"])
+    ap.add_argument("--funnel-relax", type=int, default=100,
+                    help="GN steps at the seed lambda before the first r_hat (the fit relaxes first)")
     ap.add_argument("--funnel-iters", type=int, default=6)
     ap.add_argument("--funnel-steps", type=int, default=20)
     ap.add_argument("--funnel-radius", type=float, default=0.1)
     ap.add_argument("--funnel-dlam", type=float, default=0.01)
+    ap.add_argument("--eager", action="store_true",
+                    help="--workload batched: one host worker thread per stream instead of the batched graph")
     ap.add_argument("--graph", action="store_true",
                     help="step through the captured CUDA graphs (gn_step_graph; batched: one graph launch per "
                          "batched step, gn_batch_graph_step)")
@@ -383,8 +388,7 @@ def run_funnel(args):
     from paper_2509_14185_gb300 import build as B
     B.build()
     from paper_2509_14185_gb300 import gn, inputs
-    name = args.workload if args.workload != "batched" else "ccf_stable"
-    make = inputs.WORKLOADS[name]
+    make = inputs.WORKLOADS[args.funnel_workload]
     seed0 = make.__defaults__[0]
     fits = []
     for f in range(args.funnel_fits):
@@ -401,6 +405,8 @@ def run_funnel(args):
     hist_l = [[l] for l in lams]
     hist_r = [[] for _ in fits]
     iter_ms, losses = [], []
+    for _ in range(args.funnel_relax):      # relax at the seed lambda first
+        lams2, gams, infos, st = batch.gn_batch_graph_step(lams, gams)
     for it in range(args.funnel_iters):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -424,7 +430,8 @@ def run_funnel(args):
     batch.close()
     final = [h[-1] for h in hist_l]
     print(json.dumps({"mode": "funnel_inference", "workload": fits[0].name, "fits": len(fits),
-                      "precision": args.precision, "steps_per_iteration": args.funnel_steps,
+                      "precision": args.precision, "relax_steps": args.funnel_relax,
+                      "steps_per_iteration": args.funnel_steps,
                       "radius": args.funnel_radius, "dlambda": args.funnel_dlam,
                       "ms_per_iteration": statistics.median(iter_ms),
                       "fit_steps_per_s": len(fits) * args.funnel_steps / (statistics.median(iter_ms) * 1e-3),
@@ -766,7 +773,7 @@ def run_batched(args):
     thetas = [torch.tensor(w.theta, dtype=torch.float64, device="cuda") for w in fits]
     lams = [w.lam for w in fits]
     gams = [w.gamma for w in fits]
-    if args.graph:
+    if args.graph or not args.eager:
         batch.gn_batch_capture_graph(thetas)
         step = lambda l, g: batch.gn_batch_graph_step(l, g)
     else:
@@ -818,7 +825,8 @@ def run_batched(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": f"batched_ccf_sweep_{n}_fits", "fits": n,
-                           "launch": "one CUDA graph launch per batched step (every fit a branch)" if args.graph
+                           "launch": "one CUDA graph launch per batched step (every fit a branch)"
+                           if (args.graph or not args.eager)
                            else f"{args.streams} streams, one host worker thread each",
                            "params_range": [min(Pps), max(Pps)], "n_pts_range": [min(rows) - 1, max(rows) - 1],
                            "gram_precision": args.precision if args.precision == "fp64"
