@@ -102,6 +102,20 @@ class Jet:
         t1 = 1.0 - t * t
         return self.chain(t, t1, -2.0 * t * t1)
 
+    def cos(self):
+        c, sn = np.cos(self.v), np.sin(self.v)
+        return self.chain(c, -sn, -c)
+
+    def sin(self):
+        c, sn = np.cos(self.v), np.sin(self.v)
+        return self.chain(sn, c, -sn)
+
+    @staticmethod
+    def vconcat(a, b):
+        """Rows of a on top of rows of b (components (rows, n))."""
+        return Jet(np.concatenate([a.v, b.v]), [np.concatenate([x, y]) for x, y in zip(a.g, b.g)],
+                   [[np.concatenate([x, y]) for x, y in zip(r, t)] for r, t in zip(a.h, b.h)])
+
     def matvec(self, W, b=None):
         """Affine map a = W h + b applied to a jet whose components are (in, n) arrays.
         The bias enters the value only; derivatives pass through W linearly."""

@@ -108,7 +108,7 @@ class Problem:
     """One profile fit: equation, MLP widths, collocation and wall points, loss weights."""
 
     def __init__(self, equation, widths, y, y_bnd=None, rho=None, c_bnd=1.0,
-                 y_norm=(1.0, 0.0), c_norm=1.0, c_norm_w=1.0, hilbert_m=1024, stage1=None):
+                 y_norm=(1.0, 0.0), c_norm=1.0, c_norm_w=1.0, hilbert_m=1024, stage1=None, fourier=None):
         self.eq = int(equation)
         self.widths = list(widths)
         self.d = DIM[self.eq]
@@ -127,8 +127,14 @@ class Problem:
         self.c_norm_w = float(c_norm_w)
         self.M = int(hilbert_m)
         self.ne = N_EQ[self.eq]
+        # Fourier-feature network (Methods, "Multi-stage Training", item 2): fourier = B, an
+        # (m' x m) array drawn by the caller; the layer after the linear input layer (widths[1]
+        # = m) is the fixed map x -> [cos(B x), sin(B x)] (widths[2] = 2 m'), not trained.
+        self.fourier = None if fourier is None else np.asarray(fourier, dtype=np.float64)
+        if self.fourier is not None:
+            assert self.fourier.shape == (self.widths[2] // 2, self.widths[1]) and self.widths[2] % 2 == 0
         self.P = sum(self.widths[i] * self.widths[i + 1] + self.widths[i + 1]
-                     for i in range(len(self.widths) - 1))
+                     for i in range(len(self.widths) - 1) if not (self.fourier is not None and i == 1))
         self.n_rows = self.n * self.ne + self.nb + 1
         # Multi-stage training (Methods, "Multi-stage Training"): stage1 = (widths1, theta1, eps)
         # makes every field Phi = Phi_1 + eps Phi_2 with Phi_1 the frozen stage-1 network and
@@ -142,11 +148,15 @@ class Problem:
             self.stage1 = (w1, np.asarray(th1, dtype=np.float64), float(eps))
 
     # -- network ----------------------------------------------------------
-    def layers(self, theta, widths=None):
+    def layers(self, theta, widths=None, fourier=None):
+        """(W, b) per layer from theta; with a Fourier layer its entry is (B, None), not in theta."""
         widths = self.widths if widths is None else widths
         out, off = [], 0
         for i in range(len(widths) - 1):
             fi, fo = widths[i], widths[i + 1]
+            if fourier is not None and i == 1:
+                out.append((fourier, None))
+                continue
             W = theta[off:off + fi * fo].reshape(fo, fi)
             off += fi * fo
             b = theta[off:off + fo]
@@ -155,13 +165,21 @@ class Problem:
         assert off == len(theta)
         return out
 
-    def mlp(self, theta, z, widths=None):
-        """tanh MLP with linear last layer applied to the input jet z (components (d_in, n))."""
+    def mlp(self, theta, z, widths=None, fourier=None):
+        """tanh MLP with linear last layer applied to the input jet z (components (d_in, n)).
+        With a Fourier layer: linear input layer (no activation), then [cos(B x), sin(B x)]."""
         h = z
-        L = self.layers(theta, widths)
+        L = self.layers(theta, widths, fourier)
         for i, (W, b) in enumerate(L):
             a = h.matvec(W, b)
-            h = a if i == len(L) - 1 else a.tanh()
+            if i == len(L) - 1:
+                h = a
+            elif fourier is not None and i == 0:
+                h = a
+            elif fourier is not None and i == 1:
+                h = Jet.vconcat(a.cos(), a.sin())
+            else:
+                h = a.tanh()
         return h
 
     # -- ansatz -------------------------------------------------------------
@@ -188,7 +206,7 @@ class Problem:
         else:
             beta = yj[1] / u.sqrt()
             z = Jet.stack([q, beta])
-        nn = self.mlp(theta, z, widths)
+        nn = self.mlp(theta, z, widths, self.fourier if widths is None else None)
         out = []
         for a, (kind, k) in enumerate(field_specs(self.eq, lam)):
             out.append(_prefactor(kind, yj, u) * nn[a] * q.pow(-k))
