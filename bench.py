@@ -69,7 +69,8 @@ def parse():
     ap.add_argument("--streams", type=int, default=8, help="--workload batched: CUDA streams (host workers)")
     ap.add_argument("--multistage", action="store_true",
                     help="two-stage training (stage 2 learns the error of stage 1; own JSON line)")
-    ap.add_argument("--stage-steps", type=int, nargs=2, default=[200, 200])
+    ap.add_argument("--stage-steps", type=int, nargs=2, default=[300, 300])
+    ap.add_argument("--ms-workload", default="burgers_half", choices=["burgers_half", "ccf_stable"])
     ap.add_argument("--funnel", action="store_true",
                     help="funnel inference of lambda over a batch of fits at fixed lambda (own JSON line)")
     ap.add_argument("--funnel-fits", type=int, default=16)
@@ -322,55 +323,102 @@ def micro_jacobian(args):
 
 
 def run_multistage(args):
-    """Two-stage training (Methods, "Multi-stage Training") on the GPU: stage 1 trains the
-    workload's network for --stage-steps[0] damped GN steps (lambda trainable, captured
-    graphs); stage 2 freezes it and trains a second network of the same shape on the
-    stage-2 problem (fields Phi_1 + eps Phi_2, rows / eps, lambda fixed, eps = the stage-1
-    max residual on the collocation points) for --stage-steps[1] steps.  Reports the max d0
-    residual on a dense validation grid after each stage and the device time of each."""
+    """Two-stage training (Methods, "Multi-stage Training") on the GPU.  Stage 1 trains the
+    workload's network at its fixed lambda (Burgers: the admissible lambda = 1/2) for
+    --stage-steps[0] damped GN steps (captured graphs); eps = its max residual on the
+    collocation points.  Stage 2 freezes it and trains a second network on the stage-2
+    problem (fields Phi_1 + eps Phi_2, rows / eps) for --stage-steps[1] steps, in two
+    variants: a tanh MLP of the stage-1 shape, and the paper's Fourier-feature network whose
+    B ~ N(0, sigma^2) has sigma = 2 pi f_d, f_d the dominant frequency of the stage-1
+    residual as a function of the network input q (FFT on a uniform q grid).  Reports the max
+    d0 residual on a dense grid inside the training range after each stage, and for Burgers
+    the max error against the closed-form profile (U^3 + U + y = 0)."""
+    import numpy as np
     import torch
     from paper_2509_14185_gb300 import build as B
     B.build()
     from paper_2509_14185_gb300 import gn, inputs
-    name = args.workload if args.workload in ("ccf_stable", "ccf_unstable1") else "ccf_stable"
-    w = inputs.WORKLOADS[name]()
+    w = inputs.WORKLOADS[args.ms_workload]()
     prec = {"fp64": gn.GN_PREC_FP64, "split": gn.GN_PREC_SPLIT_BF16, "split_all": gn.GN_PREC_SPLIT_ALL}[args.precision]
-    grid = validation_grid_1d()
+    grid = np.concatenate([10.0 ** np.linspace(-3, 3, 60000), np.linspace(1e-3, 10.0, 40000)]).reshape(1, -1)
 
-    def steps(prob, theta, lam, gam, n):
+    def make(widths, fourier=None, pts=None):
+        return gn.GNProblem(w.equation, widths, w.y if pts is None else pts, y_norm=w.y_norm, c_norm=w.c_norm,
+                            hilbert_m=w.hilbert_m, precision=prec, n_slices=args.slices, fourier_B=fourier)
+
+    def train(prob, theta, lam, n):
+        gam, hist = w.gamma, []
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()
-        hist = []
-        for k in range(n):
-            rc, lam, gam, info = prob.gn_step_graph(theta, lam, gam)
+        for _ in range(n):
+            rc, lam2, gam, info = prob.gn_step_graph(theta, lam, gam)
             hist.append(info["loss_after"])
         e1.record()
         torch.cuda.synchronize()
-        return lam, gam, e0.elapsed_time(e1), hist
+        return e0.elapsed_time(e1) * 1e-3, hist
 
-    p1 = gn.GNProblem.from_workload(w, precision=prec, n_slices=args.slices)
+    lam = w.lam
+    p1 = make(w.widths)
+    p1.gn_set_lambda_trainable(False)
     th1 = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
-    lam, gam, ms1, h1 = steps(p1, th1, w.lam, w.gamma, args.stage_steps[0])
+    s1, h1 = train(p1, th1, lam, args.stage_steps[0])
     eps = p1.gn_max_residual(th1, lam)
-    val1 = gn.GNProblem(w.equation, w.widths, grid, y_norm=w.y_norm, c_norm=w.c_norm, hilbert_m=w.hilbert_m)
-    res1 = val1.gn_max_residual(th1, lam)
-    p2 = gn.GNProblem.from_workload(w, precision=prec, n_slices=args.slices)
-    p2.gn_set_stage1(w.widths, th1, lam, eps)
-    th2 = torch.tensor(inputs.xavier_init(w.widths, 777), dtype=torch.float64, device="cuda")
-    lam2, gam2, ms2, h2 = steps(p2, th2, lam, w.gamma, args.stage_steps[1])
-    val2 = gn.GNProblem(w.equation, w.widths, grid, y_norm=w.y_norm, c_norm=w.c_norm, hilbert_m=w.hilbert_m)
-    val2.gn_set_stage1(w.widths, th1, lam, eps)
-    res2 = val2.gn_max_residual(th2, lam)
-    print(json.dumps({"mode": "multistage", "workload": w.name, "precision": args.precision,
-                      "grid_points": int(grid.shape[1]), "lambda": lam, "eps": eps,
-                      "stage1": {"steps": len(h1), "device_s": ms1 * 1e-3, "loss": h1[-1],
-                                 "max_res_train": eps, "max_res_grid": res1},
-                      "stage2": {"steps": len(h2), "device_s": ms2 * 1e-3, "loss": h2[-1],
-                                 "max_res_train": p2.gn_max_residual(th2, lam), "max_res_grid": res2},
-                      "gain_grid": res1 / res2 if res2 > 0 else None,
-                      "stage2_loss_curve": h2[:: max(1, len(h2) // 10)]}))
-    for q in (p1, p2, val1, val2):
+    v1 = make(w.widths, pts=grid)
+    res1 = v1.gn_max_residual(th1, lam)
+
+    def exact_err(fields):
+        if w.equation != inputs.BURGERS:
+            return None
+        yv = grid[0]
+        sq = np.sqrt(yv * yv / 4.0 + 1.0 / 27.0)
+        U = np.cbrt(-yv / 2.0 + sq) + np.cbrt(-yv / 2.0 - sq)
+        return float(np.max(np.abs(fields - U)))
+
+    U1 = p1.gn_field_jets(th1, lam, grid).cpu().numpy()[:, 0]
+    out = {"mode": "multistage", "workload": w.name, "precision": args.precision, "lambda": lam,
+           "grid": "1e5 points inside the training range", "eps": eps,
+           "stage1": {"steps": len(h1), "device_s": s1, "loss": h1[-1], "max_res_grid": res1,
+                      "max_err_exact": exact_err(U1)}}
+
+    # dominant frequency of the stage-1 residual in the network input q = (1 + y^2)^(-1/(2(1+lam)))
+    qg = np.linspace((1.0 + 1e6) ** (-0.5 / (1.0 + lam)), (1.0 + 1e-6) ** (-0.5 / (1.0 + lam)), 4096)
+    yq = np.sqrt(np.maximum(qg ** (-2.0 * (1.0 + lam)) - 1.0, 1e-12)).reshape(1, -1)
+    vq = make(w.widths, pts=yq)
+    r, _ = vq.residual(th1, lam)
+    Rq = r.cpu().numpy()[:-1] / np.sqrt(2.0 / yq.shape[1])
+    spec = np.abs(np.fft.rfft(Rq - Rq.mean()))
+    kd = int(np.argmax(spec[1:]) + 1)
+    f_d = kd / (qg[-1] - qg[0])
+    sigma = 2.0 * np.pi * f_d
+    out["fourier_sigma"] = sigma
+    out["residual_dominant_frequency"] = f_d
+
+    m, mf = 16, 16
+    variants = [("tanh", list(w.widths), None,
+                 inputs.xavier_init(w.widths, 777)),
+                ("fourier", [1, m, 2 * mf, w.widths[-2], 1], sigma * inputs.normal(778, mf * m).reshape(mf, m),
+                 None)]
+    for name, widths2, Bm, th_init in variants:
+        if th_init is None:
+            P2 = (widths2[0] * m + m) + (2 * mf * widths2[3] + widths2[3]) + (widths2[3] + 1)
+            th_init = 0.3 * inputs.normal(779, P2)
+        p2 = make(widths2, Bm)
+        p2.gn_set_stage1(w.widths, th1, lam, eps)
+        th2 = torch.tensor(th_init, dtype=torch.float64, device="cuda")
+        s2, h2 = train(p2, th2, lam, args.stage_steps[1])
+        v2 = make(widths2, Bm, pts=grid)
+        v2.gn_set_stage1(w.widths, th1, lam, eps)
+        res2 = v2.gn_max_residual(th2, lam)
+        U2 = v2.gn_field_jets(th2, lam, grid).cpu().numpy()[:, 0]
+        out["stage2_" + name] = {"mlp": widths2, "steps": len(h2), "device_s": s2, "loss": h2[-1],
+                                 "max_res_grid": res2, "gain_max_res": res1 / res2 if res2 > 0 else None,
+                                 "max_err_exact": exact_err(U1 + eps * U2),
+                                 "loss_curve": h2[:: max(1, len(h2) // 6)]}
+        for q in (p2, v2):
+            q.close()
+    print(json.dumps(out))
+    for q in (p1, v1, vq):
         q.close()
     return 0
 

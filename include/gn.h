@@ -111,6 +111,14 @@ typedef struct gn_problem {
   int hilbert_m;             /* CCF only: nodes M of the discrete Hilbert operator (even, 8..16384) */
   int precision;             /* enum gn_precision used by gn_step for the Gram */
   int n_slices;              /* split precision only: BF16 slices per FP64 value (1..6) */
+  int fourier_m;             /* 0: tanh MLP.  > 0: Fourier-feature network (Methods, "Multi-stage
+                                Training", item 2): layer 0 is the linear input layer (no
+                                activation, widths[1] = m), layer 1 the fixed map
+                                x -> [cos(B x), sin(B x)] (widths[2] = 2 fourier_m, no parameters,
+                                not in theta), then tanh layers and the linear output layer;
+                                n_layers >= 3 */
+  const double* fourier_B;   /* host [fourier_m x widths[1]] row-major, B ~ N(0, sigma^2) drawn by
+                                the caller; copied by gn_init */
 } gn_problem;
 
 /* Normalisation row (data loss) per equation, fixed by the library:
@@ -325,6 +333,15 @@ int gn_lambda_inference(gn_handle* h, const double* theta, double lambda, double
  * point index.  Overwrites the handle's residual buffer.  Synchronises. */
 int gn_signed_max_residual(gn_handle* h, const double* theta, double lambda, double radius, double* r_hat,
                            int64_t* point);
+
+/* The profile itself: the handle's network fields Phi_A (Eq. ansatz_vorticity and its
+ * generalisation, envelopes included) at caller points.  y: device SoA [d][n]; out: device
+ * [n][ld] with ld from gn_field_jets_ld: per field its value, gradient (d entries) and
+ * Hessian (2D: d11, d12, d22; 1D: one 0), then for CCF the value of g = Theta / y.  In a
+ * stage-2 handle these are Phi_2's fields (the composed profile is Phi_1 + eps Phi_2).
+ * Asynchronous on the handle's stream.  Cites: Methods, "Solution Modeling". */
+int gn_field_jets(gn_handle* h, const double* theta, double lambda, const double* y, int64_t n, double* out);
+int gn_field_jets_ld(const gn_handle* h, int64_t* ld);
 
 /* The funnel-inference update (item 3): n = 1: lambda_0 + dlambda; n >= 2: the secant zero
  * through the last two pairs, lambda_n - r_n (lambda_n - lambda_{n-1}) / (r_n - r_{n-1}).

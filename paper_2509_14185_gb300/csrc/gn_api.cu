@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "gn_internal.cuh"
 
@@ -55,6 +56,9 @@ int validate(const gn_problem* p) {
     if (p->hilbert_m < 8 || p->hilbert_m > 16384 || (p->hilbert_m & 1)) return GN_ERR_INVALID;
   }
   if (p->precision < GN_PREC_FP64 || p->precision > GN_PREC_SPLIT_ALL) return GN_ERR_INVALID;
+  if (p->fourier_m < 0) return GN_ERR_INVALID;
+  if (p->fourier_m > 0 && (p->n_layers < 3 || p->widths[2] != 2 * p->fourier_m || !p->fourier_B))
+    return GN_ERR_INVALID;
   if (p->precision != GN_PREC_FP64 && (p->n_slices < 1 || p->n_slices > 6)) return GN_ERR_INVALID;
   return GN_OK;
 }
@@ -69,7 +73,7 @@ cudaError_t dalloc(T** p, size_t count) {
 void free_all(gn_handle* h) {
   void* ptrs[] = {h->ema_ws, h->wt, h->theta_t, h->r, h->J, h->G, h->A, h->Linv, h->g, h->delta, h->vtmp, h->red,
                   h->flag, h->gpart, h->kf, h->dcoef, h->snode, h->gnode, h->Jg, h->ug, h->sU, h->tnode,
-                  h->split_ws, h->base_int, h->base_wall, h->base_norm, h->base_node};
+                  h->split_ws, h->base_int, h->base_wall, h->base_norm, h->base_node, h->fourierW};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->hpin) cudaFreeHost(h->hpin);
@@ -97,6 +101,7 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
   a.lamp = ps.lamp;
   a.flag = h->flag;
   a.lam_frozen = h->lam_frozen;
+  a.fW = h->fourierW;
   a.eps = h->stage_eps;
   a.base_ld = h->base_ld;
   // stage 2: rows are R(Phi_1 + eps Phi_2) / eps (unless the caller wants R itself)
@@ -344,11 +349,17 @@ int gn_init(const gn_problem* p, void* cuda_stream, gn_handle** out) {
     net.w[l] = p->widths[l];
     if (net.w[l] > net.maxw) net.maxw = net.w[l];
   }
+  net.fourier = p->fourier_m > 0 ? 1 : 0;
   for (int l = 0; l < net.L; l++) {
-    net.offW[l] = off;
     net.offT[l] = offT;
-    off += (int64_t)net.w[l] * net.w[l + 1];
     offT += (int64_t)net.w[l] * net.w[l + 1];
+    if (net.fourier && l == 1) {   // the fixed Fourier map takes no place in theta
+      net.offW[l] = -1;
+      net.offB[l] = -1;
+      continue;
+    }
+    net.offW[l] = off;
+    off += (int64_t)net.w[l] * net.w[l + 1];
     net.offB[l] = off;
     off += net.w[l + 1];
   }
@@ -370,7 +381,8 @@ int gn_init(const gn_problem* p, void* cuda_stream, gn_handle** out) {
   };
   const int64_t Pp = h->Pp;
   const int64_t nvec = (Pp > h->n_rows ? Pp : h->n_rows);
-  A(dalloc(&h->wt, h->P));
+  A(dalloc(&h->wt, offT > h->P ? offT : h->P));
+  if (net.fourier) A(dalloc(&h->fourierW, (size_t)net.w[2] * net.w[1]));
   A(dalloc(&h->theta_t, h->P));
   A(dalloc(&h->r, h->n_rows));
   if (ok) A(dalloc(&h->J, (size_t)h->jrows * h->ldJ));
@@ -403,6 +415,18 @@ int gn_init(const gn_problem* p, void* cuda_stream, gn_handle** out) {
     return GN_ERR_OOM;
   }
   cudaError_t e = cudaMemsetAsync(h->flag, 0, 4 * sizeof(int), h->st);
+  if (e == cudaSuccess && net.fourier) {
+    // rows [B; B] (cos half, sin half) and their transposed copy at offT[1] of the weight copy
+    const int m = net.w[1], mf = net.w[2] / 2;
+    std::vector<double> rows((size_t)2 * mf * m), tr((size_t)2 * mf * m);
+    for (int o = 0; o < 2 * mf; o++)
+      for (int i = 0; i < m; i++) rows[(size_t)o * m + i] = p->fourier_B[(size_t)(o % mf) * m + i];
+    for (int i = 0; i < m; i++)
+      for (int o = 0; o < 2 * mf; o++) tr[(size_t)i * 2 * mf + o] = rows[(size_t)o * m + i];
+    e = cudaMemcpy(h->fourierW, rows.data(), rows.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(h->wt + net.offT[1], tr.data(), tr.size() * sizeof(double), cudaMemcpyHostToDevice);
+  }
   double yn[2] = {p->y_norm[0], p->y_norm[1]};
   if (e == cudaSuccess) e = cudaMemcpyAsync(norm_point(h), yn, 2 * sizeof(double), cudaMemcpyHostToDevice, h->st);
   if (e == cudaSuccess && h->eq == GN_CCF) e = hilbert_build(p->y, p->n_pts, h->M, h->kf, h->dcoef, h->snode, h->st);

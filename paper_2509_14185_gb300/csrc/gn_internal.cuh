@@ -47,6 +47,9 @@ struct NetDesc {
   int64_t offT[GN_MAX_LAYERS];      // W_l^T offset in the transposed copy (in x out)
   int maxw;                         // widest layer (including input / output)
   int64_t P;                        // parameter count
+  int fourier;                      // 1: layer 0 is linear (no activation) and layer 1 the fixed
+                                    // Fourier map [cos(B x), sin(B x)] (not in theta; its rows
+                                    // are [B; B], its transposed copy sits at offT[1] in wt)
 };
 
 // Arguments of one jet-kernel launch (one point kind).
@@ -84,6 +87,7 @@ struct JetArgs {
   const double* base;
   int64_t base_ld;
   double eps;
+  const double* fW;      // Fourier layer rows [B; B] (2m' x m, row-major) when net.fourier
 };
 
 struct Workspace;
@@ -151,6 +155,7 @@ struct gn_handle {
   double* base_wall = nullptr;    // [n_bnd][base_ld]
   double* base_norm = nullptr;    // [base_ld]
   double* base_node = nullptr;    // [Mh] (CCF)
+  double* fourierW = nullptr;     // Fourier layer rows [B; B] (2m' x m), when the network has one
 };
 
 namespace gn {

@@ -200,10 +200,11 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
       const int in = net.w[l], out = net.w[l + 1];
       const double* hin = H + (int64_t)l * CF * ldw;
       const double* wtl = A.wt + net.offT[l];
+      const bool fixed = net.fourier && l == 1;   // the Fourier map: no bias, not in theta
       const double* bl = A.theta + net.offB[l];
       for (int o = lane; o < out; o += 32) {
         double acc[CF];
-        acc[0] = bl[o];
+        acc[0] = fixed ? 0.0 : bl[o];
 #pragma unroll
         for (int c = 1; c < CF; c++) acc[c] = 0.0;
         for (int i = 0; i < in; i++) {
@@ -214,9 +215,22 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
         if (l < L - 1) {
           double* ho = H + (int64_t)(l + 1) * CF * ldw;
           double* ao = AS + (int64_t)l * (CR - 1) * ldw;
-          const double t = tanh(acc[0]);
-          const double t1 = 1.0 - t * t;
-          const double t2 = -2.0 * t * t1;
+          // activation and its first three derivatives: tanh; identity on a Fourier
+          // network's linear input layer; cos / sin on its Fourier layer's two halves
+          double t, t1, t2, t3;
+          if (net.fourier && l == 0) {
+            t = acc[0]; t1 = 1.0; t2 = 0.0; t3 = 0.0;
+          } else if (fixed) {
+            double sn, cs;
+            sincos(acc[0], &sn, &cs);
+            if (o < out / 2) { t = cs; t1 = -sn; t2 = -cs; t3 = sn; }
+            else { t = sn; t1 = cs; t2 = -sn; t3 = -cs; }
+          } else {
+            t = tanh(acc[0]);
+            t1 = 1.0 - t * t;
+            t2 = -2.0 * t * t1;
+            t3 = -2.0 * t1 * t1 - 2.0 * t * t2;
+          }
           ho[o] = t;
           if (D == 1) {
             ho[1 * ldw + o] = t1 * acc[1];
@@ -230,7 +244,6 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
             ho[4 * ldw + o] = t2 * aq * ab + t1 * aqb;
             ho[5 * ldw + o] = t2 * ab * ab + t1 * abb;
             if (CF > 6) {
-              const double t3 = -2.0 * t1 * t1 - 2.0 * t * t2;
               ho[6 * ldw + o] = t3 * aq * aq * aq + 3.0 * t2 * aq * aqq + t1 * acc[6];
               ho[7 * ldw + o] = t3 * aq * aq * ab + t2 * (2.0 * aq * aqb + ab * aqq) + t1 * acc[7];
               ho[8 * ldw + o] = t3 * aq * ab * ab + t2 * (2.0 * ab * aqb + aq * abb) + t1 * acc[8];
@@ -462,7 +475,8 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
         // weight and bias entries: W_l[o][i] = sum_c abar_c[o] h_c[i]; b_l[o] = abar_v[o]
         const int64_t nW = (int64_t)out * in;
         const int64_t off = net.offW[l];
-        for (int64_t idx = lane; idx < nW + out; idx += 32) {
+        const bool fixed = net.fourier && l == 1;   // no parameters: no J columns
+        for (int64_t idx = lane; idx < (fixed ? 0 : nW + out); idx += 32) {
           double v;
           if (idx < nW) {
             const int o = (int)(idx / in);
@@ -478,7 +492,7 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
         }
         if (l == 0) break;
         // hbar_c[i] = sum_o W_l[o][i] abar_c[o]
-        const double* Wl = A.theta + off;
+        const double* Wl = fixed ? A.fW : A.theta + off;
         for (int i = lane; i < in; i += 32) {
           double acc[CR];
 #pragma unroll
@@ -488,17 +502,27 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
 #pragma unroll
             for (int c = 0; c < CR; c++) acc[c] = fma(wv, ab[c * ldw + o], acc[c]);
           }
-          // pull back through the tanh jet of hidden layer l-1 (output H[l])
-          const double t = hin[i];
-          const double t1 = 1.0 - t * t;
-          const double t2 = -2.0 * t * t1;
+          // pull back through the activation jet of hidden layer l-1 (output H[l]): its
+          // derivatives from the stored outputs (tanh: t; Fourier: the cos/sin pair)
+          double t1, t2, t3;
+          if (net.fourier && l - 1 == 0) {
+            t1 = 1.0; t2 = 0.0; t3 = 0.0;
+          } else if (net.fourier && l - 1 == 1) {
+            const int half = in / 2;
+            if (i < half) { const double cs = hin[i], sn = hin[i + half]; t1 = -sn; t2 = -cs; t3 = sn; }
+            else { const double sn = hin[i], cs = hin[i - half]; t1 = cs; t2 = -sn; t3 = -cs; }
+          } else {
+            const double t = hin[i];
+            t1 = 1.0 - t * t;
+            t2 = -2.0 * t * t1;
+            t3 = -2.0 * t1 * t1 - 2.0 * t * t2;
+          }
           const double* as = AS + (int64_t)(l - 1) * (CR - 1) * ldw;
           if (D == 1) {
             const double az = as[i];
             hb[i] = acc[0] * t1 + acc[1] * t2 * az;
             hb[ldw + i] = acc[1] * t1;
           } else {
-            const double t3 = -2.0 * t1 * t1 - 2.0 * t * t2;
             const double aq = as[i], abv = as[ldw + i], aqq = as[2 * ldw + i], aqb = as[3 * ldw + i],
                          abb = as[4 * ldw + i];
             hb[i] = acc[0] * t1 + acc[1] * t2 * aq + acc[2] * t2 * abv + acc[3] * (t3 * aq * aq + t2 * aqq) +
@@ -522,6 +546,7 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
 
 __global__ void transpose_weights_kernel(const NetDesc net, const double* __restrict__ theta, double* wt) {
   for (int l = 0; l < net.L; l++) {
+    if (net.fourier && l == 1) continue;   // the fixed Fourier layer's copy is written once
     const int in = net.w[l], out = net.w[l + 1];
     const int64_t n = (int64_t)in * out;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;

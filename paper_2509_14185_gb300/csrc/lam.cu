@@ -117,6 +117,7 @@ int gn_lambda_inference(gn_handle* h, const double* theta, double lambda, double
   a.eq = h->eq;
   a.theta = theta;
   a.wt = h->wt;
+  a.fW = h->fourierW;
   a.lam = lambda;
   a.flag = h->flag;
   a.mode = MODE_RESIDUAL;
@@ -174,6 +175,37 @@ int gn_signed_max_residual(gn_handle* h, const double* theta, double lambda, dou
   GN_L_TRY(cudaStreamSynchronize(h->st));
   *r_hat = h->hpin[42];
   if (point) *point = (int64_t)h->hpin[43];
+  return GN_OK;
+}
+
+int gn_field_jets(gn_handle* h, const double* theta, double lambda, const double* y, int64_t n, double* out) {
+  if (!h || !theta || !out || n < 0 || (n > 0 && !y)) return GN_ERR_INVALID;
+  if (n == 0) return GN_OK;
+  cudaStream_t st = h->st;
+  GN_L_TRY(launch_transpose_weights(h->net, theta, h->wt, st));
+  JetArgs a;
+  memset(&a, 0, sizeof(a));
+  a.net = h->net;
+  a.eq = h->eq;
+  a.theta = theta;
+  a.wt = h->wt;
+  a.fW = h->fourierW;
+  a.lam = lambda;
+  a.flag = h->flag;
+  a.mode = MODE_RESIDUAL;
+  a.kind = KIND_PROBE;
+  a.n = n;
+  a.y = y;
+  a.ystride = n;
+  a.wscale = 1.0;
+  a.r = out;
+  GN_L_TRY(launch_jet(a, st, nullptr));
+  return GN_OK;
+}
+
+int gn_field_jets_ld(const gn_handle* h, int64_t* ld) {
+  if (!h || !ld) return GN_ERR_INVALID;
+  *ld = probe_ld(h->eq, h->d, h->nf);
   return GN_OK;
 }
 

@@ -54,6 +54,8 @@ class gn_problem(ctypes.Structure):
         ("hilbert_m", ctypes.c_int),
         ("precision", ctypes.c_int),
         ("n_slices", ctypes.c_int),
+        ("fourier_m", ctypes.c_int),
+        ("fourier_B", ctypes.c_void_p),
     ]
 
 
@@ -107,6 +109,8 @@ EXPORTS = {
     "gn_set_gram_split": (ctypes.c_int, [_P, ctypes.c_int]),
     "gn_set_lambda_trainable": (ctypes.c_int, [_P, ctypes.c_int]),
     "gn_set_stage1": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _D, _D]),
+    "gn_field_jets": (ctypes.c_int, [_P, _P, _D, _P, _I64, _P]),
+    "gn_field_jets_ld": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
     "gn_lambda_inference": (ctypes.c_int, [_P, _P, _D, ctypes.POINTER(_D)]),
     "gn_signed_max_residual": (ctypes.c_int, [_P, _P, _D, _D, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
     "gn_funnel_next": (ctypes.c_int, [_P, _P, ctypes.c_int, _D, ctypes.POINTER(_D)]),
@@ -165,7 +169,8 @@ class GNProblem:
     """One profile fit bound to a libgn handle (device memory owned by torch and libgn)."""
 
     def __init__(self, equation, widths, y, y_bnd=None, rho=None, c_bnd=1.0, y_norm=(1.0, 0.0), c_norm=1.0,
-                 c_norm_w=1.0, hilbert_m=1024, precision=GN_PREC_FP64, n_slices=4, device="cuda", stream=None):
+                 c_norm_w=1.0, hilbert_m=1024, precision=GN_PREC_FP64, n_slices=4, device="cuda", stream=None,
+                 fourier_B=None):
         lib()
         self.device = torch.device(device)
         self.equation = int(equation)
@@ -195,6 +200,11 @@ class GNProblem:
         p.hilbert_m = int(hilbert_m)
         p.precision = int(precision)
         p.n_slices = int(n_slices)
+        if fourier_B is not None:
+            # host copy kept alive for gn_init (which copies it)
+            self._fourier_B = np.ascontiguousarray(np.asarray(fourier_B, dtype=np.float64))
+            p.fourier_m = int(self._fourier_B.shape[0])
+            p.fourier_B = self._fourier_B.ctypes.data
         self._prob = p
         self.stream = stream
         h = ctypes.c_void_p()
@@ -244,6 +254,18 @@ class GNProblem:
         w = (ctypes.c_int * len(widths1))(*[int(v) for v in widths1])
         _check(lib().gn_set_stage1(self.h, len(widths1) - 1, w, _ptr(theta1), float(lam), float(eps)),
                "gn_set_stage1")
+
+    def gn_field_jets(self, theta, lam, y):
+        """Field jets of the handle's network at points y (d, n): a device tensor (n, ld)."""
+        y = torch.as_tensor(np.ascontiguousarray(np.asarray(y, dtype=np.float64).reshape(self.d, -1)),
+                            device=self.device)
+        ld = _I64()
+        _check(lib().gn_field_jets_ld(self.h, ctypes.byref(ld)), "gn_field_jets_ld")
+        out = torch.empty((y.shape[1], ld.value), dtype=torch.float64, device=self.device)
+        _check(lib().gn_field_jets(self.h, _ptr(theta), float(lam), _ptr(y), y.shape[1], _ptr(out)),
+               "gn_field_jets")
+        torch.cuda.synchronize(self.device)
+        return out
 
     def gn_lambda_inference(self, theta, lam):
         out = _D()

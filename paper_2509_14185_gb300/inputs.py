@@ -200,6 +200,14 @@ def ccf_unstable_1d(seed: int = 2) -> Workload:
                np.zeros((1, 0)), 0.6057, seed)
 
 
+def burgers_half_1d(seed: int = 6) -> Workload:
+    """Burgers at lambda = 1/2 (the paper's worked example, whose smooth profile with U(-2) = 1
+    is known in closed form): MLP 1-32-32-1, 1024 points (512 log-spaced on [1e-3, 1e3] + 512
+    uniform on [1e-3, 1e3])."""
+    y = points_1d(512, 512, 1e-3, 1e3, seed, uniform_lo=1e-3)
+    return _wl("burgers_half_1d_mlp1x32x32x1_n1024", BURGERS, [1, 32, 32, 1], y, np.zeros((1, 0)), 0.5, seed)
+
+
 def ipm_2d(seed: int = 4) -> Workload:
     """IPM with boundary: MLP 2-64x4-2, 256 log radii in [1e-3, 1e3] x 256 seeded angles,
     plus 4096 wall points; lambda seed 1/0.9723 (the paper's empirical law at n = 0)."""
@@ -260,6 +268,7 @@ def small_case(equation: int, widths: Sequence[int], n_pts: int, n_bnd: int = 0,
 
 
 WORKLOADS = {
+    "burgers_half": burgers_half_1d,
     "ccf_stable": ccf_stable_1d,
     "ccf_unstable1": ccf_unstable_1d,
     "ipm": ipm_2d,

@@ -94,3 +94,26 @@ def test_signed_max_residual_matches_oracle(name):
         assert abs(val_g - val_o) <= TOL * abs(val_o)
     assert prob.gn_signed_max_residual(th, w.lam, 0.5 * r.min()) == (0.0, -1)
     prob.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_field_jets_match_oracle(name):
+    """gn_field_jets (the profile and its derivatives at caller points) vs the oracle's fields."""
+    w = small(name)
+    p = oracle_problem(w)
+    prob = gpu_problem(w)
+    pts = p.y[:, ::7]
+    out = host(prob.gn_field_jets(dev(w.theta), w.lam, pts))
+    F = p.fields(w.theta, w.lam, pts, extra_g=(name == "ccf"))
+    d, nf = p.d, len(F) - (1 if name == "ccf" else 0)
+    nj = 1 + d + (1 if d == 1 else 3)
+    for f in range(nf):
+        assert rel(out[:, f * nj], F[f].v) <= TOL
+        for i in range(d):
+            assert rel(out[:, f * nj + 1 + i], F[f].g[i]) <= TOL
+        if d == 2:
+            for k, (i, j) in enumerate([(0, 0), (0, 1), (1, 1)]):
+                assert rel(out[:, f * nj + 3 + k], F[f].h[i][j]) <= TOL
+    if name == "ccf":
+        assert rel(out[:, nf * nj], F[-1].v) <= TOL
+    prob.close()
