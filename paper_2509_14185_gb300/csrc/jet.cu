@@ -132,13 +132,15 @@ template <int D> __device__ YJ<D> envelope(const double* y, double u, int m, Dl 
   return ymul<D>(Y, Wj);
 }
 
-// Per-warp shared-memory layout (doubles).  H[j][c][ldw]: j = 0 network input,
-// j = 1..L-1 outputs of hidden layers; AS[l][c-1][ldw] derivative components of
+// Per-warp shared-memory layout (doubles).  H[j][c][ldw] for c < C_R: j = 0 network
+// input, j = 1..L-1 outputs of hidden layers (the reverse pass reads them); the forward-only
+// components c >= C_R (the third order the lambda column needs) of layer j live in a
+// two-layer ping-pong X[j & 1][c - C_R][ldw]; AS[l][c-1][ldw] derivative components of
 // hidden pre-activations; BA, BB [C_R][ldw] adjoint ping-pong; NN [NF][CF].
 __host__ __device__ inline int64_t jet_smem_doubles(const NetDesc& net, int CF, int CR, int NF) {
   const int64_t ldw = net.maxw;
-  return (int64_t)net.L * CF * ldw + (int64_t)(net.L - 1) * (CR - 1) * ldw + 2 * (int64_t)CR * ldw +
-         (int64_t)NF * CF + 2;
+  return (int64_t)net.L * CR * ldw + 2 * (int64_t)(CF - CR) * ldw + (int64_t)(net.L - 1) * (CR - 1) * ldw +
+         2 * (int64_t)CR * ldw + (int64_t)NF * CF + 2;
 }
 
 template <int EQ, int MODE>
@@ -155,7 +157,12 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
   extern __shared__ double sm[];
   double* base = sm + (int64_t)warp * jet_smem_doubles(net, CF, CR, NF);
   double* H = base;
-  double* AS = H + (int64_t)L * CF * ldw;
+  double* XH = H + (int64_t)L * CR * ldw;               // forward-only components, ping-pong
+  double* AS = XH + 2 * (int64_t)(CF - CR) * ldw;
+  // component c of layer j's jets
+  auto hc = [&](int j, int c) -> double* {
+    return c < CR ? H + ((int64_t)j * CR + c) * ldw : XH + ((int64_t)(j & 1) * (CF - CR) + (c - CR)) * ldw;
+  };
   double* BA = AS + (int64_t)(L - 1) * (CR - 1) * ldw;
   double* BB = BA + CR * ldw;
   double* NN = BB + CR * ldw;
@@ -183,7 +190,8 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
     if (D == 2) beta = y[1] / sqrt(u);
 
     // ---- 1. network input jets ------------------------------------------
-    for (int idx = lane; idx < CF * ldw; idx += 32) H[idx] = 0.0;
+    for (int idx = lane; idx < CR * ldw; idx += 32) H[idx] = 0.0;
+    for (int idx = lane; idx < (CF - CR) * ldw; idx += 32) XH[idx] = 0.0;
     __syncwarp();
     if (lane == 0) {
       H[0 * ldw + 0] = q.v;
@@ -198,7 +206,9 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
     // ---- 2. forward through the layers ------------------------------------
     for (int l = 0; l < L; l++) {
       const int in = net.w[l], out = net.w[l + 1];
-      const double* hin = H + (int64_t)l * CF * ldw;
+      const double* hinc[CF];
+#pragma unroll
+      for (int c = 0; c < CF; c++) hinc[c] = hc(l, c);
       const double* wtl = A.wt + net.offT[l];
       const bool fixed = net.fourier && l == 1;   // the Fourier map: no bias, not in theta
       const double* bl = A.theta + net.offB[l];
@@ -210,10 +220,12 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
         for (int i = 0; i < in; i++) {
           const double wv = __ldg(wtl + (int64_t)i * out + o);
 #pragma unroll
-          for (int c = 0; c < CF; c++) acc[c] = fma(wv, hin[c * ldw + i], acc[c]);
+          for (int c = 0; c < CF; c++) acc[c] = fma(wv, hinc[c][i], acc[c]);
         }
         if (l < L - 1) {
-          double* ho = H + (int64_t)(l + 1) * CF * ldw;
+          double* hoc[CF];
+#pragma unroll
+          for (int c = 0; c < CF; c++) hoc[c] = hc(l + 1, c);
           double* ao = AS + (int64_t)l * (CR - 1) * ldw;
           // activation and its first three derivatives: tanh; identity on a Fourier
           // network's linear input layer; cos / sin on its Fourier layer's two halves
@@ -231,22 +243,22 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
             t2 = -2.0 * t * t1;
             t3 = -2.0 * t1 * t1 - 2.0 * t * t2;
           }
-          ho[o] = t;
+          hoc[0][o] = t;
           if (D == 1) {
-            ho[1 * ldw + o] = t1 * acc[1];
-            if (CF > 2) ho[2 * ldw + o] = t2 * acc[1] * acc[1] + t1 * acc[2];
+            hoc[1][o] = t1 * acc[1];
+            if (CF > 2) hoc[2][o] = t2 * acc[1] * acc[1] + t1 * acc[2];
             ao[o] = acc[1];
           } else {
             const double aq = acc[1], ab = acc[2], aqq = acc[3], aqb = acc[4], abb = acc[5];
-            ho[1 * ldw + o] = t1 * aq;
-            ho[2 * ldw + o] = t1 * ab;
-            ho[3 * ldw + o] = t2 * aq * aq + t1 * aqq;
-            ho[4 * ldw + o] = t2 * aq * ab + t1 * aqb;
-            ho[5 * ldw + o] = t2 * ab * ab + t1 * abb;
+            hoc[1][o] = t1 * aq;
+            hoc[2][o] = t1 * ab;
+            hoc[3][o] = t2 * aq * aq + t1 * aqq;
+            hoc[4][o] = t2 * aq * ab + t1 * aqb;
+            hoc[5][o] = t2 * ab * ab + t1 * abb;
             if (CF > 6) {
-              ho[6 * ldw + o] = t3 * aq * aq * aq + 3.0 * t2 * aq * aqq + t1 * acc[6];
-              ho[7 * ldw + o] = t3 * aq * aq * ab + t2 * (2.0 * aq * aqb + ab * aqq) + t1 * acc[7];
-              ho[8 * ldw + o] = t3 * aq * ab * ab + t2 * (2.0 * ab * aqb + aq * abb) + t1 * acc[8];
+              hoc[6][o] = t3 * aq * aq * aq + 3.0 * t2 * aq * aqq + t1 * acc[6];
+              hoc[7][o] = t3 * aq * aq * ab + t2 * (2.0 * aq * aqb + ab * aqq) + t1 * acc[7];
+              hoc[8][o] = t3 * aq * ab * ab + t2 * (2.0 * ab * aqb + aq * abb) + t1 * acc[8];
             }
 #pragma unroll
             for (int c = 1; c < 6; c++) ao[(c - 1) * ldw + o] = acc[c];
@@ -471,7 +483,7 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
       double* hb = BB;
       for (int l = L - 1; l >= 0; l--) {
         const int in = net.w[l], out = net.w[l + 1];
-        const double* hin = H + (int64_t)l * CF * ldw;
+        const double* hin = H + (int64_t)l * CR * ldw;   // components c < C_R, ldw apart
         // weight and bias entries: W_l[o][i] = sum_c abar_c[o] h_c[i]; b_l[o] = abar_v[o]
         const int64_t nW = (int64_t)out * in;
         const int64_t off = net.offW[l];
@@ -572,7 +584,7 @@ cudaError_t launch_eq(const JetArgs& a, cudaStream_t st, int64_t* warps_used) {
   constexpr int CR = JT<D>::CR;
   constexpr int CF = (MODE == MODE_RESIDUAL) ? CR : JT<D>::CF;
   const int64_t per_warp = jet_smem_doubles(a.net, CF, CR, NF) * (int64_t)sizeof(double);
-  constexpr int64_t kSmemCap = 200 * 1024;
+  constexpr int64_t kSmemCap = 227 * 1024;   // the opt-in maximum per block
   int wpb = 8;
   while (wpb > 1 && per_warp * wpb > kSmemCap) wpb--;
   if (per_warp > kSmemCap) return cudaErrorInvalidValue;
