@@ -58,7 +58,8 @@ def parse():
                          "benchmark's 1-64-64-64-1 net)")
     ap.add_argument("--equal-residual", action="store_true",
                     help="FP64 path for --er-steps steps vs split path to the same max residual (own JSON line)")
-    ap.add_argument("--er-steps", type=int, default=50)
+    ap.add_argument("--er-steps", type=int, default=50,
+                    help="--equal-residual: FP64 steps (the workload is --workload: ccf_unstable1, ccf_stable or ipm)")
     ap.add_argument("--ema-vs-exact", action="store_true",
                     help="head-to-head on the same kernels: exact-G damped GN vs the paper's EMA rank-1 "
                          "optimiser, loss against device time (own JSON line)")
@@ -99,6 +100,15 @@ def validation_grid_1d(n_log=60000, n_uni=40000):
     return g.reshape(1, -1)
 
 
+def validation_grid_2d(n_r=512, n_a=256):
+    """Dense 2D validation grid (the paper's grids are in its SI): radii log-spaced on
+    [1e-4, 1e4] times angles uniform on [0, pi/2] (quadrant), 131072 points."""
+    import numpy as np
+    r = np.repeat(10.0 ** np.linspace(-4, 4, n_r), n_a)
+    a = np.tile(np.linspace(0.0, 0.5 * np.pi, n_a), n_r)
+    return np.stack([r * np.cos(a), r * np.sin(a)])
+
+
 def equal_residual(args):
     """Residual reached by the FP64 path after N GN steps, and the device time the split
     path needs to reach 1.1x that residual from the same initialisation.  The residual
@@ -109,8 +119,9 @@ def equal_residual(args):
     from paper_2509_14185_gb300 import build as B
     B.build()
     from paper_2509_14185_gb300 import gn, inputs
-    w = inputs.ccf_unstable_1d()
-    grid = validation_grid_1d()
+    name = args.workload if args.workload in ("ccf_unstable1", "ccf_stable", "ipm") else "ccf_unstable1"
+    w = inputs.WORKLOADS[name]()
+    grid = validation_grid_1d() if w.d == 1 else validation_grid_2d()
     val = gn.GNProblem(w.equation, w.widths, grid, y_norm=w.y_norm, c_norm=w.c_norm, hilbert_m=w.hilbert_m)
 
     def run(prec, max_steps, target=None):
