@@ -756,7 +756,6 @@ cudaError_t ensure_chol_streams(gn_handle* h) {
   cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
   if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->st_hi, cudaStreamNonBlocking, greatest);
   if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->st_lo, cudaStreamNonBlocking, least);
-  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->st_mid, cudaStreamNonBlocking, greatest);
   return e;
 }
 
@@ -788,10 +787,9 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
     const cudaError_t e = ensure_chol_streams(h);
     if (e != cudaSuccess) return e;
   }
-  cudaStream_t sh = h->st_hi, sl = h->st_lo, sm = h->st_mid;
+  cudaStream_t sh = h->st_hi, sl = h->st_lo;
   const int64_t nstrip = (n + kStrip - 1) / kStrip;
-  const int64_t npanel = (n + NB - 1) / NB;
-  std::vector<cudaEvent_t> evs(2 * nstrip + 4 + 3 * npanel, nullptr);
+  std::vector<cudaEvent_t> evs(2 * nstrip + 3, nullptr);
   cudaError_t err = cudaSuccess;
   for (auto& e : evs)
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
@@ -806,14 +804,6 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
   cudaEvent_t* evA = evs.data();            // [t]: strip t's next-columns update done
   cudaEvent_t* evB = evs.data() + nstrip;   // [t]: strip t's deferred bulk update done
   cudaEvent_t e0 = evs[2 * nstrip], e_hi = evs[2 * nstrip + 1], e_lo = evs[2 * nstrip + 2];
-  // look-ahead inside a strip, per panel p: evP[p] its diagonal factor is done (sh), evN[p] the
-  // in-strip update of the next block's rows is done (sm), evR[p] the rest of its panel rows
-  // are solved (sm)
-  cudaEvent_t e_mid = evs[2 * nstrip + 3];
-  cudaEvent_t* evP = evs.data() + 2 * nstrip + 4;
-  cudaEvent_t* evN = evP + npanel;
-  cudaEvent_t* evR = evN + npanel;
-  std::vector<char> haveR(npanel, 0);
   std::vector<char> launchedB(nstrip, 0);
   auto fail = [&](int code) {
     *rc_out = code;
@@ -822,7 +812,6 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
   if ((err = cudaEventRecord(e0, st)) != cudaSuccess) return err;
   if ((err = cudaStreamWaitEvent(sh, e0, 0)) != cudaSuccess) return err;
   if ((err = cudaStreamWaitEvent(sl, e0, 0)) != cudaSuccess) return err;
-  if ((err = cudaStreamWaitEvent(sm, e0, 0)) != cudaSuccess) return err;
   if ((err = cudaMemsetAsync(U, 0, (size_t)n * n * sizeof(float2), sh)) != cudaSuccess) return err;
   if (b && (err = cudaMemcpyAsync(w, b, n * sizeof(double), cudaMemcpyDeviceToDevice, sh)) != cudaSuccess) return err;
   for (int64_t t = 0; t < nstrip; t++) {
@@ -838,70 +827,29 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
     strip.kpad = kStrip;
     strip.echunk = NB;
     strip.estride = estride;
-    // The strip's chain with a look-ahead of one block.  Per panel p (rows [k0, k1)), the
-    // critical path on sh only touches the next block's rows [k1, k2): the in-strip update of
-    // the diagonal block, the diagonal factor, and the panel solve of rows [k1, k2).  The
-    // in-strip update of the rows below and the panel solve of rows [k2, n) run on sm beside
-    // it.  Every element sees the same products in the same order as without the split.
-    int64_t last_r = -1;   // the last panel of this strip whose rest rows were solved on sm
+    // the strip's chain: in-strip updates, diagonal factors, panels
     for (int64_t k0 = s0; k0 < s1; k0 += NB) {
-      const int64_t pi = k0 / NB;
       const int kb = (int)((n - k0) < NB ? (n - k0) : NB);
       const int kofs = (int)(k0 - s0);
-      const int64_t k1 = k0 + kb;
-      const int64_t k2 = (k1 + NB < n) ? k1 + NB : n;
-      const float2* Uk = (k0 > 0) ? U : nullptr;
       if (kofs > 0) {
-        // rows [k0, k1) of the panels before p - 1 in this strip are solved on sm
-        if (kofs >= 2 * NB && haveR[pi - 2] && (err = cudaStreamWaitEvent(sh, evR[pi - 2], 0)) != cudaSuccess)
-          return err;
-        // U[k0:k1, k0:k1] += L[k0:k1, s0:k0] L[k0:k1, s0:k0]^T (sh)
+        // U[k0:, k0:k0+kb] += L[k0:, s0:k0] L[k0:k0+kb, s0:k0]^T
         OzOperand v = oz_operand_rows(strip, S, k0 - s0);
         v.kuse = kofs;
-        rc = oz_gemm(S, false, v, v, kb, kb, reinterpret_cast<double*>(U + k0 * n + k0), n, 3, nullptr,
+        rc = oz_gemm(S, false, v, v, n - k0, kb, reinterpret_cast<double*>(U + k0 * n + k0), n, 3, nullptr,
                      h->flag + 2, sh);
         if (rc) return fail(rc);
-        // U[k1:, k0:k1] += L[k1:, s0:k0] L[k0:k1, s0:k0]^T (sm; next block first)
-        if (k1 < n) {
-          OzOperand vn = oz_operand_rows(v, S, kb);
-          rc = oz_gemm(S, false, vn, v, k2 - k1, kb, reinterpret_cast<double*>(U + k1 * n + k0), n, 3, nullptr,
-                       h->flag + 2, sm);
-          if (rc) return fail(rc);
-          if ((err = cudaEventRecord(evN[pi], sm)) != cudaSuccess) return err;
-          if (k2 < n) {
-            OzOperand vf = oz_operand_rows(v, S, kb + (k2 - k1));
-            rc = oz_gemm(S, false, vf, v, n - k2, kb, reinterpret_cast<double*>(U + k2 * n + k0), n, 3, nullptr,
-                         h->flag + 2, sm);
-            if (rc) return fail(rc);
-          }
-        }
       }
+      const float2* Uk = (k0 > 0) ? U : nullptr;
       err = launch_potrf<ArithDF>(A, lda, k0, kb, Uk, n, Linv, LinvDF, scales, b ? w : nullptr, y, yDF, flag, sh);
       if (err != cudaSuccess) return err;
+      const int64_t k1 = k0 + kb;
       if (k1 >= n) break;
-      if ((err = cudaEventRecord(evP[pi], sh)) != cudaSuccess) return err;
-      const float2* LkDF = LinvDF + (k0 / NB) * NB * NB;
-      const int* sck = scales + (k0 / NB) * NB;
-      int* eo = strip.e + (kofs / NB) * estride;
-      // the next block's rows on the critical path
-      if (kofs > 0 && (err = cudaStreamWaitEvent(sh, evN[pi], 0)) != cudaSuccess) return err;
-      err = launch_panel_split(S, A, lda, k0, kb, k1, k2, Uk, n, LkDF, sck, strip, eo, s0, kofs, yDF,
+      err = launch_panel_split(S, A, lda, k0, kb, k1, n, Uk, n, LinvDF + (k0 / NB) * NB * NB,
+                               scales + (k0 / NB) * NB, strip, strip.e + (kofs / NB) * estride, s0, kofs, yDF,
                                b ? w : nullptr, flag, sh);
       if (err != cudaSuccess) return err;
-      // the rest of the panel on sm
-      if (k2 < n) {
-        if ((err = cudaStreamWaitEvent(sm, evP[pi], 0)) != cudaSuccess) return err;
-        err = launch_panel_split(S, A, lda, k0, kb, k2, n, Uk, n, LkDF, sck, strip, eo, s0, kofs, yDF,
-                                 b ? w : nullptr, flag, sm);
-        if (err != cudaSuccess) return err;
-        if ((err = cudaEventRecord(evR[pi], sm)) != cudaSuccess) return err;
-        haveR[pi] = 1;
-        last_r = pi;
-      }
     }
     if (s1 >= n) break;
-    // everything below this strip's panels is solved before the bulk update reads it
-    if (last_r >= 0 && (err = cudaStreamWaitEvent(sh, evR[last_r], 0)) != cudaSuccess) return err;
     // bulk update of the trailing matrix, U[s1:, s1:] += L[s1:, s0:s1] L[s1:, s0:s1]^T
     OzOperand wb = oz_operand_rows(strip, S, s1 - s0);
     // (a) the next strip's columns now, on the critical path; the deferred update of strip
@@ -927,9 +875,7 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
   }
   if ((err = cudaEventRecord(e_hi, sh)) != cudaSuccess) return err;
   if ((err = cudaEventRecord(e_lo, sl)) != cudaSuccess) return err;
-  if ((err = cudaEventRecord(e_mid, sm)) != cudaSuccess) return err;
   if ((err = cudaStreamWaitEvent(st, e_hi, 0)) != cudaSuccess) return err;
-  if ((err = cudaStreamWaitEvent(st, e_mid, 0)) != cudaSuccess) return err;
   return cudaStreamWaitEvent(st, e_lo, 0);
 }
 

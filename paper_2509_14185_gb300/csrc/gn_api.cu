@@ -446,7 +446,6 @@ int gn_destroy(gn_handle* h) {
   graph_release(h);
   if (h->st_hi) cudaStreamDestroy(h->st_hi);
   if (h->st_lo) cudaStreamDestroy(h->st_lo);
-  if (h->st_mid) cudaStreamDestroy(h->st_mid);
   free_all(h);
   if (h->tmaps) free(h->tmaps);
   delete h;

@@ -142,7 +142,6 @@ struct gn_handle {
   // streams of the split factorisation's look-ahead (created on first use)
   cudaStream_t st_hi = nullptr;   // critical path (high priority)
   cudaStream_t st_lo = nullptr;   // deferred bulk updates (low priority)
-  cudaStream_t st_mid = nullptr;  // look-ahead inside a strip: updates and panel rows below the next block
   // graph-captured step (created on first use of gn_step_graph or by a batch capture)
   gn::GraphState* gs = nullptr;
   int capturing = 0;              // a stream capture is in progress: no workspace may grow
