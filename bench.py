@@ -82,8 +82,11 @@ def parse():
     ap.add_argument("--funnel-steps", type=int, default=20)
     ap.add_argument("--funnel-radius", type=float, default=0.1)
     ap.add_argument("--funnel-dlam", type=float, default=0.01)
+    ap.add_argument("--gram-split", type=int, default=0,
+                    help="force the split Gram's split-K factor (0: autotuned per shape)")
     ap.add_argument("--eager", action="store_true",
-                    help="--workload batched: one host worker thread per stream instead of the batched graph")
+                    help="step with gn_step (host decisions between launches) instead of the captured graphs; "
+                         "--workload batched: one host worker thread per stream instead of the batched graph")
     ap.add_argument("--graph", action="store_true",
                     help="step through the captured CUDA graphs (gn_step_graph; batched: one graph launch per "
                          "batched step, gn_batch_graph_step)")
@@ -829,6 +832,9 @@ def run_batched(args):
     fits = replica_workload("batched", rank)
     prec = {"fp64": gn.GN_PREC_FP64, "split": gn.GN_PREC_SPLIT_BF16, "split_all": gn.GN_PREC_SPLIT_ALL}[args.precision]
     batch = gn.GNBatch(fits, n_streams=args.streams, precision=prec, n_slices=args.slices)
+    if args.gram_split:
+        for f in range(len(fits)):
+            gn.lib().gn_set_gram_split(batch.handle(f), int(args.gram_split))
     thetas = [torch.tensor(w.theta, dtype=torch.float64, device="cuda") for w in fits]
     lams = [w.lam for w in fits]
     gams = [w.gamma for w in fits]
@@ -884,6 +890,7 @@ def run_batched(args):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": f"batched_ccf_sweep_{n}_fits", "fits": n,
+                           "gram_split": args.gram_split or "autotuned",
                            "launch": "one CUDA graph launch per batched step (every fit a branch)"
                            if (args.graph or not args.eager)
                            else f"{args.streams} streams, one host worker thread each",
@@ -945,7 +952,8 @@ def main():
     stream = torch.cuda.current_stream()
     theta = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
     lam, gam = w.lam, w.gamma
-    gn_step = prob.gn_step_graph if args.graph else prob.gn_step
+    use_graph = args.graph or not args.eager
+    gn_step = prob.gn_step_graph if use_graph else prob.gn_step
     for _ in range(args.warmup):
         rc, lam, gam, info = gn_step(theta, lam, gam)
         if rc < 0:
@@ -1001,8 +1009,9 @@ def main():
     # per-phase device times (library CUDA events on the launch stream, averaged over the timed steps);
     # a captured graph is timed as a whole, so its phases come from eager steps of the same kernels
     # on a copy of the parameters, after the timed region
-    phase_src = "timed steps"
-    if args.graph:
+    phase_src = "timed steps (CUDA events on the launch stream; inside the graph as event nodes)"
+    phases = [statistics.mean(i["ms_phase"][k] for i in infos) for k in range(7)]
+    if use_graph and phases[1] == 0.0:   # a streamed Jacobian carries no per-phase marks
         th2 = theta.clone()
         l2, g2, pinfos = lam, gam, []
         for _ in range(max(2, min(args.steps, 5))):
@@ -1010,8 +1019,6 @@ def main():
             pinfos.append(i2)
         phases = [statistics.mean(i["ms_phase"][k] for i in pinfos) for k in range(7)]
         phase_src = f"{len(pinfos)} eager gn_step calls after the timed region (same kernels as the graph)"
-    else:
-        phases = [statistics.mean(i["ms_phase"][k] for i in infos) for k in range(7)]
     kernels = kernel_report(prob, args, phases)
     # the roofline object describes the largest single kernel, the Gram launch (the Cholesky
     # phase is a chain of several kernels and is reported beside it under "kernels")
@@ -1059,7 +1066,7 @@ def main():
                 "gpu_launches": int(launches),
                 "phase_ms": {"jacobian": phases[0], "gram": phases[1], "factor": phases[3], "solve": phases[4],
                              "line_search": phases[5], "total": phases[6], "source": phase_src},
-                "step_call": "gn_step_graph (captured CUDA graphs)" if args.graph else "gn_step",
+                "step_call": "gn_step_graph (captured CUDA graphs)" if use_graph else "gn_step",
                 "final": {"loss": infos[-1]["loss_after"], "lambda": lam, "damping": gam,
                           "trials": [i["n_trials"] for i in infos]}}
         print(json.dumps(line))

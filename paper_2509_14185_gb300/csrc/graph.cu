@@ -57,6 +57,11 @@ struct GraphState {
                                   // handle's own stream may be the legacy default stream,
                                   // which cannot be captured)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_in = nullptr;
+  // phase marks recorded inside the handle's own graphs (external event nodes): 0 start,
+  // 1 Jacobian done, 2 Gram and gradient done, 4 factorisation start, 5 solves done,
+  // 6 model scalars done, 7 commit done; 3 is unused
+  cudaEvent_t evp[8] = {};
+  bool marks = false;   // the graphs carry the marks (one row block; not a batch branch)
   int precision = -1, n_slices = -1, lam_frozen = -1, staged = -1;   // of the handle when captured
   double stage_eps = 0.0;
   // kernels per replay, for gn_kernel_launches: outside the trial bodies (step graph, solve
@@ -165,26 +170,35 @@ unsigned grid_for(int64_t n) {
 }
 
 // Rows, Jacobian (row blocks), Gram and gradient, loss: the first half of gn_step.
-int capture_rows_gram(gn_handle* h, const double* theta) {
+// An external event node marking a phase boundary (only in graphs that carry the marks).
+int mark(gn_handle* h, bool on, int k) {
+  if (on) GN_G_TRY(cudaEventRecordWithFlags(h->gs->evp[k], h->st, cudaEventRecordExternal));
+  return GN_OK;
+}
+
+int capture_rows_gram(gn_handle* h, const double* theta, bool marks) {
   GraphState* gs = h->gs;
   cudaStream_t st = h->st;
   GN_G_TRY(cudaMemsetAsync(h->flag + 2, 0, sizeof(int), st));
   const int64_t nblk = (h->n_rows + h->jrows - 1) / h->jrows;
-  for (int64_t b = 0; b < nblk; b++) {
+  marks = marks && nblk == 1;
+  int rc = mark(h, marks, 0);
+  for (int64_t b = 0; b < nblk && !rc; b++) {
     const int64_t lo = b * h->jrows;
     const int64_t hi = (lo + h->jrows < h->n_rows) ? lo + h->jrows : h->n_rows;
     Pass ps = {MODE_JACOBIAN, h->r, h->J, h->ldJ, lo, hi, nullptr, &gs->ds->lam};
-    int rc = run_pass(h, theta, 0.0, ps, nullptr);
-    if (rc) return rc;
-    rc = gram_into(h, h->J, h->ldJ, hi - lo, h->r + lo, h->G, h->g, h->precision, b > 0);
-    if (rc) return rc;
+    rc = run_pass(h, theta, 0.0, ps, nullptr);
+    if (!rc) rc = mark(h, marks, 1);
+    if (!rc) rc = gram_into(h, h->J, h->ldJ, hi - lo, h->r + lo, h->G, h->g, h->precision, b > 0);
+    if (!rc) rc = mark(h, marks, 2);
   }
+  if (rc) return rc;
   GN_G_TRY(mirror_lower(h->G, h->Pp, h->Pp, st));
   return loss_of(h, h->r, 0);
 }
 
 // The second half: damped factorisation and solve, model scalars, IF(trial) x 8, commit.
-int capture_solve(gn_handle* h, double* theta) {
+int capture_solve(gn_handle* h, double* theta, bool marks) {
   GraphState* gs = h->gs;
   cudaStream_t st = h->st;
   const int64_t Pp = h->Pp, P = h->P;
@@ -200,6 +214,7 @@ int capture_solve(gn_handle* h, double* theta) {
   for (int t = 0; t < kMaxTrials; t++)
     GN_G_TRY(cudaGraphConditionalHandleCreate(&cond[t], cg, 0, cudaGraphCondAssignDefault));
 
+  if (mark(h, marks, 4)) return GN_ERR_CUDA;
   add_diag_state_kernel<<<1024, 256, 0, st>>>(h->G, h->A, Pp, Pp, ds);
   count_launch();
   GN_G_TRY(cudaGetLastError());
@@ -215,6 +230,7 @@ int capture_solve(gn_handle* h, double* theta) {
     GN_G_TRY(cholesky_factor(h->A, Pp, Pp, h->Linv, h->flag + 1, st));
     GN_G_TRY(cholesky_solve(h->A, Pp, Pp, h->Linv, h->g, h->delta, h->vtmp, st));
   }
+  if (mark(h, marks, 5)) return GN_ERR_CUDA;
   GN_G_TRY(dot_partial(h->g, h->delta, Pp, h->red, st));
   GN_G_TRY(finish_sum(h->red, h->red + 257, st));
   GN_G_TRY(dgemv_n(h->G, Pp, Pp, Pp, h->delta, h->vtmp, 0.0, st));
@@ -223,6 +239,7 @@ int capture_solve(gn_handle* h, double* theta) {
   model_kernel<<<1, 1, 0, st>>>(h->red, h->delta, P, h->flag, ds, cond[0]);
   count_launch();
   GN_G_TRY(cudaGetLastError());
+  if (mark(h, marks, 6)) return GN_ERR_CUDA;
 
   for (int t = 0; t < kMaxTrials; t++) {
     const cudaGraphNode_t* deps = nullptr;
@@ -268,7 +285,7 @@ int capture_solve(gn_handle* h, double* theta) {
   commit_kernel<<<grid_for(P), 256, 0, st>>>(theta, h->theta_t, P, ds);
   count_launch();
   GN_G_TRY(cudaGetLastError());
-  return GN_OK;
+  return mark(h, marks, 7);
 }
 
 // Capture one graph on h->st: the whole step (with_rows) or the solve part only.
@@ -277,8 +294,9 @@ int capture(gn_handle* h, double* theta, bool with_rows, cudaGraph_t* out) {
   GN_G_TRY(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
   h->capturing = 1;
   const long long k0 = g_launches.load();
-  int rc = with_rows ? capture_rows_gram(h, theta) : GN_OK;
-  if (!rc) rc = capture_solve(h, theta);
+  const bool marks = h->gs->marks;
+  int rc = with_rows ? capture_rows_gram(h, theta, marks) : GN_OK;
+  if (!rc) rc = capture_solve(h, theta, marks);
   // capture counted each launch once; replays add what actually runs
   const long long k = g_launches.load() - k0;
   g_launches.fetch_sub(k);
@@ -317,6 +335,7 @@ int ensure_state(gn_handle* h, StepState* external_ds) {
     GN_G_TRY(cudaEventCreate(&gs->ev0));
     GN_G_TRY(cudaEventCreate(&gs->ev1));
     GN_G_TRY(cudaEventCreateWithFlags(&gs->ev_in, cudaEventDisableTiming));
+    for (auto& e : gs->evp) GN_G_TRY(cudaEventCreate(&e));
   }
   GraphState* gs = h->gs;
   if (external_ds) {
@@ -338,6 +357,7 @@ int ensure_state(gn_handle* h, StepState* external_ds) {
 int build_graphs(gn_handle* h, double* theta, bool with_step) {
   GraphState* gs = h->gs;
   destroy_graphs(gs);
+  gs->marks = with_step;   // a batch fit's retry graph carries none
   int rc = prepare_for_capture(h);
   if (rc) return rc;
   GN_G_TRY(cudaStreamSynchronize(h->st));   // nothing of an earlier eager call may be in flight
@@ -418,6 +438,8 @@ void graph_release(gn_handle* h) {
   if (gs->ev_in) cudaEventDestroy(gs->ev_in);
   if (gs->ev0) cudaEventDestroy(gs->ev0);
   if (gs->ev1) cudaEventDestroy(gs->ev1);
+  for (auto e : gs->evp)
+    if (e) cudaEventDestroy(e);
   delete gs;
   h->gs = nullptr;
 }
@@ -432,8 +454,8 @@ int graph_prepare_fit(gn_handle* h, void* ds_slot, double* theta) {
 int graph_capture_fit_step(gn_handle* h, double* theta) {
   h->capturing = 1;
   const long long k0 = g_launches.load();
-  int rc = capture_rows_gram(h, theta);
-  if (!rc) rc = capture_solve(h, theta);
+  int rc = capture_rows_gram(h, theta, false);
+  if (!rc) rc = capture_solve(h, theta, false);
   const long long k = g_launches.load() - k0;
   g_launches.fetch_sub(k);
   h->gs->k_branch = k - kMaxTrials * h->gs->k_trial;
@@ -491,6 +513,19 @@ int gn_step_graph(gn_handle* h, double* theta, double* lambda, double* damping, 
   float ms = 0.f;
   cudaEventElapsedTime(&ms, gs->ev0, gs->ev1);
   inf.ms_phase[6] = ms;
+  if (gs->marks && (h->n_rows + h->jrows - 1) / h->jrows == 1) {
+    auto el = [&](int a, int b) {
+      float v = 0.f;
+      return cudaEventElapsedTime(&v, gs->evp[a], gs->evp[b]) == cudaSuccess ? (double)v : 0.0;
+    };
+    inf.ms_phase[0] = el(0, 1);   // Jacobian
+    inf.ms_phase[1] = el(1, 2);   // Gram and gradient
+    if (inf.status != GN_ERR_NOT_SPD) {
+      inf.ms_phase[3] = el(4, 5);   // damped factorisation and solves (the last replay)
+      inf.ms_phase[4] = el(5, 6);   // model scalars
+      inf.ms_phase[5] = el(6, 7);   // line search and commit
+    }
+  }
   if (info) *info = inf;
   return status;
 }

@@ -69,6 +69,10 @@ def test_graph_step_matches_oracle():
     d_o = np.concatenate([w.theta - th_o, [w.lam - lam_o]])
     cond = np.linalg.cond(info_o["G"] + info_o["gamma_used"] * np.eye(len(d_o)))
     assert rel(d_gpu, d_o) <= max(TOL, 1e-15 * cond)
+    # the phase marks inside the graph time the Jacobian, the Gram and the solve
+    ph = info["ms_phase"]
+    assert ph[0] > 0 and ph[1] > 0 and ph[3] > 0 and ph[5] > 0
+    assert ph[0] + ph[1] + ph[3] + ph[4] + ph[5] <= ph[6] * 1.001
     prob.close()
 
 
