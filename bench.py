@@ -1009,7 +1009,8 @@ def main():
     # per-phase device times (library CUDA events on the launch stream, averaged over the timed steps);
     # a captured graph is timed as a whole, so its phases come from eager steps of the same kernels
     # on a copy of the parameters, after the timed region
-    phase_src = "timed steps (CUDA events on the launch stream; inside the graph as event nodes)"
+    phase_src = ("timed steps (CUDA events on the launch stream, recorded inside the graph as event nodes)"
+                 if use_graph else "timed steps (library CUDA events on the launch stream)")
     phases = [statistics.mean(i["ms_phase"][k] for i in infos) for k in range(7)]
     if use_graph and phases[1] == 0.0:   # a streamed Jacobian carries no per-phase marks
         th2 = theta.clone()
