@@ -75,7 +75,10 @@ def parse():
     ap.add_argument("--funnel", action="store_true",
                     help="funnel inference of lambda over a batch of fits at fixed lambda (own JSON line)")
     ap.add_argument("--funnel-fits", type=int, default=16)
-    ap.add_argument("--funnel-workload", default="ccf_stable", choices=["ccf_stable", "ccf_unstable1", "ipm"])
+    ap.add_argument("--funnel-workload", default="ccf_stable",
+                    choices=["ccf_stable", "ccf_unstable1", "ipm", "burgers_half"])
+    ap.add_argument("--funnel-spread", type=float, default=0.02,
+                    help="relative spread of the fits' lambda seeds around the workload's seed")
     ap.add_argument("--funnel-relax", type=int, default=100,
                     help="GN steps at the seed lambda before the first r_hat (the fit relaxes first)")
     ap.add_argument("--funnel-iters", type=int, default=6)
@@ -455,7 +458,7 @@ def run_funnel(args):
     fits = []
     for f in range(args.funnel_fits):
         w = make(seed=seed0 + 100 + f)
-        w.lam = w.lam * (1.0 + 0.02 * (f / max(1, args.funnel_fits - 1) - 0.5))
+        w.lam = w.lam * (1.0 + args.funnel_spread * (f / max(1, args.funnel_fits - 1) - 0.5))
         fits.append(w)
     prec = {"fp64": gn.GN_PREC_FP64, "split": gn.GN_PREC_SPLIT_BF16, "split_all": gn.GN_PREC_SPLIT_ALL}[args.precision]
     batch = gn.GNBatch(fits, n_streams=min(8, len(fits)), precision=prec, n_slices=args.slices)
@@ -499,7 +502,8 @@ def run_funnel(args):
                       "fit_steps_per_s": len(fits) * args.funnel_steps / (statistics.median(iter_ms) * 1e-3),
                       "median_loss_per_iteration": losses,
                       "lambda_final": {"median": statistics.median(final), "min": min(final), "max": max(final)},
-                      "lambda_history": hist_l[:4], "r_hat_history": hist_r[:4]}))
+                      "lambda_history": hist_l[:: max(1, len(hist_l) // 4)],
+                      "r_hat_history": hist_r[:: max(1, len(hist_r) // 4)]}))
     return 0
 
 

@@ -64,7 +64,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed for {cmd[-3]}")
     if jobs or not os.path.exists(LIB):
-        cmd = [cc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
+        cmd = [cc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)

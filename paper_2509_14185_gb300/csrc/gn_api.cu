@@ -9,6 +9,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gn_internal.cuh"
 
 using namespace gn;
@@ -280,6 +282,20 @@ int gram_into(gn_handle* h, const double* J, int64_t ld, int64_t nrows, const do
 }  // namespace gn
 
 namespace {
+
+// NVTX ranges naming the host-side phases of a step (shown by Nsight Systems; no-ops when no
+// tool is attached).
+struct Phases {
+  bool open = false;
+  void next(const char* name) {
+    if (open) nvtxRangePop();
+    nvtxRangePushA(name);
+    open = true;
+  }
+  ~Phases() {
+    if (open) nvtxRangePop();
+  }
+};
 
 struct Timer {
   cudaEvent_t ev[9];
@@ -597,6 +613,7 @@ int gn_step(gn_handle* h, double* theta, double* lambda, double* damping, gn_ste
   const double lam = *lambda;
   double gamma = *damping;
   Timer tm(st);
+  Phases ph;
   GN_TRY_CUDA(cudaMemsetAsync(h->flag + 2, 0, sizeof(int), st));
   tm.mark(0);
   // 1. rows and Jacobian, Gram and gradient, streamed in row blocks
@@ -608,9 +625,11 @@ int gn_step(gn_handle* h, double* theta, double* lambda, double* damping, gn_ste
     const int64_t hi = (lo + h->jrows < h->n_rows) ? lo + h->jrows : h->n_rows;
     Pass ps = {MODE_JACOBIAN, h->r, h->J, h->ldJ, lo, hi, nullptr};
     tm.mark(1);
+    ph.next("gn_step: jacobian");
     rc = run_pass(h, theta, lam, ps, nullptr);
     if (rc) return rc;
     tm.mark(2);
+    ph.next("gn_step: gram");
     rc = gram_into(h, h->J, h->ldJ, hi - lo, h->r + lo, h->G, h->g, h->precision, b > 0);
     if (rc) return rc;
     tm.mark(3);
@@ -630,6 +649,7 @@ int gn_step(gn_handle* h, double* theta, double* lambda, double* damping, gn_ste
     t_gram = tm.ms(2, 3);
   }
   // 2. damped solve
+  ph.next("gn_step: damped solve");
   int retries = 0;
   rc = gn_damped_solve(h, h->G, h->g, &gamma, h->delta, &retries);
   tm.mark(5);
@@ -662,6 +682,7 @@ int gn_step(gn_handle* h, double* theta, double* lambda, double* damping, gn_ste
     return GN_ERR_NONFINITE;
   }
   // 4. Armijo backtracking on residual-only evaluations
+  ph.next("gn_step: line search");
   const double c1 = 1e-4;
   double alpha = 1.0;
   bool accepted = false;
