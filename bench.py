@@ -74,15 +74,15 @@ def parse():
     ap.add_argument("--ms-workload", default="burgers_half", choices=["burgers_half", "ccf_stable"])
     ap.add_argument("--funnel", action="store_true",
                     help="funnel inference of lambda over a batch of fits at fixed lambda (own JSON line)")
-    ap.add_argument("--funnel-fits", type=int, default=16)
-    ap.add_argument("--funnel-workload", default="ccf_stable",
+    ap.add_argument("--funnel-fits", type=int, default=8)
+    ap.add_argument("--funnel-workload", default="burgers_half",
                     choices=["ccf_stable", "ccf_unstable1", "ipm", "burgers_half"])
-    ap.add_argument("--funnel-spread", type=float, default=0.02,
+    ap.add_argument("--funnel-spread", type=float, default=0.2,
                     help="relative spread of the fits' lambda seeds around the workload's seed")
-    ap.add_argument("--funnel-relax", type=int, default=100,
+    ap.add_argument("--funnel-relax", type=int, default=1500,
                     help="GN steps at the seed lambda before the first r_hat (the fit relaxes first)")
-    ap.add_argument("--funnel-iters", type=int, default=6)
-    ap.add_argument("--funnel-steps", type=int, default=20)
+    ap.add_argument("--funnel-iters", type=int, default=8)
+    ap.add_argument("--funnel-steps", type=int, default=300)
     ap.add_argument("--funnel-radius", type=float, default=0.1)
     ap.add_argument("--funnel-dlam", type=float, default=0.01)
     ap.add_argument("--gram-split", type=int, default=0,
@@ -443,7 +443,8 @@ def run_multistage(args):
 def run_funnel(args):
     """Funnel inference of lambda (Methods, "Identifying Admissible lambda Values", item 3)
     over a batch of fits: --funnel-fits copies of the workload with different seeded point
-    sets and initialisations and lambda seeds spread by 2 % around the workload's seed, each
+    sets and initialisations and lambda seeds spread evenly over +-(--funnel-spread)/2 of the
+    workload's seed (default: Burgers around its admissible lambda = 1/2), each
     held at a fixed lambda (gn_set_lambda_trainable(0)) and trained --funnel-steps damped GN
     steps per iteration (one batched CUDA-graph launch per step); then r_hat(lambda), the
     signed residual of largest magnitude within --funnel-radius of the origin, is read for
