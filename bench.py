@@ -87,6 +87,9 @@ def parse():
     ap.add_argument("--funnel-dlam", type=float, default=0.01)
     ap.add_argument("--gram-split", type=int, default=0,
                     help="force the split Gram's split-K factor (0: autotuned per shape)")
+    ap.add_argument("--pipeline", type=int, default=None,
+                    help="tiles per Gram chunk of the pipelined graph step (-1: 7/8 of the SM count; "
+                         "default: the library's, off: Gram then factorisation)")
     ap.add_argument("--eager", action="store_true",
                     help="step with gn_step (host decisions between launches) instead of the captured graphs; "
                          "--workload batched: one host worker thread per stream instead of the batched graph")
@@ -711,7 +714,7 @@ def gram_executed_flops(rows, Pp, S):
     return S * (S + 1) / 2 * (nt * (nt + 1) / 2) * 128 * 128 * kpad * 2.0
 
 
-def kernel_report(prob, args, phases):
+def kernel_report(prob, args, phases, pipe_tiles=0):
     """Roofline entries of the step's dense phases (algorithmic FLOP / measured phase time).
 
     Gram: rows * P'(P'+1) FLOP (symmetric half).  FP64 path: DFMA pipe against the
@@ -739,13 +742,19 @@ def kernel_report(prob, args, phases):
         pk, src = measured_peak("bf16_tflops_sustained", 1700.0)
         executed = gram_executed_flops(rows, Pp, S)
         tens = executed / (gram_ms * 1e-3) / 1e12
-        traffic = (GRAM_TRAFFIC_BYTES_CCF_S6 if (S == 6 and getattr(args, "workload", "") == "ccf_unstable1")
-                   else None)
+        # DRAM bytes of the whole-triangle launch from one ncu capture; the pipelined step's
+        # chunk launches run inside a graph with conditional nodes, where ncu lists no kernels
+        traffic = (GRAM_TRAFFIC_BYTES_CCF_S6 if (S == 6 and getattr(args, "workload", "") == "ccf_unstable1"
+                                                 and not pipe_tiles) else None)
         out["gram"] = {"bound": "tensor", "achieved": tens, "peak": pk, "unit": "TFLOP/s", "frac": tens / pk,
                        "traffic": traffic, "traffic_unit": "bytes per launch" if traffic else None, "ms": gram_ms,
                        "kernel": f"ozaki_kernel<{S},1,0> (split Gram: BF16 slice products on tcgen05, TMEM "
                                  "accumulators; the slicing pre-pass is inside the timed phase)",
                        "peak_source": src + ", sustained: the kernel runs inside a long step",
+                       **({"pipelined": f"column-major chunks of <= {pipe_tiles} tiles on the lowest-priority "
+                                        "stream beside the factorisation; ms is the Gram's wall time (slicing "
+                                        "to its last chunk) while it shares the SMs with the factorisation"}
+                          if pipe_tiles else {}),
                        "executed_flops_per_launch": executed,
                        "fp64_equivalent_tflops": gram_flops / (gram_ms * 1e-3) / 1e12,
                        "algorithmic_flops_per_launch": gram_flops}
@@ -954,6 +963,8 @@ def main():
     w = replica_workload(args.workload, rank)
     prec = {"fp64": gn.GN_PREC_FP64, "split": gn.GN_PREC_SPLIT_BF16, "split_all": gn.GN_PREC_SPLIT_ALL}[args.precision]
     prob = gn.GNProblem.from_workload(w, precision=prec, n_slices=args.slices)
+    if args.pipeline is not None:
+        prob.gn_set_pipeline(args.pipeline)
     stream = torch.cuda.current_stream()
     theta = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
     lam, gam = w.lam, w.gamma
@@ -1025,7 +1036,9 @@ def main():
             pinfos.append(i2)
         phases = [statistics.mean(i["ms_phase"][k] for i in pinfos) for k in range(7)]
         phase_src = f"{len(pinfos)} eager gn_step calls after the timed region (same kernels as the graph)"
-    kernels = kernel_report(prob, args, phases)
+    # the pipelined step (graph path) runs the Gram in column chunks beside the factorisation
+    pipe_tiles = prob.gn_pipeline_tiles() if use_graph else 0
+    kernels = kernel_report(prob, args, phases, pipe_tiles)
     # the roofline object describes the largest single kernel, the Gram launch (the Cholesky
     # phase is a chain of several kernels and is reported beside it under "kernels")
     roof = dict(kernels["gram"])
@@ -1070,8 +1083,11 @@ def main():
                                   else {})),
                 "roofline": roof, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(launches),
-                "phase_ms": {"jacobian": phases[0], "gram": phases[1], "factor": phases[3], "solve": phases[4],
-                             "line_search": phases[5], "total": phases[6], "source": phase_src},
+                "phase_ms": dict({"jacobian": phases[0], "gram": phases[1], "factor": phases[3],
+                                  "solve": phases[4], "line_search": phases[5], "total": phases[6],
+                                  "source": phase_src},
+                                 **({"overlap": f"pipelined step (Gram chunks of {pipe_tiles} tiles): the gram "
+                                                "and factor phases run at the same time"} if pipe_tiles else {})),
                 "step_call": "gn_step_graph (captured CUDA graphs)" if use_graph else "gn_step",
                 "final": {"loss": infos[-1]["loss_after"], "lambda": lam, "damping": gam,
                           "trials": [i["n_trials"] for i in infos]}}

@@ -172,6 +172,25 @@ int gn_set_precision(gn_handle* h, int precision, int n_slices);
 int gn_set_gram_split(gn_handle* h, int ksplit);
 int gn_gram_split_choice(const gn_handle* h, int64_t nrows, int* ksplit);
 
+/* Pipelined Gram and factorisation in gn_step_graph (precision GN_PREC_SPLIT_ALL, one row
+ * block, split-K factor 1).  The lower tiles of G = J~^T J~ are computed column by column in
+ * chunks of at most `tiles` 128 x 128 tiles (one launch each, on a stream of the lowest
+ * priority); the damped copy A = G + gamma I of each finished band of 256 columns is made at
+ * once, and the factorisation's chain (highest priority) starts each 256-column strip as soon as
+ * its band is in A, so the latency-bound factorisation runs beside the tensor-bound Gram on the
+ * SMs the chunks leave free.  The arithmetic is unchanged: results equal the unpipelined step
+ * bit for bit.  tiles = 0 (the default) keeps the unpipelined order (Gram, then factorisation);
+ * -1 picks 7/8 of the SM count; a change takes effect at the next capture.  On GB300 the
+ * factorisation's wide kernels (panel solves, trailing updates) slow down on the SMs the chunks
+ * leave free about as much as the overlap saves, hence off by default.  GN_ERR_INVALID for
+ * tiles < -1.  Cites: Methods, "Second-order Optimizer" (the damped normal equations the step
+ * solves); the pipelining is this library's scheduling. */
+int gn_set_pipeline(gn_handle* h, int tiles);
+/* *tiles = tiles per Gram chunk that the next capture of gn_step_graph uses (0: the step does
+ * not pipeline: another precision, several row blocks, a split-K Gram, fewer than 4 tile
+ * columns, or the pipeline off).  GN_ERR_INVALID for null arguments. */
+int gn_pipeline_tiles(gn_handle* h, int64_t* tiles);
+
 /* ---- evaluation --------------------------------------------------------- */
 
 /* r_out[0..n_rows) = r~(theta, lambda); *loss_out (host, may be NULL) = h = |r~|^2/2.

@@ -730,7 +730,7 @@ cudaError_t cholesky_factor(double* A, int64_t n, int64_t lda, double* Linv, int
 // diagonal factor forms y_k = Linv_k w_k and the panel kernel applies it to
 // the rows below (w: n doubles of work space, y: n doubles out).
 // *rc_out receives a GN_ERR_* code on failure.
-constexpr int64_t kStrip = 4 * NB;
+constexpr int64_t kStrip = kCholStrip;
 
 // Split workspace of cholesky_factor_split: U (n x n double-FP32), two strip operands
 // (slices and four exponent arrays each), the double-float diagonal inverses, their
@@ -749,18 +749,36 @@ size_t chol_split_ws_bytes(int64_t n, int S) {
   return ub + 2 * (sb + eb) + lb + cb + yb + 256;
 }
 
-// The look-ahead's two streams (critical path at high priority, deferred bulk updates at low).
+// The look-ahead's streams: the critical path at the highest priority, the deferred bulk
+// updates in the middle, and the pipelined step's Gram chunks at the lowest (numerically
+// greater is lower; with only two levels the last two share one).
 cudaError_t ensure_chol_streams(gn_handle* h) {
   if (h->st_hi) return cudaSuccess;
   int least = 0, greatest = 0;
   cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  const int middle = greatest + (least - greatest + 1) / 2;
   if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->st_hi, cudaStreamNonBlocking, greatest);
-  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->st_lo, cudaStreamNonBlocking, least);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->st_lo, cudaStreamNonBlocking, middle);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->st_g, cudaStreamNonBlocking, least);
   return e;
 }
 
+int ensure_chol_ws(gn_handle* h, size_t need) {
+  if (h->chol_ws_bytes >= need) return GN_OK;
+  if (h->capturing) {   // prepare_for_capture sized it; growing now would allocate inside a capture
+    set_detail(__FILE__, __LINE__, "factorisation workspace would grow during a graph capture");
+    return GN_ERR_UNSUPPORTED;
+  }
+  if (h->chol_ws) cudaFree(h->chol_ws);   // synchronises: no kernel still reads it
+  h->chol_ws = nullptr;
+  h->chol_ws_bytes = 0;
+  if (GN_NOTE(cudaMalloc(&h->chol_ws, need)) != cudaSuccess) return GN_ERR_OOM;
+  h->chol_ws_bytes = need;
+  return GN_OK;
+}
+
 cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t lda, double* Linv, int* flag, int S,
-                                  const double* b, double* y, double* w, int* rc_out) {
+                                  const double* b, double* y, double* w, int* rc_out, const cudaEvent_t* gate) {
   cudaStream_t st = h->st;
   *rc_out = GN_OK;
   auto rup = [](int64_t v, int64_t m) { return (v + m - 1) / m * m; };
@@ -772,12 +790,12 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
   const int64_t nblk = (n + NB - 1) / NB;
   const size_t lb = rup(nblk * NB * NB * sizeof(float2), 256);
   const size_t cb = rup(nblk * NB * sizeof(int), 256);
-  int rc = ensure_split_ws(h, chol_split_ws_bytes(n, S));
+  int rc = ensure_chol_ws(h, chol_split_ws_bytes(n, S));
   if (rc) {
     *rc_out = rc;
     return cudaErrorMemoryAllocation;
   }
-  unsigned char* base = static_cast<unsigned char*>(h->split_ws);
+  unsigned char* base = static_cast<unsigned char*>(h->chol_ws);
   float2* U = reinterpret_cast<float2*>(base);
   unsigned char* strip_base = base + ub;   // two strip operands of sb + eb bytes
   float2* LinvDF = reinterpret_cast<float2*>(base + ub + 2 * (sb + eb));
@@ -814,9 +832,15 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
   if ((err = cudaStreamWaitEvent(sl, e0, 0)) != cudaSuccess) return err;
   if ((err = cudaMemsetAsync(U, 0, (size_t)n * n * sizeof(float2), sh)) != cudaSuccess) return err;
   if (b && (err = cudaMemcpyAsync(w, b, n * sizeof(double), cudaMemcpyDeviceToDevice, sh)) != cudaSuccess) return err;
+  cudaEvent_t waited = nullptr;
   for (int64_t t = 0; t < nstrip; t++) {
     const int64_t s0 = t * kStrip;
     const int64_t s1 = (s0 + kStrip < n) ? s0 + kStrip : n;
+    // the strip's columns of A may still be in production (pipelined step)
+    if (gate && gate[t] && gate[t] != waited) {
+      if ((err = cudaStreamWaitEvent(sh, gate[t], 0)) != cudaSuccess) return err;
+      waited = gate[t];
+    }
     // strip operand t % 2 (rows relative to s0); its previous user, strip t - 2's deferred
     // update, finished before strip t - 1's next-columns update (the wait below)
     unsigned char* sbase = strip_base + (t & 1) * (sb + eb);

@@ -75,7 +75,7 @@ cudaError_t dalloc(T** p, size_t count) {
 void free_all(gn_handle* h) {
   void* ptrs[] = {h->ema_ws, h->wt, h->theta_t, h->r, h->J, h->G, h->A, h->Linv, h->g, h->delta, h->vtmp, h->red,
                   h->flag, h->gpart, h->kf, h->dcoef, h->snode, h->gnode, h->Jg, h->ug, h->sU, h->tnode,
-                  h->split_ws, h->base_int, h->base_wall, h->base_norm, h->base_node, h->fourierW};
+                  h->split_ws, h->chol_ws, h->base_int, h->base_wall, h->base_norm, h->base_node, h->fourierW};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->hpin) cudaFreeHost(h->hpin);
@@ -462,6 +462,7 @@ int gn_destroy(gn_handle* h) {
   graph_release(h);
   if (h->st_hi) cudaStreamDestroy(h->st_hi);
   if (h->st_lo) cudaStreamDestroy(h->st_lo);
+  if (h->st_g) cudaStreamDestroy(h->st_g);
   free_all(h);
   if (h->tmaps) free(h->tmaps);
   delete h;
@@ -492,6 +493,18 @@ int gn_set_precision(gn_handle* h, int precision, int n_slices) {
 int gn_set_gram_split(gn_handle* h, int ksplit) {
   if (!h || ksplit < 0 || ksplit > 8) return GN_ERR_INVALID;
   h->gram_ksplit = ksplit;
+  return GN_OK;
+}
+
+int gn_set_pipeline(gn_handle* h, int tiles) {
+  if (!h || tiles < -1) return GN_ERR_INVALID;
+  h->pipe_tiles = tiles;
+  return GN_OK;
+}
+
+int gn_pipeline_tiles(gn_handle* h, int64_t* tiles) {
+  if (!h || !tiles) return GN_ERR_INVALID;
+  *tiles = pipeline_chunk_tiles(h);
   return GN_OK;
 }
 

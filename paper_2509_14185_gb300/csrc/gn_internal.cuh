@@ -5,6 +5,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <vector>
 #include <stdint.h>
 
 #include <atomic>
@@ -140,8 +141,17 @@ struct gn_handle {
   double* ema_ws = nullptr;
   int64_t ema_len = 0;
   // streams of the split factorisation's look-ahead (created on first use)
-  cudaStream_t st_hi = nullptr;   // critical path (high priority)
-  cudaStream_t st_lo = nullptr;   // deferred bulk updates (low priority)
+  cudaStream_t st_hi = nullptr;   // critical path (highest priority)
+  cudaStream_t st_lo = nullptr;   // deferred bulk updates (middle priority)
+  cudaStream_t st_g = nullptr;    // Gram chunks of the pipelined step (lowest priority)
+  // the split factorisation's own workspace (U, strip operands, diagonal inverses), apart from
+  // split_ws so that it can run while the Gram still reads its operand
+  void* chol_ws = nullptr;
+  size_t chol_ws_bytes = 0;
+  // pipelined step: the Gram runs as column-major chunks of at most pipe_tiles 128 x 128 tiles
+  // beside the factorisation (0, the default: off, Gram then factorisation; -1: chosen from
+  // the SM count)
+  int pipe_tiles = 0;
   // graph-captured step (created on first use of gn_step_graph or by a batch capture)
   gn::GraphState* gs = nullptr;
   int capturing = 0;              // a stream capture is in progress: no workspace may grow
@@ -216,6 +226,9 @@ cudaError_t dgemv_t_scratch(const double* A, int64_t lda, int64_t m, int64_t n, 
 cudaError_t dgemv_n(const double* A, int64_t lda, int64_t m, int64_t n, const double* x, double* y,
                     double beta, cudaStream_t st);   // y[m] = beta*y + A x
 cudaError_t mirror_lower(double* G, int64_t n, int64_t ld, cudaStream_t st);
+// A = G + gamma I on the lower triangle's columns [c0, c1) (gamma: device scalar)
+cudaError_t add_diag_band(const double* G, double* A, int64_t n, int64_t ld, int64_t c0, int64_t c1,
+                          const double* gamma, cudaStream_t st);
 cudaError_t copy_add_diag(const double* G, double* A, int64_t n, int64_t ld, double gamma, cudaStream_t st);
 cudaError_t max_abs_rows(const double* r, int64_t n, int stride_valid, double* red, cudaStream_t st);
 cudaError_t finish_max(double* red, double* out_dev, cudaStream_t st);
@@ -226,6 +239,7 @@ cudaError_t hilbert_build(const double* y, int64_t n, int M, double* kf, double*
 
 // Cholesky (FP64, blocked, lower, in place on A row-major) and solves.
 constexpr int kCholNB = 64;
+constexpr int64_t kCholStrip = 4 * kCholNB;   // columns per strip of the split factorisation
 cudaError_t cholesky_factor(double* A, int64_t n, int64_t lda, double* Linv, int* flag, cudaStream_t st);
 cudaError_t cholesky_solve(const double* A, int64_t n, int64_t lda, const double* Linv, const double* b,
                            double* x, double* tmp, cudaStream_t st);   // tmp: 2n doubles
@@ -281,15 +295,40 @@ int oz_prepare_rows(int S, const double* X, int64_t ld, int64_t n, int64_t k, co
 // ksplit > 1 (modes 0-2, single exponents only): the contraction is cut into ksplit parts
 // over that many more CTAs, whose partial tiles (part: tiles * ksplit * 128 * 128 float2)
 // are summed by a second launch.
+// range (sym only): just the tiles [tile0, tile0 + ntiles) of the lower triangle, numbered row by
+// row or, with colmajor, column by column (the first c mt - c (c - 1) / 2 tiles are tile columns
+// 0 .. c - 1, mt = ceil(M / 128)); ntiles < 0: every tile.
+struct OzRange {
+  int64_t tile0 = 0, ntiles = -1;
+  int colmajor = 0;
+};
 int oz_gemm(int S, bool sym, const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, double* C, int64_t ldc,
-            int mode, const double* rowscale, int* flag, cudaStream_t st, int ksplit = 1, void* part = nullptr);
+            int mode, const double* rowscale, int* flag, cudaStream_t st, int ksplit = 1, void* part = nullptr,
+            const OzRange& range = OzRange());
 // Gram through oz_gemm (lower tiles); returns GN_ERR_* codes.
 int split_gram(gn_handle* h, const double* J, int64_t ld, int64_t nrows, double* G, int accumulate);
+// Tiles per chunk of the pipelined Gram for this handle's step, 0 when the step does not
+// pipeline (another precision, several row blocks, split-K, a small G or pipe_tiles == 0).
+int64_t pipeline_chunk_tiles(gn_handle* h);
+// The pipelined Gram: J~'s operand on st, then sg forked from st and, on sg, the lower tiles of
+// G column by column in launches of at most `chunk` tiles; after each launch, the 256-column
+// strips it finished are copied into A = G + gamma I (lower triangle; gamma a device scalar) and
+// gate[t] is set to an event recorded after their copy (one per strip).  Last, G's upper
+// triangle is mirrored on sg.  Events are created into `events`; the caller destroys them once
+// the work is captured or done, and joins sg back.
+int split_gram_pipelined(gn_handle* h, const double* J, int64_t ld, int64_t nrows, double* G, double* A,
+                         const double* gamma, int64_t chunk, cudaStream_t st, cudaStream_t sg,
+                         std::vector<cudaEvent_t>& events, std::vector<cudaEvent_t>& gate);
 // grow the handle's split workspace to at least `need` bytes
 int ensure_split_ws(gn_handle* h, size_t need);
 // blocked Cholesky whose trailing updates run through oz_gemm
 // (with b: also the forward substitution L y = b, w being n doubles of work space)
+// gate (may be null): one event per 256-column strip (null entries: none); the strip's chain
+// waits for its event before it reads the strip's columns of A.
 cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t lda, double* Linv, int* flag, int S,
-                                  const double* b, double* y, double* w, int* rc_out);
+                                  const double* b, double* y, double* w, int* rc_out,
+                                  const cudaEvent_t* gate = nullptr);
+// the factorisation's workspace, grown to `need` bytes (never inside a capture)
+int ensure_chol_ws(gn_handle* h, size_t need);
 
 }  // namespace gn

@@ -6,7 +6,11 @@
 // and the new damping.  Here those decisions run in one-thread kernels on a
 // device-resident state (StepState), so one step is a fixed launch sequence:
 //
-//   graph "step"  = rows + Jacobian + Gram + g + loss, then the "solve" part
+//   graph "step"  = rows + Jacobian + Gram + g + loss, then the "solve" part;
+//                   under SPLIT_ALL (one row block) the Gram runs as column-major
+//                   chunks on a low-priority stream and the factorisation starts
+//                   each 256-column strip as soon as its columns are in A
+//                   (the pipelined step: same arithmetic, overlapped schedule)
 //   graph "solve" = G + gamma I, factorisation, triangular solves, the model
 //                   scalars, eight conditional IF nodes in sequence whose
 //                   bodies are the Armijo trials (theta_t = theta - alpha delta,
@@ -62,7 +66,7 @@ struct GraphState {
   // 6 model scalars done, 7 commit done; 3 is unused
   cudaEvent_t evp[8] = {};
   bool marks = false;   // the graphs carry the marks (one row block; not a batch branch)
-  int precision = -1, n_slices = -1, lam_frozen = -1, staged = -1;   // of the handle when captured
+  int precision = -1, n_slices = -1, lam_frozen = -1, staged = -1, pipe = -2;   // of the handle when captured
   double stage_eps = 0.0;
   // kernels per replay, for gn_kernel_launches: outside the trial bodies (step graph, solve
   // graph, a batch's step branch) and per line-search trial that runs
@@ -198,7 +202,10 @@ int capture_rows_gram(gn_handle* h, const double* theta, bool marks) {
 }
 
 // The second half: damped factorisation and solve, model scalars, IF(trial) x 8, commit.
-int capture_solve(gn_handle* h, double* theta, bool marks) {
+// gate (pipelined step): A's strips are copied by the Gram's stream, which signals each strip
+// through its gate event and the whole Gram (with G's mirror) through join.
+int capture_solve(gn_handle* h, double* theta, bool marks, const cudaEvent_t* gate = nullptr,
+                  cudaEvent_t join = nullptr) {
   GraphState* gs = h->gs;
   cudaStream_t st = h->st;
   const int64_t Pp = h->Pp, P = h->P;
@@ -215,14 +222,16 @@ int capture_solve(gn_handle* h, double* theta, bool marks) {
     GN_G_TRY(cudaGraphConditionalHandleCreate(&cond[t], cg, 0, cudaGraphCondAssignDefault));
 
   if (mark(h, marks, 4)) return GN_ERR_CUDA;
-  add_diag_state_kernel<<<1024, 256, 0, st>>>(h->G, h->A, Pp, Pp, ds);
-  count_launch();
-  GN_G_TRY(cudaGetLastError());
+  if (!gate) {
+    add_diag_state_kernel<<<1024, 256, 0, st>>>(h->G, h->A, Pp, Pp, ds);
+    count_launch();
+    GN_G_TRY(cudaGetLastError());
+  }
   GN_G_TRY(cudaMemsetAsync(h->flag + 1, 0, sizeof(int), st));
   if (h->precision == GN_PREC_SPLIT_ALL) {
     int rc = GN_OK;
     cudaError_t e = cholesky_factor_split(h, h->A, Pp, Pp, h->Linv, h->flag + 1, h->n_slices, h->g, h->vtmp + Pp,
-                                          h->vtmp, &rc);
+                                          h->vtmp, &rc, gate);
     if (rc) return rc;
     GN_G_TRY(e);
     GN_G_TRY(cholesky_solve_backward(h->A, Pp, Pp, h->Linv, h->vtmp + Pp, h->delta, h->vtmp, st));
@@ -231,6 +240,7 @@ int capture_solve(gn_handle* h, double* theta, bool marks) {
     GN_G_TRY(cholesky_solve(h->A, Pp, Pp, h->Linv, h->g, h->delta, h->vtmp, st));
   }
   if (mark(h, marks, 5)) return GN_ERR_CUDA;
+  if (join) GN_G_TRY(cudaStreamWaitEvent(st, join, 0));   // the model reads all of G
   GN_G_TRY(dot_partial(h->g, h->delta, Pp, h->red, st));
   GN_G_TRY(finish_sum(h->red, h->red + 257, st));
   GN_G_TRY(dgemv_n(h->G, Pp, Pp, Pp, h->delta, h->vtmp, 0.0, st));
@@ -288,15 +298,57 @@ int capture_solve(gn_handle* h, double* theta, bool marks) {
   return mark(h, marks, 7);
 }
 
+// The pipelined step (one row block, SPLIT_ALL): rows and Jacobian; then the Gram as column
+// chunks on the lowest-priority stream, which copies each finished 256-column strip into
+// A = G + gamma I and signals it; the factorisation starts each strip at its signal.  The
+// gradient and the loss run on the capture stream beside the first chunks.
+int capture_pipelined(gn_handle* h, double* theta, bool marks, int64_t chunk) {
+  GraphState* gs = h->gs;
+  cudaStream_t st = h->st;
+  GN_G_TRY(cudaMemsetAsync(h->flag + 2, 0, sizeof(int), st));
+  int rc = mark(h, marks, 0);
+  Pass ps = {MODE_JACOBIAN, h->r, h->J, h->ldJ, 0, h->n_rows, nullptr, &gs->ds->lam};
+  if (!rc) rc = run_pass(h, theta, 0.0, ps, nullptr);
+  if (!rc) rc = mark(h, marks, 1);
+  if (rc) return rc;
+  GN_G_TRY(ensure_chol_streams(h));
+  std::vector<cudaEvent_t> events, gate;
+  struct Guard {   // captured dependencies are edges of the graph: the events can go afterwards
+    std::vector<cudaEvent_t>& v;
+    ~Guard() {
+      for (auto e : v)
+        if (e) cudaEventDestroy(e);
+    }
+  } guard{events};
+  cudaStream_t sg = h->st_g;
+  rc = split_gram_pipelined(h, h->J, h->ldJ, h->n_rows, h->G, h->A, &gs->ds->gamma, chunk, st, sg, events, gate);
+  if (rc) return rc;
+  if (marks) GN_G_TRY(cudaEventRecordWithFlags(gs->evp[2], sg, cudaEventRecordExternal));
+  cudaEvent_t join = nullptr;
+  GN_G_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+  events.push_back(join);
+  GN_G_TRY(cudaEventRecord(join, sg));
+  GN_G_TRY(dgemv_t_scratch(h->J, h->ldJ, h->n_rows, h->Pp, h->r, h->g, 0.0, h->vtmp, st));
+  rc = loss_of(h, h->r, 0);
+  if (rc) return rc;
+  return capture_solve(h, theta, marks, gate.data(), join);
+}
+
 // Capture one graph on h->st: the whole step (with_rows) or the solve part only.
 int capture(gn_handle* h, double* theta, bool with_rows, cudaGraph_t* out) {
   *out = nullptr;
+  const int64_t chunk = with_rows ? pipeline_chunk_tiles(h) : 0;   // (queries the device: before capture)
   GN_G_TRY(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
   h->capturing = 1;
   const long long k0 = g_launches.load();
   const bool marks = h->gs->marks;
-  int rc = with_rows ? capture_rows_gram(h, theta, marks) : GN_OK;
-  if (!rc) rc = capture_solve(h, theta, marks);
+  int rc = GN_OK;
+  if (chunk > 0) {
+    rc = capture_pipelined(h, theta, marks, chunk);
+  } else {
+    rc = with_rows ? capture_rows_gram(h, theta, marks) : GN_OK;
+    if (!rc) rc = capture_solve(h, theta, marks);
+  }
   // capture counted each launch once; replays add what actually runs
   const long long k = g_launches.load() - k0;
   g_launches.fetch_sub(k);
@@ -376,6 +428,7 @@ int build_graphs(gn_handle* h, double* theta, bool with_step) {
   gs->lam_frozen = h->lam_frozen;
   gs->staged = h->staged;
   gs->stage_eps = h->stage_eps;
+  gs->pipe = h->pipe_tiles;
   return GN_OK;
 }
 
@@ -489,7 +542,8 @@ int gn_step_graph(gn_handle* h, double* theta, double* lambda, double* damping, 
   if (rc) return rc;
   GraphState* gs = h->gs;
   if (gs->theta != theta || !gs->x_step || gs->precision != h->precision || gs->n_slices != h->n_slices ||
-      gs->lam_frozen != h->lam_frozen || gs->staged != h->staged || gs->stage_eps != h->stage_eps) {
+      gs->lam_frozen != h->lam_frozen || gs->staged != h->staged || gs->stage_eps != h->stage_eps ||
+      gs->pipe != h->pipe_tiles) {
     rc = build_graphs(h, theta, true);
     if (rc) return rc;
   }

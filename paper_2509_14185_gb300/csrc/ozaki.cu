@@ -201,7 +201,30 @@ struct OzArgs {
   int ksplit;
   int cps;
   float2* part;
+  // tile range (sym): the launch computes tiles [tile0, tile0 + grid / ksplit) of the mt-square
+  // lower triangle, numbered row by row or (colmajor) column by column
+  int64_t tile0;
+  int64_t mt;
+  int colmajor;
 };
+
+// Lower-triangular tile t of an mt x mt tile grid.  Row order: row ti holds tiles
+// ti (ti + 1) / 2 .. + ti.  Column order (colmajor): column tj holds the next mt - tj tiles, so
+// the first C(c) = c mt - c (c - 1) / 2 tiles are exactly the tile columns 0 .. c - 1.  It is
+// row order read backwards on the triangle reflected about its anti-diagonal,
+// (ti, tj) -> (mt - 1 - tj, mt - 1 - ti), which maps the lower triangle onto itself.
+__device__ __forceinline__ void sym_tile(int64_t t, int64_t mt, int colmajor, int64_t& ti, int64_t& tj) {
+  if (colmajor) t = mt * (mt + 1) / 2 - 1 - t;
+  ti = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((ti + 1) * (ti + 2) / 2 <= t) ti++;
+  while (ti * (ti + 1) / 2 > t) ti--;
+  tj = t - ti * (ti + 1) / 2;
+  if (colmajor) {
+    const int64_t a = mt - 1 - tj, b = mt - 1 - ti;
+    ti = a;
+    tj = b;
+  }
+}
 
 // ---------------------------------------------------------------------------
 // main kernel
@@ -226,14 +249,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int64_t ti, tj;
-  const int64_t tb = blockIdx.x / p.ksplit;   // output tile
+  const int64_t tb = p.tile0 + blockIdx.x / p.ksplit;   // output tile
   const int ksp = (int)(blockIdx.x % p.ksplit);
   if (SYM) {  // lower-triangular tile ti >= tj
-    const int64_t t = tb;
-    ti = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-    while ((ti + 1) * (ti + 2) / 2 <= t) ti++;
-    while (ti * (ti + 1) / 2 > t) ti--;
-    tj = t - ti * (ti + 1) / 2;
+    sym_tile(tb, p.mt, p.colmajor, ti, tj);
   } else {
     ti = tb / p.nt;
     tj = tb % p.nt;
@@ -495,18 +514,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 // split order (deterministic), then the same store / add / subtract as the fused epilogue.
 template <bool SYM>
 __global__ void __launch_bounds__(256) oz_splitk_reduce(const float2* __restrict__ part, int ksplit, OzArgs p) {
-  const int64_t tb = blockIdx.x;
+  const int64_t tb = p.tile0 + blockIdx.x;
   int64_t ti, tj;
   if (SYM) {
-    ti = (int64_t)((sqrt(8.0 * (double)tb + 1.0) - 1.0) * 0.5);
-    while ((ti + 1) * (ti + 2) / 2 <= tb) ti++;
-    while (ti * (ti + 1) / 2 > tb) ti--;
-    tj = tb - ti * (ti + 1) / 2;
+    sym_tile(tb, p.mt, p.colmajor, ti, tj);
   } else {
     ti = tb / p.nt;
     tj = tb % p.nt;
   }
-  const float2* src = part + (size_t)tb * ksplit * (TM * TN);
+  const float2* src = part + (size_t)blockIdx.x * ksplit * (TM * TN);
   for (int idx = threadIdx.x; idx < TM * TN; idx += 256) {
     const int r = idx / TN, cc = idx % TN;
     const int64_t gi = ti * TM + r, gj = tj * TN + cc;
@@ -683,7 +699,7 @@ int prep_rows(const double* X, int64_t ld, int64_t n, int64_t k, const OzOperand
 
 template <int S, bool SYM>
 int launch_oz(const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, double* C, int64_t ldc, int mode,
-              const double* rowscale, int* flag, cudaStream_t st, int ksplit, void* part) {
+              const double* rowscale, int* flag, cudaStream_t st, int ksplit, void* part, const OzRange& range) {
   CUtensorMap ma, mb;
   int rc = encode(A, S, &ma);
   if (rc) return rc;
@@ -711,7 +727,17 @@ int launch_oz(const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, doub
   a.mode = mode;
   a.rowscale = rowscale;
   a.flag = flag;
-  const int64_t tiles = SYM ? mt * (mt + 1) / 2 : mt * nt;
+  const int64_t all_tiles = SYM ? mt * (mt + 1) / 2 : mt * nt;
+  a.tile0 = 0;
+  a.mt = mt;
+  a.colmajor = 0;
+  int64_t tiles = all_tiles;
+  if (range.ntiles >= 0) {   // a range of the triangle's tiles (sym only)
+    if (!SYM || range.tile0 < 0 || range.tile0 + range.ntiles > all_tiles) return GN_ERR_INVALID;
+    a.tile0 = range.tile0;
+    a.colmajor = range.colmajor;
+    tiles = range.ntiles;
+  }
   if (tiles <= 0) return GN_OK;
   const int nchunk_all = (int)((a.Kpad / BKS + a.spc - 1) / a.spc);
   if (ksplit < 1 || ch || mode == 3 || !part) ksplit = 1;   // split-K: single-exponent modes 0-2 only
@@ -785,15 +811,16 @@ OzOperand oz_operand_rows(const OzOperand& op, int S, int64_t row_off) {
 }
 
 int oz_gemm(int S, bool sym, const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, double* C, int64_t ldc,
-            int mode, const double* rowscale, int* flag, cudaStream_t st, int ksplit, void* part) {
+            int mode, const double* rowscale, int* flag, cudaStream_t st, int ksplit, void* part,
+            const OzRange& range) {
   if (A.kpad != B.kpad || A.kuse != B.kuse || A.kuse % BKS != 0 || A.kuse > A.kpad) return GN_ERR_INVALID;
   if (A.echunk != B.echunk || A.estride != B.estride || A.echunk % BKS != 0 || A.echunk > SPC * BKS ||
       (A.echunk > 0 && A.estride <= 0))
     return GN_ERR_INVALID;
 #define GN_OZ_CASE(s)                                                                     \
   case s:                                                                                 \
-    return sym ? launch_oz<s, true>(A, B, M, N, C, ldc, mode, rowscale, flag, st, ksplit, part)   \
-               : launch_oz<s, false>(A, B, M, N, C, ldc, mode, rowscale, flag, st, ksplit, part);
+    return sym ? launch_oz<s, true>(A, B, M, N, C, ldc, mode, rowscale, flag, st, ksplit, part, range)   \
+               : launch_oz<s, false>(A, B, M, N, C, ldc, mode, rowscale, flag, st, ksplit, part, range);
   switch (S) {
     GN_OZ_CASE(1)
     GN_OZ_CASE(2)
@@ -948,8 +975,8 @@ int prepare_for_capture(gn_handle* h) {
                          (size_t)64 * rup(h->Pp, 128) * 8 + 512;
       if (hil > need) need = hil;
     }
-    const size_t ch = chol_split_ws_bytes(h->Pp, S);
-    if (ch > need) need = ch;
+    const int rc = ensure_chol_ws(h, chol_split_ws_bytes(h->Pp, S));
+    if (rc) return rc;
     if (GN_NOTE(ensure_chol_streams(h)) != cudaSuccess) return GN_ERR_CUDA;
   }
   const int rc = ensure_split_ws(h, need);
@@ -982,6 +1009,72 @@ int split_gram(gn_handle* h, const double* J, int64_t ld, int64_t nrows, double*
   }
   rc = oz_gemm(S, true, op, op, h->Pp, h->Pp, G, h->Pp, accumulate ? 1 : 0, nullptr, h->flag + 2, h->st, ks, kpart);
   if (rc) return rc;
+  return GN_OK;
+}
+
+int64_t pipeline_chunk_tiles(gn_handle* h) {
+  if (h->pipe_tiles == 0 || h->precision != GN_PREC_SPLIT_ALL || h->n_rows <= 0) return 0;
+  if ((h->n_rows + h->jrows - 1) / h->jrows != 1) return 0;
+  int ks = h->gram_ksplit;
+  if (ks <= 0 && !lookup(h->n_slices, h->Pp, h->n_rows, &ks)) ks = 1;
+  if (ks != 1) return 0;
+  if ((h->Pp + TM - 1) / TM < 4) return 0;   // a G this small is one strip or two
+  if (h->pipe_tiles > 0) return h->pipe_tiles;
+  int sms = 0;
+  if (GN_NOTE(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->dev)) != cudaSuccess || sms < 8)
+    return 0;
+  return sms - sms / 8;   // leave an eighth of the SMs to the factorisation's chain
+}
+
+int split_gram_pipelined(gn_handle* h, const double* J, int64_t ld, int64_t nrows, double* G, double* A,
+                         const double* gamma, int64_t chunk, cudaStream_t st, cudaStream_t sg,
+                         std::vector<cudaEvent_t>& events, std::vector<cudaEvent_t>& gate) {
+  const int S = h->n_slices;
+  const int64_t n = h->Pp;
+  if (S < 1 || S > kOzMaxSlices || nrows <= 0 || chunk <= 0) return GN_ERR_INVALID;
+  const size_t opb = oz_operand_bytes(S, n, nrows);
+  const size_t cmb = (size_t)CM_CHUNKS * rup(n, TM) * 8 + 256;
+  int rc = ensure_split_ws(h, opb + cmb + gram_part_bytes(n, gram_max_split(h, nrows)));
+  if (rc) return rc;
+  OzOperand op = oz_operand_at(h->split_ws, S, n, nrows);
+  double* part = reinterpret_cast<double*>(static_cast<unsigned char*>(h->split_ws) + opb);
+  rc = oz_prepare_cols(S, J, ld, nrows, n, op, part, st);
+  if (rc) return rc;
+  auto new_event = [&](cudaEvent_t* e) -> bool {
+    *e = nullptr;
+    if (GN_NOTE(cudaEventCreateWithFlags(e, cudaEventDisableTiming)) != cudaSuccess) return false;
+    events.push_back(*e);
+    return true;
+  };
+  cudaEvent_t fork;
+  if (!new_event(&fork) || GN_NOTE(cudaEventRecord(fork, st)) != cudaSuccess ||
+      GN_NOTE(cudaStreamWaitEvent(sg, fork, 0)) != cudaSuccess)
+    return GN_ERR_CUDA;
+  const int64_t mt = (n + TM - 1) / TM, total = mt * (mt + 1) / 2;
+  const int64_t nstrip = (n + kCholStrip - 1) / kCholStrip;
+  gate.assign((size_t)nstrip, nullptr);
+  auto before = [&](int64_t c) { return c * mt - c * (c - 1) / 2; };   // tiles of the columns < c
+  int64_t tc = 0, strips_done = 0;
+  for (int64_t t0 = 0; t0 < total; t0 += chunk) {
+    OzRange rg;
+    rg.tile0 = t0;
+    rg.ntiles = (t0 + chunk < total) ? chunk : total - t0;
+    rg.colmajor = 1;
+    rc = oz_gemm(S, true, op, op, n, n, G, n, 0, nullptr, h->flag + 2, sg, 1, nullptr, rg);
+    if (rc) return rc;
+    while (tc < mt && before(tc + 1) <= t0 + rg.ntiles) tc++;   // tile columns [0, tc) are done
+    const int64_t sd = (tc * TM >= n) ? nstrip : tc * TM / kCholStrip;   // so are strips [0, sd)
+    if (sd > strips_done) {
+      const int64_t c0 = strips_done * kCholStrip, c1 = (sd * kCholStrip < n) ? sd * kCholStrip : n;
+      if (GN_NOTE(add_diag_band(G, A, n, n, c0, c1, gamma, sg)) != cudaSuccess) return GN_ERR_CUDA;
+      cudaEvent_t e;
+      if (!new_event(&e) || GN_NOTE(cudaEventRecord(e, sg)) != cudaSuccess) return GN_ERR_CUDA;
+      for (int64_t t = strips_done; t < sd; t++) gate[(size_t)t] = e;
+      strips_done = sd;
+    }
+  }
+  if (strips_done != nstrip) return GN_ERR_INVALID;   // every strip must have its gate
+  if (GN_NOTE(mirror_lower(G, n, n, sg)) != cudaSuccess) return GN_ERR_CUDA;
   return GN_OK;
 }
 

@@ -129,6 +129,22 @@ __global__ void copy_add_diag_kernel(const double* __restrict__ G, double* A, in
   }
 }
 
+// A[r][c] = G[r][c] (+ *gamma on the diagonal) for the columns [c0, c1) and rows r >= c of
+// the lower triangle: one band of the damped matrix the factorisation reads.
+__global__ void add_diag_band_kernel(const double* __restrict__ G, double* A, int64_t n, int64_t ld, int64_t c0,
+                                     int64_t c1, const double* __restrict__ gamma) {
+  const double gm = *gamma;
+  const int64_t w = c1 - c0, total = (n - c0) * w;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = c0 + idx / w, c = c0 + idx % w;
+    if (c > r) continue;
+    double v = G[r * ld + c];
+    if (r == c) v += gm;
+    A[r * ld + c] = v;
+  }
+}
+
 // G = u u^T (first) or beta G + (1 - beta) u u^T, the whole n x n matrix (row-major, ld)
 __global__ void ema_rank1_kernel(double* G, int64_t n, int64_t ld, const double* __restrict__ u, double beta,
                                  int first) {
@@ -228,6 +244,16 @@ cudaError_t dgemv_n(const double* A, int64_t lda, int64_t m, int64_t n, const do
 cudaError_t mirror_lower(double* G, int64_t n, int64_t ld, cudaStream_t st) {
   const int64_t nb = (n + 31) / 32;
   mirror_lower_kernel<<<dim3((unsigned)nb, (unsigned)nb), dim3(32, 8), 0, st>>>(G, n, ld);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t add_diag_band(const double* G, double* A, int64_t n, int64_t ld, int64_t c0, int64_t c1,
+                          const double* gamma, cudaStream_t st) {
+  if (c1 <= c0 || c0 >= n) return cudaSuccess;
+  const int64_t total = (n - c0) * (c1 - c0);
+  int64_t b = (total + 255) / 256;
+  if (b > 2048) b = 2048;
+  add_diag_band_kernel<<<(unsigned)b, 256, 0, st>>>(G, A, n, ld, c0, c1, gamma);
   count_launch();
   return cudaGetLastError();
 }

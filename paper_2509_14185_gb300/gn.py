@@ -107,6 +107,8 @@ EXPORTS = {
     "gn_batch_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "gn_batch_destroy": (ctypes.c_int, [_P]),
     "gn_set_gram_split": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gn_set_pipeline": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gn_pipeline_tiles": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
     "gn_set_lambda_trainable": (ctypes.c_int, [_P, ctypes.c_int]),
     "gn_set_stage1": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _D, _D]),
     "gn_field_jets": (ctypes.c_int, [_P, _P, _D, _P, _I64, _P]),
@@ -239,6 +241,16 @@ class GNProblem:
 
     def gn_set_gram_split(self, ksplit):
         _check(lib().gn_set_gram_split(self.h, int(ksplit)), "gn_set_gram_split")
+
+    def gn_set_pipeline(self, tiles):
+        """Tiles per Gram chunk of the pipelined graph step (0, the default: off; -1: from the SM count)."""
+        _check(lib().gn_set_pipeline(self.h, int(tiles)), "gn_set_pipeline")
+
+    def gn_pipeline_tiles(self):
+        """Tiles per Gram chunk of the next captured step (0: that step is not pipelined)."""
+        t = _I64(0)
+        _check(lib().gn_pipeline_tiles(self.h, ctypes.byref(t)), "gn_pipeline_tiles")
+        return int(t.value)
 
     def gn_gram_split_choice(self, nrows=None):
         k = ctypes.c_int(0)
