@@ -81,6 +81,14 @@ void free_all(gn_handle* h) {
   if (h->hpin) cudaFreeHost(h->hpin);
 }
 
+void destroy_side(gn_handle* h) {
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->st_aux) cudaStreamDestroy(h->st_aux);
+  h->ev_fork = h->ev_join = nullptr;
+  h->st_aux = nullptr;
+}
+
 // Device copy of the normalisation point: red[512 .. 513].
 double* norm_point(gn_handle* h) { return h->red + 512; }
 
@@ -113,6 +121,60 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
   const int64_t n = h->p.n_pts;
   if (ps.mode == MODE_GRADIENT) GN_TRY_CUDA(cudaMemsetAsync(h->gpart, 0, h->gpart_warps * a.ldg * 8, st));
 
+  // wall points and the normalisation row: rows of their own.  In residual and Jacobian
+  // modes they run on the handle's side stream, beside the Hilbert nodes and the interior
+  // (a one-point pass is latency-bound; alone it would add its whole latency); gradient mode
+  // accumulates every kind into the same per-warp partials, so it keeps them in order.
+  const bool side = ps.mode != MODE_GRADIENT && h->st_aux;
+  auto edge_rows = [&](cudaStream_t sx) -> int {
+    // wall points
+    if (h->p.n_bnd > 0) {
+      JetArgs b = a;
+      b.kind = KIND_WALL;
+      b.mode = ps.mode;
+      b.n = h->p.n_bnd;
+      b.y = h->p.y_bnd;
+      b.ystride = h->p.n_bnd;
+      b.wscale = rs * sqrt(2.0 * h->p.c_bnd / (double)h->p.n_bnd);
+      b.base = h->staged ? h->base_wall : nullptr;
+      b.row0 = n * h->ne;
+      b.r = ps.r;
+      b.J = ps.J;
+      b.ldJ = ps.ldJ;
+      b.jrow_lo = ps.jlo;
+      b.jrow_hi = ps.jhi;
+      b.seed = ps.seed;
+      GN_TRY_CUDA(launch_jet(b, sx, nullptr));
+    }
+    // normalisation row
+    {
+      JetArgs b = a;
+      b.kind = KIND_NORM;
+      b.mode = ps.mode;
+      b.n = 1;
+      b.y = norm_point(h);
+      b.ystride = 1;
+      b.wscale = rs * sqrt(2.0 * h->p.c_norm_w);
+      b.base = h->staged ? h->base_norm : nullptr;
+      b.c_norm = h->p.c_norm;
+      b.row0 = h->n_rows - 1;
+      b.r = ps.r;
+      b.J = ps.J;
+      b.ldJ = ps.ldJ;
+      b.jrow_lo = ps.jlo;
+      b.jrow_hi = ps.jhi;
+      b.seed = ps.seed;
+      GN_TRY_CUDA(launch_jet(b, sx, nullptr));
+    }
+    return GN_OK;
+  };
+  if (side) {
+    GN_TRY_CUDA(cudaEventRecord(h->ev_fork, st));
+    GN_TRY_CUDA(cudaStreamWaitEvent(h->st_aux, h->ev_fork, 0));
+    int rc = edge_rows(h->st_aux);
+    if (rc) return rc;
+    GN_TRY_CUDA(cudaEventRecord(h->ev_join, h->st_aux));
+  }
   // CCF: g at the positive Hilbert nodes (and their Jacobian rows), then U's K part.
   if (h->eq == GN_CCF) {
     JetArgs b = a;
@@ -156,44 +218,9 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
     b.sU = h->sU;
     GN_TRY_CUDA(launch_jet(b, st, nullptr));
   }
-  // wall points
-  if (h->p.n_bnd > 0) {
-    JetArgs b = a;
-    b.kind = KIND_WALL;
-    b.mode = ps.mode;
-    b.n = h->p.n_bnd;
-    b.y = h->p.y_bnd;
-    b.ystride = h->p.n_bnd;
-    b.wscale = rs * sqrt(2.0 * h->p.c_bnd / (double)h->p.n_bnd);
-    b.base = h->staged ? h->base_wall : nullptr;
-    b.row0 = n * h->ne;
-    b.r = ps.r;
-    b.J = ps.J;
-    b.ldJ = ps.ldJ;
-    b.jrow_lo = ps.jlo;
-    b.jrow_hi = ps.jhi;
-    b.seed = ps.seed;
-    GN_TRY_CUDA(launch_jet(b, st, nullptr));
-  }
-  // normalisation row
-  {
-    JetArgs b = a;
-    b.kind = KIND_NORM;
-    b.mode = ps.mode;
-    b.n = 1;
-    b.y = norm_point(h);
-    b.ystride = 1;
-    b.wscale = rs * sqrt(2.0 * h->p.c_norm_w);
-    b.base = h->staged ? h->base_norm : nullptr;
-    b.c_norm = h->p.c_norm;
-    b.row0 = h->n_rows - 1;
-    b.r = ps.r;
-    b.J = ps.J;
-    b.ldJ = ps.ldJ;
-    b.jrow_lo = ps.jlo;
-    b.jrow_hi = ps.jhi;
-    b.seed = ps.seed;
-    GN_TRY_CUDA(launch_jet(b, st, nullptr));
+  if (!side) {
+    int rc = edge_rows(st);
+    if (rc) return rc;
   }
   if (h->eq == GN_CCF && ps.mode == MODE_JACOBIAN) {
     // J[i, :] += sU_i * sum_j' Kf[i][j'] Jg[j', :] for interior rows inside the block
@@ -222,6 +249,7 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
                         ps.J + (lo - ps.jlo) * ps.ldJ, ps.ldJ, false, h->sU + lo, st));
     }
   }
+  if (side) GN_TRY_CUDA(cudaStreamWaitEvent(st, h->ev_join, 0));
   if (ps.mode == MODE_GRADIENT) {
     if (h->eq == GN_CCF && n > 0) {
       // t_j' = sum_i Kf[i][j'] c_i (c = seed * w * dR/dU, left in sU), then node pass seeded by t
@@ -447,7 +475,17 @@ int gn_init(const gn_problem* p, void* cuda_stream, gn_handle** out) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(norm_point(h), yn, 2 * sizeof(double), cudaMemcpyHostToDevice, h->st);
   if (e == cudaSuccess && h->eq == GN_CCF) e = hilbert_build(p->y, p->n_pts, h->M, h->kf, h->dcoef, h->snode, h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  // the side stream of the wall and normalisation passes (highest priority: a one-CTA pass
+  // should not queue behind the interior pass's CTAs)
+  if (e == cudaSuccess) {
+    int least = 0, greatest = 0;
+    e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->st_aux, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+  }
   if (e != cudaSuccess) {
+    destroy_side(h);
     free_all(h);
     delete h;
     return GN_ERR_CUDA;
@@ -463,6 +501,7 @@ int gn_destroy(gn_handle* h) {
   if (h->st_hi) cudaStreamDestroy(h->st_hi);
   if (h->st_lo) cudaStreamDestroy(h->st_lo);
   if (h->st_g) cudaStreamDestroy(h->st_g);
+  destroy_side(h);
   free_all(h);
   if (h->tmaps) free(h->tmaps);
   delete h;

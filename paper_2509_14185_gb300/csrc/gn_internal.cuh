@@ -144,6 +144,10 @@ struct gn_handle {
   cudaStream_t st_hi = nullptr;   // critical path (highest priority)
   cudaStream_t st_lo = nullptr;   // deferred bulk updates (middle priority)
   cudaStream_t st_g = nullptr;    // Gram chunks of the pipelined step (lowest priority)
+  // side stream of the wall and normalisation passes (residual and Jacobian modes), with the
+  // events that fork it from and join it to the handle's stream
+  cudaStream_t st_aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // the split factorisation's own workspace (U, strip operands, diagonal inverses), apart from
   // split_ws so that it can run while the Gram still reads its operand
   void* chol_ws = nullptr;

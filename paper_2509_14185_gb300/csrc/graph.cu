@@ -57,6 +57,8 @@ struct GraphState {
   cudaGraph_t g_step = nullptr, g_solve = nullptr;
   cudaGraphExec_t x_step = nullptr, x_solve = nullptr;
   cudaStream_t body = nullptr;    // capture stream of the line-search bodies
+  cudaStream_t body_aux = nullptr;   // the bodies' side stream (the handle's own st_aux has
+                                     // joined the step's capture, a sequence of its own)
   cudaStream_t gst = nullptr;     // stream the graphs are captured on and launched into (the
                                   // handle's own stream may be the legacy default stream,
                                   // which cannot be captured)
@@ -271,6 +273,8 @@ int capture_solve(gn_handle* h, double* theta, bool marks, const cudaEvent_t* ga
     GN_G_TRY(cudaStreamBeginCaptureToGraph(gs->body, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
     const long long k0 = g_launches.load();
     h->st = gs->body;
+    cudaStream_t aux_saved = h->st_aux;
+    if (h->st_aux) h->st_aux = gs->body_aux;   // a side stream that no other capture holds
     trial_kernel<<<grid_for(P), 256, 0, gs->body>>>(theta, h->delta, P, h->theta_t, ds);
     count_launch();
     int rc = GN_NOTE(cudaGetLastError()) == cudaSuccess ? GN_OK : GN_ERR_CUDA;
@@ -286,6 +290,7 @@ int capture_solve(gn_handle* h, double* theta, bool marks, const cudaEvent_t* ga
       if (GN_NOTE(cudaGetLastError()) != cudaSuccess) rc = GN_ERR_CUDA;
     }
     h->st = st;
+    h->st_aux = aux_saved;
     gs->k_trial = g_launches.load() - k0;
     cudaGraph_t out = nullptr;
     const cudaError_t ee = GN_NOTE(cudaStreamEndCapture(gs->body, &out));
@@ -383,6 +388,9 @@ int ensure_state(gn_handle* h, StepState* external_ds) {
     if (GN_NOTE(cudaMallocHost((void**)&gs->hs, sizeof(StepState))) != cudaSuccess) return GN_ERR_OOM;
     memset(gs->hs, 0, sizeof(StepState));
     GN_G_TRY(cudaStreamCreateWithFlags(&gs->body, cudaStreamNonBlocking));
+    int least = 0, greatest = 0;
+    GN_G_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    GN_G_TRY(cudaStreamCreateWithPriority(&gs->body_aux, cudaStreamNonBlocking, greatest));
     GN_G_TRY(cudaStreamCreateWithFlags(&gs->gst, cudaStreamNonBlocking));
     GN_G_TRY(cudaEventCreate(&gs->ev0));
     GN_G_TRY(cudaEventCreate(&gs->ev1));
@@ -487,6 +495,7 @@ void graph_release(gn_handle* h) {
   if (gs->ds_owned && gs->ds) cudaFree(gs->ds);
   if (gs->hs) cudaFreeHost(gs->hs);
   if (gs->body) cudaStreamDestroy(gs->body);
+  if (gs->body_aux) cudaStreamDestroy(gs->body_aux);
   if (gs->gst) cudaStreamDestroy(gs->gst);
   if (gs->ev_in) cudaEventDestroy(gs->ev_in);
   if (gs->ev0) cudaEventDestroy(gs->ev0);
