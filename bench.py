@@ -693,7 +693,7 @@ def micro_chol(args):
     res = float((A @ delta - g).abs().max() / (A.abs().max() * delta.abs().max()))
     print(json.dumps({"micro": "chol", "precision": args.precision, "n": Pp, "ms_median": statistics.median(times),
                       "ms_min": min(times), "rc": rc, "retries": retries, "backward_error": res,
-                      "diag_arith": "fp64" if os.environ.get("GN_DIAG_FP64") else "df"}))
+                      "diag_arith": "double-float"}))
     prob.close()
     return 0
 

@@ -165,8 +165,6 @@ struct ArithDF {
 };
 
 constexpr int kPotrfTPR = 16;                       // threads per row of the diagonal block
-constexpr int kPotrfEPT = NB / kPotrfTPR;             // elements (columns) per thread
-constexpr int kPotrfThreads = NB * kPotrfTPR;         // 1024
 constexpr size_t kPotrfSmem = (size_t)(NB * (NB + 1) + 4 * NB) * 8;   // final columns + 2 x 2 broadcast rows
 
 // Factor and invert the diagonal block B = A[k0:k0+kb, k0:k0+kb] (minus U, the
@@ -182,26 +180,30 @@ constexpr size_t kPotrfSmem = (size_t)(NB * (NB + 1) + 4 * NB) * 8;   // final c
 // so no value is rescaled inside the chain.  S[i][c] and Y[i][c] share one
 // register: column c of S is final (and published) at step c, exactly when
 // Y[i][c] starts to accumulate.  Thread (i, g) holds row i's elements
-// c = g + 16m (m = 0..3) in registers: four independent chains per thread,
-// 32 warps to hide the FP32 latency of the double-float arithmetic.
+// c = g + TPR m (m < 64 / TPR) in registers: independent chains per thread,
+// and with TPR = 16 (1024 threads, 4 chains each) 32 warps to hide the FP32
+// latency of the double-float arithmetic.  The sweep is a chain of dependent
+// steps: fewer threads per row (8: 5 % slower, 4: 30 % slower on GB300) leave
+// that latency exposed, though each thread then repeats less per-row work.
 // Each step publishes column j of S and row j of Y to shared memory (double
 // buffered, so one barrier per column suffices).  At the end
 // L'[i][j] = S[i][j] / sqrt(d_j) and L'^{-1}[i][c] = Y[i][c] / sqrt(d_i);
 // undoing D gives L = D^-1 L' and Linv = L'^{-1} D, written in FP64.
-template <class AR>
-__global__ void __launch_bounds__(kPotrfThreads) potrf_inv_kernel(double* A, int64_t lda, int64_t k0, int kb,
+template <class AR, int TPR>
+__global__ void __launch_bounds__(NB * TPR) potrf_inv_kernel(double* A, int64_t lda, int64_t k0, int kb,
                                                                   const float2* __restrict__ U, int64_t ldu,
                                                                   double* Linv, float2* LinvDF, int* scOut,
                                                                   const double* fw, double* fy, float2* fyDF,
                                                                   int* flag) {
   using T = typename AR::T;
+  constexpr int EPT = NB / TPR;   // elements (columns) per thread
   extern __shared__ __align__(16) unsigned char smraw[];
   T (*Lf)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smraw);   // unscaled final columns S[i][j], i >= j
   T* colbuf = reinterpret_cast<T*>(smraw) + NB * (NB + 1);     // [2][NB]: column j of S
   T* rowbuf = colbuf + 2 * NB;                                 // [2][NB]: row j of Y; reused for 1/sqrt(d)
   __shared__ int sc[NB];
   if (*flag) return;
-  const int t = threadIdx.x, i = t / kPotrfTPR, g = t % kPotrfTPR;
+  const int t = threadIdx.x, i = t / TPR, g = t % TPR;
   if (t < NB) {
     int e = 0;
     if (t < kb) {
@@ -215,10 +217,10 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_inv_kernel(double* A, int
     sc[t] = e;
   }
   __syncthreads();
-  T X[kPotrfEPT];
+  T X[EPT];
 #pragma unroll
-  for (int m = 0; m < kPotrfEPT; m++) {
-    const int c = g + kPotrfTPR * m;
+  for (int m = 0; m < EPT; m++) {
+    const int c = g + TPR * m;
     X[m] = AR::zero();
     if (i < kb && c <= i) {
       float2 u;
@@ -231,24 +233,24 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_inv_kernel(double* A, int
     T* cb = colbuf + (j & 1) * NB;
     T* rb = rowbuf + (j & 1) * NB;
     if (i < kb) {
-      if (g == j % kPotrfTPR && i >= j) {
+      if (g == j % TPR && i >= j) {
         // the owner of column j: constant register indices only (no indexed registers)
-        static_assert(kPotrfEPT == 4, "one case per register below");
-        T v;
-        switch (j / kPotrfTPR) {
-          case 0: v = X[0]; X[0] = AR::zero(); break;
-          case 1: v = X[1]; X[1] = AR::zero(); break;
-          case 2: v = X[2]; X[2] = AR::zero(); break;
-          default: v = X[3]; X[3] = AR::zero(); break;
-        }
+        const int jm = j / TPR;
+        T v = AR::zero();
+#pragma unroll
+        for (int m = 0; m < EPT; m++)
+          if (m == jm) {
+            v = X[m];
+            X[m] = AR::zero();
+          }
         // from here on the register accumulates Y[i][j] (0 below the diagonal of I)
         cb[i] = v;
         Lf[i][j] = v;
       }
       if (i == j) {
 #pragma unroll
-        for (int m = 0; m < kPotrfEPT; m++)
-          if (g + kPotrfTPR * m < j) rb[g + kPotrfTPR * m] = X[m];
+        for (int m = 0; m < EPT; m++)
+          if (g + TPR * m < j) rb[g + TPR * m] = X[m];
       }
     }
     __syncthreads();
@@ -259,11 +261,11 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_inv_kernel(double* A, int
     }
     if (i > j && i < kb) {
       const T a = AR::mul(cb[i], AR::rcp(d));
-      const int mmax = (i - g) >= 0 ? (i - g) / kPotrfTPR : -1;   // columns c = g + TPR m <= i
+      const int mmax = (i - g) >= 0 ? (i - g) / TPR : -1;   // columns c = g + TPR m <= i
 #pragma unroll
-      for (int m = 0; m < kPotrfEPT; m++) {
+      for (int m = 0; m < EPT; m++) {
         if (m > mmax) break;
-        const int c = g + kPotrfTPR * m;
+        const int c = g + TPR * m;
         // trailing: S[c][j] (column j); inverse: Y[j][c] (row j), with Y[j][j] = 1
         const T* src = (c > j) ? &cb[c] : &rb[c];
         const T v = (c == j) ? AR::one() : *src;
@@ -282,8 +284,8 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_inv_kernel(double* A, int
   double* Lk = Linv + (k0 / NB) * NB * NB;
   float2* Lf2 = LinvDF ? LinvDF + (k0 / NB) * NB * NB : nullptr;
 #pragma unroll
-  for (int m = 0; m < kPotrfEPT; m++) {
-    const int c = g + kPotrfTPR * m;
+  for (int m = 0; m < EPT; m++) {
+    const int c = g + TPR * m;
     T v = AR::zero();
     if (i < kb && c <= i) v = (c == i) ? rs[i] : AR::mul(X[m], rs[i]);   // L'^{-1}[i][c] = Y[i][c] / sqrt(d_i)
     Lk[i * NB + c] = (i < kb && c <= i) ? AR::store_scaled(v, -sc[c]) : 0.0;
@@ -294,19 +296,19 @@ __global__ void __launch_bounds__(kPotrfThreads) potrf_inv_kernel(double* A, int
   if (Lf2 && t < NB) scOut[(k0 / NB) * NB + t] = sc[t];
   if constexpr (std::is_same<T, DF>::value) {
     // forward substitution, block k: y_k = Linv_k w_k = L'^{-1} (D w_k); thread (i, g) sums its
-    // eight columns, the eight threads of row i combine their sums (lanes 8(i mod 4) .. +7)
+    // columns, the TPR threads of row i (consecutive lanes) combine their sums
     if (fw) {
       T acc = AR::zero();
 #pragma unroll
-      for (int m = 0; m < kPotrfEPT; m++) {
-        const int c = g + kPotrfTPR * m;
+      for (int m = 0; m < EPT; m++) {
+        const int c = g + TPR * m;
         if (i < kb && c <= i) {
           const T v = (c == i) ? rs[i] : AR::mul(X[m], rs[i]);
           acc = AR::add(acc, AR::mul(v, AR::load_scaled(fw[k0 + c], nullptr, -sc[c])));
         }
       }
 #pragma unroll
-      for (int o = 1; o < kPotrfTPR; o <<= 1) {
+      for (int o = 1; o < TPR; o <<= 1) {
         const T other = {__shfl_xor_sync(0xffffffffu, acc.h, o), __shfl_xor_sync(0xffffffffu, acc.l, o)};
         acc = AR::add(acc, other);
       }
@@ -625,8 +627,8 @@ cudaError_t launch_potrf(double* A, int64_t lda, int64_t k0, int kb, const float
                          float2* LinvDF, int* scOut, const double* fw, double* fy, float2* fyDF, int* flag,
                          cudaStream_t st) {
   static_assert(kPotrfSmem <= 48 * 1024, "the diagonal factor's shared memory needs no opt-in");
-  potrf_inv_kernel<AR><<<1, kPotrfThreads, kPotrfSmem, st>>>(A, lda, k0, kb, U, ldu, Linv, LinvDF, scOut, fw, fy,
-                                                              fyDF, flag);
+  potrf_inv_kernel<AR, kPotrfTPR><<<1, NB * kPotrfTPR, kPotrfSmem, st>>>(A, lda, k0, kb, U, ldu, Linv, LinvDF, scOut,
+                                                                          fw, fy, fyDF, flag);
   count_launch();
   return cudaGetLastError();
 }
