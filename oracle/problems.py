@@ -108,7 +108,8 @@ class Problem:
     """One profile fit: equation, MLP widths, collocation and wall points, loss weights."""
 
     def __init__(self, equation, widths, y, y_bnd=None, rho=None, c_bnd=1.0,
-                 y_norm=(1.0, 0.0), c_norm=1.0, c_norm_w=1.0, hilbert_m=1024, stage1=None, fourier=None):
+                 y_norm=(1.0, 0.0), c_norm=1.0, c_norm_w=1.0, hilbert_m=1024, stage1=None, fourier=None,
+                 y_inf=None, c_inf=1.0):
         self.eq = int(equation)
         self.widths = list(widths)
         self.d = DIM[self.eq]
@@ -125,6 +126,12 @@ class Problem:
         self.y_norm = tuple(float(v) for v in y_norm)
         self.c_norm = float(c_norm)
         self.c_norm_w = float(c_norm_w)
+        # decay points Y_inf of the data loss (Methods, "Training Loss", second data-loss term):
+        # the normalised field must vanish far from the origin
+        self.y_inf = (np.zeros((self.d, 0)) if y_inf is None
+                      else np.asarray(y_inf, dtype=np.float64).reshape(self.d, -1))
+        self.ninf = self.y_inf.shape[1]
+        self.c_inf = float(c_inf)
         self.M = int(hilbert_m)
         self.ne = N_EQ[self.eq]
         # Fourier-feature network (Methods, "Multi-stage Training", item 2): fourier = B, an
@@ -135,7 +142,7 @@ class Problem:
             assert self.fourier.shape == (self.widths[2] // 2, self.widths[1]) and self.widths[2] % 2 == 0
         self.P = sum(self.widths[i] * self.widths[i + 1] + self.widths[i + 1]
                      for i in range(len(self.widths) - 1) if not (self.fourier is not None and i == 1))
-        self.n_rows = self.n * self.ne + self.nb + 1
+        self.n_rows = self.n * self.ne + self.nb + self.ninf + 1
         # Multi-stage training (Methods, "Multi-stage Training"): stage1 = (widths1, theta1, eps)
         # makes every field Phi = Phi_1 + eps Phi_2 with Phi_1 the frozen stage-1 network and
         # Phi_2 this problem's network, and divides every row by eps (the normalised stage-2
@@ -243,6 +250,13 @@ class Problem:
             return np.zeros(0)
         return self.fields(theta, lam, self.y_bnd)[-1].v
 
+    def inf_values(self, theta, lam):
+        """Decay constraint values Phi_{A0}(y) at the points of Y_inf: the value (not a
+        derivative) of the normalised field, field 0 for every equation."""
+        if self.ninf == 0:
+            return np.zeros(0)
+        return self.fields(theta, lam, self.y_inf)[0].v
+
     def norm_value(self, theta, lam):
         """Normalisation constraint value Phi_{A0}(y_norm) (Boussinesq: d1 Omega there)."""
         ys = np.array(self.y_norm[:self.d], dtype=np.float64).reshape(self.d, 1)
@@ -254,13 +268,17 @@ class Problem:
     # -- weighted rows ------------------------------------------------------
     def rows(self, theta, lam):
         """r~ such that h = 1/2 |r~|^2 is the paper's d0 loss plus data loss:
-        h = (1/(N N_E)) sum rho R^2 + (c_bnd/N_b) sum R_b^2 + c_norm_w (Phi(y_norm) - C)^2."""
+        h = (1/(N N_E)) sum rho R^2 + (c_bnd/N_b) sum R_b^2 + c_inf sum_{Y_inf} Phi(y)^2
+            + c_norm_w (Phi(y_norm) - C)^2
+        (rows in that order: interior point-major, wall, decay, normalisation last)."""
         R = self.interior_residuals(theta, lam)
         w = np.sqrt(2.0 * self.rho / (self.n * self.ne))
         inner = np.stack([w * Rk for Rk in R], axis=1).reshape(-1)   # point-major
         parts = [inner]
         if self.nb:
             parts.append(np.sqrt(2.0 * self.c_bnd / self.nb) * self.wall_values(theta, lam))
+        if self.ninf:
+            parts.append(np.sqrt(2.0 * self.c_inf) * self.inf_values(theta, lam))
         parts.append(np.array([np.sqrt(2.0 * self.c_norm_w) * (self.norm_value(theta, lam) - self.c_norm)]))
         r = np.concatenate(parts)
         return r / self.stage1[2] if self.stage1 is not None else r

@@ -1,0 +1,101 @@
+"""Pins for the data loss's decay rows (Methods, "Training Loss": the normalised field
+Phi_{A0} must vanish at a set of points Y_inf far from the origin, weight c_inf).
+
+* Constant network (every weight zero, output bias b): each field is the ansatz envelope
+  times b, Phi_A = s_A(y) b q^{-k_A} with q = (1 + |y|^2)^{-1/(2(1+lambda))}, written out
+  here from that definition for each equation's normalised field (Burgers U, CCF Theta,
+  IPM P, Boussinesq Omega: odd, even, even, odd; k = lambda, lambda, lambda, -1).  The
+  decay rows must be sqrt(2 c_inf) times those values, between the wall rows and the
+  normalisation row.
+* A decay point is a normalisation row with target 0 and the same weight (except for
+  Boussinesq, whose normalisation row is a derivative): the two assemblies agree on a
+  trained-looking random network.
+* g = J~^T r~ stays the gradient of h with decay rows (complex step of h, no Jacobian code).
+"""
+import numpy as np
+import pytest
+
+from oracle import gn
+from oracle import problems as Pb
+from paper_2509_14185_gb300 import inputs as I
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+CASES = [(Pb.BURGERS, [1, 5, 1]), (Pb.CCF, [1, 5, 1]), (Pb.IPM, [2, 5, 2]), (Pb.BOUSSINESQ, [2, 5, 3])]
+
+
+def far_points(d, n, seed):
+    rng = np.random.default_rng(seed)
+    r = 10.0 ** rng.uniform(1.0, 3.0, n)
+    if d == 1:
+        return (r * rng.choice([-1.0, 1.0], n)).reshape(1, n)
+    a = rng.uniform(0.0, np.pi / 2, n)
+    return np.stack([r * np.cos(a), r * np.sin(a)])
+
+
+def closed_form_field0(eq, y, lam, b):
+    """Phi_{A0} of the constant network NN = b, from the ansatz definition."""
+    u = 1.0 + np.sum(y * y, axis=0)
+    q = u ** (-1.0 / (2.0 * (1.0 + lam)))
+    if eq == Pb.BURGERS:
+        return (y[0] / np.sqrt(u)) * b * q ** (-lam)
+    if eq == Pb.CCF:
+        return (y[0] ** 2 / u) * b * q ** (-lam)
+    if eq == Pb.IPM:
+        return b * q ** (-lam)
+    return (y[0] / np.sqrt(u)) * b * q      # Boussinesq Omega, k = -1
+
+
+@pytest.mark.parametrize("eq,widths", CASES)
+def test_decay_rows_of_constant_network(eq, widths):
+    w = I.small_case(eq, widths, 7, n_bnd=3, m=16)
+    yinf = far_points(w.d, 5, 3)
+    c_inf = 0.7
+    p = Pb.Problem(eq, widths, w.y, w.y_bnd, y_norm=w.y_norm, hilbert_m=16, y_inf=yinf, c_inf=c_inf)
+    theta = np.zeros(p.P)
+    b = np.array([1.3, -0.4, 0.9])[: widths[-1]]
+    theta[-widths[-1]:] = b
+    lam = 0.37
+    r = p.rows(theta, lam)
+    assert len(r) == p.n_rows == p.n * p.ne + p.nb + 5 + 1
+    lo = p.n * p.ne + p.nb
+    want = np.sqrt(2.0 * c_inf) * closed_form_field0(eq, yinf, lam, b[0])
+    np.testing.assert_allclose(r[lo:lo + 5], want, rtol=1e-13, atol=1e-300)
+    # the other rows are those of the problem without decay points, in place
+    p0 = Pb.Problem(eq, widths, w.y, w.y_bnd, y_norm=w.y_norm, hilbert_m=16)
+    r0 = p0.rows(theta, lam)
+    np.testing.assert_array_equal(r[:lo], r0[:lo])
+    assert r[-1] == r0[-1]
+    # and the loss gains exactly c_inf sum Phi^2
+    assert p.loss(theta, lam) == pytest.approx(p0.loss(theta, lam) + c_inf * np.sum(want ** 2 / (2 * c_inf)),
+                                               rel=1e-14)
+
+
+@pytest.mark.parametrize("eq,widths", CASES[:3])
+def test_decay_row_is_a_zero_target_normalisation_row(eq, widths):
+    w = I.small_case(eq, widths, 6, n_bnd=2, m=16, seed=4)
+    yinf = far_points(w.d, 3, 8)
+    p = Pb.Problem(eq, widths, w.y, w.y_bnd, y_norm=w.y_norm, hilbert_m=16, y_inf=yinf, c_inf=2.5)
+    r = p.rows(w.theta, w.lam)
+    lo = p.n * p.ne + p.nb
+    for k in range(3):
+        yn = tuple(yinf[:, k]) + ((0.0,) if w.d == 1 else ())
+        pn = Pb.Problem(eq, widths, w.y, w.y_bnd, y_norm=yn, c_norm=0.0, c_norm_w=2.5, hilbert_m=16)
+        assert r[lo + k] == pytest.approx(pn.rows(w.theta, w.lam)[-1], rel=1e-14, abs=1e-300)
+
+
+@pytest.mark.parametrize("eq,widths", [(Pb.CCF, [1, 6, 1]), (Pb.BOUSSINESQ, [2, 5, 3])])
+def test_gradient_with_decay_rows(eq, widths):
+    w = I.small_case(eq, widths, 10, n_bnd=4, m=32)
+    p = Pb.Problem(eq, widths, w.y, w.y_bnd, y_norm=w.y_norm, hilbert_m=32, y_inf=far_points(w.d, 4, 1),
+                   c_inf=0.5)
+    J = gn.jacobian(p, w.theta, w.lam)
+    g = J.T @ p.rows(w.theta, w.lam)
+    x = np.concatenate([w.theta, [w.lam]]).astype(np.complex128)
+    h = 1e-30
+    for j in [0, p.P // 2, p.P]:
+        xc = x.copy()
+        xc[j] += 1j * h
+        r = p.rows(xc[:-1], xc[-1])
+        dh = (0.5 * np.sum(r * r)).imag / h
+        assert abs(dh - g[j]) <= 1e-11 * (abs(g[j]) + 1e-3 * np.max(np.abs(g)))
