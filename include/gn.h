@@ -119,6 +119,11 @@ typedef struct gn_problem {
                                 n_layers >= 3 */
   const double* fourier_B;   /* host [fourier_m x widths[1]] row-major, B ~ N(0, sigma^2) drawn by
                                 the caller; copied by gn_init */
+  int64_t n_inf;             /* decay points Y_inf of the data loss (Methods, "Training Loss"): rows
+                                sqrt(2 c_inf) Phi_A0(y), the value of the normalised field (field 0),
+                                placed after the wall rows and before the normalisation row; 0: none */
+  const double* y_inf;       /* device, SoA [d][n_inf]. Borrowed: must stay valid until gn_destroy. */
+  double c_inf;              /* weight c_inf of the decay rows (the loss gains c_inf sum Phi_A0(y)^2) */
 } gn_problem;
 
 /* Normalisation row (data loss) per equation, fixed by the library:

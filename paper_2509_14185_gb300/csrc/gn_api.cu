@@ -54,6 +54,7 @@ int validate(const gn_problem* p) {
   if (p->n_pts < 0 || (p->n_pts > 0 && !p->y)) return GN_ERR_INVALID;
   if (d == 1 && p->n_bnd != 0) return GN_ERR_INVALID;
   if (p->n_bnd < 0 || (p->n_bnd > 0 && !p->y_bnd)) return GN_ERR_INVALID;
+  if (p->n_inf < 0 || (p->n_inf > 0 && !p->y_inf) || !(p->c_inf >= 0.0)) return GN_ERR_INVALID;
   if (p->equation == GN_CCF) {
     if (p->hilbert_m < 8 || p->hilbert_m > 16384 || (p->hilbert_m & 1)) return GN_ERR_INVALID;
   }
@@ -75,7 +76,8 @@ cudaError_t dalloc(T** p, size_t count) {
 void free_all(gn_handle* h) {
   void* ptrs[] = {h->ema_ws, h->wt, h->theta_t, h->r, h->J, h->G, h->A, h->Linv, h->g, h->delta, h->vtmp, h->red,
                   h->flag, h->gpart, h->kf, h->dcoef, h->snode, h->gnode, h->Jg, h->ug, h->sU, h->tnode,
-                  h->split_ws, h->chol_ws, h->base_int, h->base_wall, h->base_norm, h->base_node, h->fourierW};
+                  h->split_ws, h->chol_ws, h->base_int, h->base_wall, h->base_norm, h->base_node, h->fourierW,
+                  h->base_inf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->hpin) cudaFreeHost(h->hpin);
@@ -138,6 +140,26 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
       b.wscale = rs * sqrt(2.0 * h->p.c_bnd / (double)h->p.n_bnd);
       b.base = h->staged ? h->base_wall : nullptr;
       b.row0 = n * h->ne;
+      b.r = ps.r;
+      b.J = ps.J;
+      b.ldJ = ps.ldJ;
+      b.jrow_lo = ps.jlo;
+      b.jrow_hi = ps.jhi;
+      b.seed = ps.seed;
+      GN_TRY_CUDA(launch_jet(b, sx, nullptr));
+    }
+    // decay rows of the data loss: sqrt(2 c_inf) Phi_A0 at the far points
+    if (h->p.n_inf > 0) {
+      JetArgs b = a;
+      b.kind = KIND_INF;
+      b.mode = ps.mode;
+      b.n = h->p.n_inf;
+      b.y = h->p.y_inf;
+      b.ystride = h->p.n_inf;
+      b.wscale = rs * sqrt(2.0 * h->p.c_inf);
+      b.base = h->staged ? h->base_inf : nullptr;
+      b.c_norm = 0.0;
+      b.row0 = n * h->ne + h->p.n_bnd;
       b.r = ps.r;
       b.J = ps.J;
       b.ldJ = ps.ldJ;
@@ -410,7 +432,7 @@ int gn_init(const gn_problem* p, void* cuda_stream, gn_handle** out) {
   net.P = off;
   h->P = off;
   h->Pp = off + 1;
-  h->n_rows = p->n_pts * h->ne + (h->d == 2 ? p->n_bnd : 0) + 1;
+  h->n_rows = p->n_pts * h->ne + (h->d == 2 ? p->n_bnd : 0) + p->n_inf + 1;
   h->ldJ = round_up(h->Pp, 16);
   const double jbytes = (double)h->n_rows * h->ldJ * 8.0;
   const double jcap = 32.0 * (1ull << 30);

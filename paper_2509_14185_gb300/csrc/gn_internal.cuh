@@ -31,7 +31,8 @@ enum PointKind : int {
   KIND_WALL = 1,      // wall point (2D): one row, the stream function value
   KIND_NORM = 2,      // normalisation point: one row
   KIND_NODE = 3,      // CCF Hilbert node: one row, g = Theta / y at the node
-  KIND_PROBE = 4      // field jets at a point: per field value, gradient, Hessian (2D) into r
+  KIND_PROBE = 4,     // field jets at a point: per field value, gradient, Hessian (2D) into r
+  KIND_INF = 5        // decay point of the data loss: one row, the value of field 0
 };
 
 enum JetMode : int { MODE_RESIDUAL = 0, MODE_JACOBIAN = 1, MODE_GRADIENT = 2 };
@@ -168,6 +169,7 @@ struct gn_handle {
   double* base_int = nullptr;     // [n_pts][base_ld]
   double* base_wall = nullptr;    // [n_bnd][base_ld]
   double* base_norm = nullptr;    // [base_ld]
+  double* base_inf = nullptr;     // [n_inf][base_ld]
   double* base_node = nullptr;    // [Mh] (CCF)
   double* fourierW = nullptr;     // Fourier layer rows [B; B] (2m' x m), when the network has one
 };

@@ -423,8 +423,9 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
       }
     } else if (kind == KIND_WALL) {
       R[0] = F[NF - 1].v;
-    } else if (kind == KIND_NORM) {
-      R[0] = (EQ == GN_BOUSSINESQ) ? F[0].g[0] : F[0].v;
+    } else if (kind == KIND_NORM || kind == KIND_INF) {
+      // normalisation: Phi_A0 (Boussinesq: d1 Omega) minus its target; decay: Phi_A0 itself
+      R[0] = (EQ == GN_BOUSSINESQ && kind == KIND_NORM) ? F[0].g[0] : F[0].v;
       R[0].v -= A.c_norm;
     } else {  // KIND_NODE (CCF): g = y/u * NN * q^{-lambda}
       const YJ<D> Eg = envelope<D>(y, u, 1, dconst(-1.0) + 0.5 * (lamd * a));

@@ -56,6 +56,9 @@ class gn_problem(ctypes.Structure):
         ("n_slices", ctypes.c_int),
         ("fourier_m", ctypes.c_int),
         ("fourier_B", ctypes.c_void_p),
+        ("n_inf", ctypes.c_int64),
+        ("y_inf", ctypes.c_void_p),
+        ("c_inf", ctypes.c_double),
     ]
 
 
@@ -172,7 +175,7 @@ class GNProblem:
 
     def __init__(self, equation, widths, y, y_bnd=None, rho=None, c_bnd=1.0, y_norm=(1.0, 0.0), c_norm=1.0,
                  c_norm_w=1.0, hilbert_m=1024, precision=GN_PREC_FP64, n_slices=4, device="cuda", stream=None,
-                 fourier_B=None):
+                 fourier_B=None, y_inf=None, c_inf=1.0):
         lib()
         self.device = torch.device(device)
         self.equation = int(equation)
@@ -185,6 +188,10 @@ class GNProblem:
         self.y_bnd = torch.from_numpy(np.ascontiguousarray(yb)).to(self.device) if yb.size else None
         self.n_bnd = yb.shape[1] if yb.size else 0
         self.rho = None if rho is None else torch.as_tensor(rho, dtype=torch.float64, device=self.device).contiguous()
+        # decay points of the data loss (SoA [d][n_inf]); rows after the wall rows
+        yi = np.zeros((self.d, 0)) if y_inf is None else np.asarray(y_inf, dtype=np.float64).reshape(self.d, -1)
+        self.y_inf = torch.from_numpy(np.ascontiguousarray(yi)).to(self.device) if yi.size else None
+        self.n_inf = yi.shape[1] if yi.size else 0
         p = gn_problem()
         p.equation = self.equation
         p.n_layers = len(self.widths) - 1
@@ -202,6 +209,9 @@ class GNProblem:
         p.hilbert_m = int(hilbert_m)
         p.precision = int(precision)
         p.n_slices = int(n_slices)
+        p.n_inf = self.n_inf
+        p.y_inf = self.y_inf.data_ptr() if self.y_inf is not None else None
+        p.c_inf = float(c_inf)
         if fourier_B is not None:
             # host copy kept alive for gn_init (which copies it)
             self._fourier_B = np.ascontiguousarray(np.asarray(fourier_B, dtype=np.float64))
@@ -221,6 +231,8 @@ class GNProblem:
 
     @classmethod
     def from_workload(cls, w, **kw):
+        kw.setdefault("y_inf", getattr(w, "y_inf", None))
+        kw.setdefault("c_inf", getattr(w, "c_inf", 1.0))
         return cls(w.equation, w.widths, w.y, w.y_bnd if w.y_bnd.size else None, w.rho, y_norm=w.y_norm,
                    c_norm=w.c_norm, hilbert_m=w.hilbert_m, **kw)
 

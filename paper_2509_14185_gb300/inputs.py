@@ -113,6 +113,8 @@ class Workload:
     y_norm: tuple = (1.0, 0.0)
     c_norm: float = 1.0
     rho: Optional[np.ndarray] = None
+    y_inf: Optional[np.ndarray] = None   # (d, n_inf) decay points of the data loss, or None
+    c_inf: float = 1.0
 
     @property
     def d(self) -> int:
