@@ -59,6 +59,10 @@ def test_decay_rows_match_oracle(name):
 
 @pytest.mark.parametrize("name", ["burgers", "ipm"])
 def test_decay_rows_gn_step_matches_oracle(name):
+    """Far decay points make G + gamma I ill-conditioned (cond ~1e9 for Burgers).  The two
+    sides' G agree to the Jacobian's parity level (~1e-14 relative), so their steps may
+    differ by cond times that; what is well-posed is that the GPU step solves the oracle's
+    damped normal equations to a backward error of rounding size."""
     w = with_decay(name, seed=5)
     p = oracle_problem(w)
     th_o, lam_o, gam_o, info_o = ogn.gn_step(p, w.theta, w.lam, w.gamma)
@@ -71,8 +75,12 @@ def test_decay_rows_gn_step_matches_oracle(name):
         assert info["alpha"] == info_o["alpha"]
         d_gpu = np.concatenate([w.theta - host(theta), [w.lam - lam]])
         d_o = np.concatenate([w.theta - th_o, [w.lam - lam_o]])
-        cond = np.linalg.cond(info_o["G"] + info_o["gamma_used"] * np.eye(len(d_o)))
-        assert rel(d_gpu, d_o) <= max(TOL, 1e-15 * cond)
+        A = info_o["G"] + info_o["gamma_used"] * np.eye(len(d_o))
+        g_o = ogn.jacobian(p, w.theta, w.lam).T @ p.rows(w.theta, w.lam)
+        delta = d_gpu / info["alpha"]
+        be = np.max(np.abs(A @ delta - g_o)) / (np.max(np.abs(A)) * np.max(np.abs(delta)) + np.max(np.abs(g_o)))
+        assert be <= 1e-12
+        assert rel(d_gpu, d_o) <= max(TOL, 1e-13 * np.linalg.cond(A))
     prob.close()
 
 
