@@ -965,6 +965,8 @@ def main():
     prob = gn.GNProblem.from_workload(w, precision=prec, n_slices=args.slices)
     if args.pipeline is not None:
         prob.gn_set_pipeline(args.pipeline)
+    if args.gram_split:
+        prob.gn_set_gram_split(args.gram_split)
     stream = torch.cuda.current_stream()
     theta = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
     lam, gam = w.lam, w.gamma
