@@ -32,8 +32,9 @@ if ROOT not in sys.path:
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one split Gram launch,
 # ozaki_kernel<6,1,0> on the CCF 1st-unstable workload (2278 tiles, S = 6), from a single-pass
-# ncu capture of `bench.py --steps 1 --warmup 1`: 18.37 GB read + 0.29 GB written.  Valid only
-# for that kernel build and workload; re-measure when either changes.
+# ncu capture of `bench.py --eager --gram-split 1 --steps 1 --warmup 1` (the eager path: ncu
+# lists no kernels inside graphs with conditional nodes): 18.18 GB read + 0.31 GB written.  Valid
+# only for that kernel build and workload; re-measure when either changes.
 GRAM_TRAFFIC_BYTES_CCF_S6 = 18.18e9 + 0.31e9
 
 METRIC = "gn_steps_per_s"
