@@ -109,7 +109,7 @@ class Problem:
 
     def __init__(self, equation, widths, y, y_bnd=None, rho=None, c_bnd=1.0,
                  y_norm=(1.0, 0.0), c_norm=1.0, c_norm_w=1.0, hilbert_m=1024, stage1=None, fourier=None,
-                 y_inf=None, c_inf=1.0):
+                 y_inf=None, c_inf=1.0, norm_field=None, norm_deriv=None):
         self.eq = int(equation)
         self.widths = list(widths)
         self.d = DIM[self.eq]
@@ -126,6 +126,12 @@ class Problem:
         self.y_norm = tuple(float(v) for v in y_norm)
         self.c_norm = float(c_norm)
         self.c_norm_w = float(c_norm_w)
+        # the constrained field A0 and whether the normalisation row takes its value (0) or its
+        # d/dy1 (1) (Methods, "Training Loss": constraints on a field's values or derivatives).
+        # Defaults: field 0's value, except Boussinesq's d1 Omega(0, 0) = 1
+        self.norm_field = 0 if norm_field is None else int(norm_field)
+        self.norm_deriv = (1 if self.eq == BOUSSINESQ else 0) if norm_deriv is None else int(norm_deriv)
+        assert 0 <= self.norm_field < N_FIELDS[self.eq] and self.norm_deriv in (0, 1)
         # decay points Y_inf of the data loss (Methods, "Training Loss", second data-loss term):
         # the normalised field must vanish far from the origin
         self.y_inf = (np.zeros((self.d, 0)) if y_inf is None
@@ -252,16 +258,17 @@ class Problem:
 
     def inf_values(self, theta, lam):
         """Decay constraint values Phi_{A0}(y) at the points of Y_inf: the value (not a
-        derivative) of the normalised field, field 0 for every equation."""
+        derivative) of the normalised field A0."""
         if self.ninf == 0:
             return np.zeros(0)
-        return self.fields(theta, lam, self.y_inf)[0].v
+        return self.fields(theta, lam, self.y_inf)[self.norm_field].v
 
     def norm_value(self, theta, lam):
-        """Normalisation constraint value Phi_{A0}(y_norm) (Boussinesq: d1 Omega there)."""
+        """Normalisation constraint value Phi_{A0}(y_norm), or its d/dy1 (the Boussinesq
+        default: d1 Omega there)."""
         ys = np.array(self.y_norm[:self.d], dtype=np.float64).reshape(self.d, 1)
-        F = self.fields(theta, lam, ys)[0]
-        if self.eq == BOUSSINESQ:
+        F = self.fields(theta, lam, ys)[self.norm_field]
+        if self.norm_deriv:
             return F.g[0][0]
         return F.v[0]
 

@@ -99,3 +99,57 @@ def test_gradient_with_decay_rows(eq, widths):
         r = p.rows(xc[:-1], xc[-1])
         dh = (0.5 * np.sum(r * r)).imag / h
         assert abs(dh - g[j]) <= 1e-11 * (abs(g[j]) + 1e-3 * np.max(np.abs(g)))
+
+
+# the normalisation constraint on another field, or on a derivative (Methods, "Training Loss":
+# constraints may act on more than one field or on derivatives of a field)
+
+def closed_form_field(eq, f, y, lam, b):
+    """Field f of the constant network NN = b from the ansatz: s_A b q^{-k_A} with the
+    parity classes (odd: s = y1 / sqrt(u), even: s = 1) and exponents of each equation."""
+    u = 1.0 + np.sum(y * y, axis=0)
+    q = u ** (-1.0 / (2.0 * (1.0 + lam)))
+    odd = y[0] / np.sqrt(u)
+    if eq == Pb.IPM:
+        return [b * q ** (-lam), odd * b * q ** (-(1.0 + 2.0 * lam))][f]
+    return [odd * b * q, b * q ** (-(lam - 1.0)), odd * b * q ** (-(1.0 + 2.0 * lam))][f]
+
+
+@pytest.mark.parametrize("eq,widths", [(Pb.IPM, [2, 4, 2]), (Pb.BOUSSINESQ, [2, 4, 3])])
+def test_normalisation_on_each_field(eq, widths):
+    w = I.small_case(eq, widths, 5, n_bnd=2, m=16)
+    lam, yn, cn, cw = 0.41, (0.7, 1.3), 0.25, 1.7
+    b = np.array([1.3, -0.4, 0.9])[: widths[-1]]
+    for f in range(widths[-1]):
+        p = Pb.Problem(eq, widths, w.y, w.y_bnd, y_norm=yn, c_norm=cn, c_norm_w=cw, norm_field=f, norm_deriv=0,
+                       y_inf=far_points(2, 3, 2), c_inf=0.6)
+        theta = np.zeros(p.P)
+        theta[-widths[-1]:] = b
+        r = p.rows(theta, lam)
+        phi = closed_form_field(eq, f, np.array(yn).reshape(2, 1), lam, b[f])[0]
+        assert r[-1] == pytest.approx(np.sqrt(2.0 * cw) * (phi - cn), rel=1e-13)
+        # the decay rows constrain the same field
+        lo = p.n * p.ne + p.nb
+        want = np.sqrt(2.0 * 0.6) * closed_form_field(eq, f, p.y_inf, lam, b[f])
+        np.testing.assert_allclose(r[lo:lo + 3], want, rtol=1e-13)
+
+
+@pytest.mark.parametrize("eq,widths,f", [(Pb.BURGERS, [1, 6, 1], 0), (Pb.IPM, [2, 6, 2], 1),
+                                         (Pb.BOUSSINESQ, [2, 6, 3], 1)])
+def test_normalisation_derivative_is_d_dy1_of_the_value(eq, widths, f):
+    w = I.small_case(eq, widths, 5, n_bnd=2, m=16, seed=9)
+    yn = (0.8, 0.6)
+    kw = dict(c_norm=0.0, c_norm_w=0.5, norm_field=f)
+    p = Pb.Problem(eq, widths, w.y, w.y_bnd, y_norm=yn, norm_deriv=1, **kw)
+    d = p.rows(w.theta, w.lam)[-1]
+    h = 1e-5
+    vals = []
+    for s in (1.0, -1.0):
+        ys = (yn[0] + s * h, yn[1])
+        pv = Pb.Problem(eq, widths, w.y, w.y_bnd, y_norm=ys, norm_deriv=0, **kw)
+        vals.append(pv.rows(w.theta, w.lam)[-1])
+    fd = (vals[0] - vals[1]) / (2 * h)
+    assert abs(d - fd) <= 1e-7 * max(1.0, abs(d))
+    # and the defaults are the equation's own constraint (Boussinesq: d1 Omega; others: the value)
+    p0 = Pb.Problem(eq, widths, w.y, w.y_bnd, y_norm=yn)
+    assert p0.norm_field == 0 and p0.norm_deriv == (1 if eq == Pb.BOUSSINESQ else 0)
