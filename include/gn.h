@@ -124,6 +124,11 @@ typedef struct gn_problem {
                                 placed after the wall rows and before the normalisation row; 0: none */
   const double* y_inf;       /* device, SoA [d][n_inf]. Borrowed: must stay valid until gn_destroy. */
   double c_inf;              /* weight c_inf of the decay rows (the loss gains c_inf sum Phi_A0(y)^2) */
+  int norm_kind;             /* the normalisation constraint (Methods, "Training Loss": on a field's
+                                value or derivative): 0 the equation's own (value of field 0;
+                                Boussinesq d Omega / d y1), 1 the value of field norm_field,
+                                2 its d/dy1.  The decay rows take the value of the same field. */
+  int norm_field;            /* field A0 for norm_kind 1 and 2 (0 .. fields - 1) */
 } gn_problem;
 
 /* Normalisation row (data loss) per equation, fixed by the library:

@@ -55,6 +55,8 @@ int validate(const gn_problem* p) {
   if (d == 1 && p->n_bnd != 0) return GN_ERR_INVALID;
   if (p->n_bnd < 0 || (p->n_bnd > 0 && !p->y_bnd)) return GN_ERR_INVALID;
   if (p->n_inf < 0 || (p->n_inf > 0 && !p->y_inf) || !(p->c_inf >= 0.0)) return GN_ERR_INVALID;
+  if (p->norm_kind < 0 || p->norm_kind > 2) return GN_ERR_INVALID;
+  if (p->norm_kind > 0 && (p->norm_field < 0 || p->norm_field >= fields_of(p->equation))) return GN_ERR_INVALID;
   if (p->equation == GN_CCF) {
     if (p->hilbert_m < 8 || p->hilbert_m > 16384 || (p->hilbert_m & 1)) return GN_ERR_INVALID;
   }
@@ -116,6 +118,9 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
   a.fW = h->fourierW;
   a.eps = h->stage_eps;
   a.base_ld = h->base_ld;
+  // the normalisation constraint's field and derivative (the decay rows use the same field)
+  a.nfield = h->p.norm_kind > 0 ? h->p.norm_field : 0;
+  a.nderiv = h->p.norm_kind == 2 || (h->p.norm_kind == 0 && h->eq == GN_BOUSSINESQ);
   // stage 2: rows are R(Phi_1 + eps Phi_2) / eps (unless the caller wants R itself)
   const double rs = (h->staged && !ps.unweighted) ? 1.0 / h->stage_eps : 1.0;
   a.ldg = round_up(h->Pp, 16);

@@ -70,6 +70,7 @@ struct JetArgs {
   const double* rho;     // interior weights (may be null)
   double wscale;         // row weight factor (see jet.cu)
   double c_norm;         // normalisation target (KIND_NORM)
+  int nfield, nderiv;    // KIND_NORM / KIND_INF: the constrained field, and d/dy1 (NORM only)
   int64_t row0;          // row of point 0, first equation
   double* r;             // r~ output (may be null)
   double* J;             // Jacobian output (MODE_JACOBIAN)

@@ -424,8 +424,15 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
     } else if (kind == KIND_WALL) {
       R[0] = F[NF - 1].v;
     } else if (kind == KIND_NORM || kind == KIND_INF) {
-      // normalisation: Phi_A0 (Boussinesq: d1 Omega) minus its target; decay: Phi_A0 itself
-      R[0] = (EQ == GN_BOUSSINESQ && kind == KIND_NORM) ? F[0].g[0] : F[0].v;
+      // normalisation: Phi_A0 or its d/dy1 minus the target; decay: Phi_A0 itself
+      Dl val = F[0].v, dy1 = F[0].g[0];
+#pragma unroll
+      for (int f = 1; f < NF; f++)   // constant register indices only
+        if (f == A.nfield) {
+          val = F[f].v;
+          dy1 = F[f].g[0];
+        }
+      R[0] = (kind == KIND_NORM && A.nderiv) ? dy1 : val;
       R[0].v -= A.c_norm;
     } else {  // KIND_NODE (CCF): g = y/u * NN * q^{-lambda}
       const YJ<D> Eg = envelope<D>(y, u, 1, dconst(-1.0) + 0.5 * (lamd * a));

@@ -59,6 +59,8 @@ class gn_problem(ctypes.Structure):
         ("n_inf", ctypes.c_int64),
         ("y_inf", ctypes.c_void_p),
         ("c_inf", ctypes.c_double),
+        ("norm_kind", ctypes.c_int),
+        ("norm_field", ctypes.c_int),
     ]
 
 
@@ -175,7 +177,7 @@ class GNProblem:
 
     def __init__(self, equation, widths, y, y_bnd=None, rho=None, c_bnd=1.0, y_norm=(1.0, 0.0), c_norm=1.0,
                  c_norm_w=1.0, hilbert_m=1024, precision=GN_PREC_FP64, n_slices=4, device="cuda", stream=None,
-                 fourier_B=None, y_inf=None, c_inf=1.0):
+                 fourier_B=None, y_inf=None, c_inf=1.0, norm_field=None, norm_deriv=None):
         lib()
         self.device = torch.device(device)
         self.equation = int(equation)
@@ -212,6 +214,11 @@ class GNProblem:
         p.n_inf = self.n_inf
         p.y_inf = self.y_inf.data_ptr() if self.y_inf is not None else None
         p.c_inf = float(c_inf)
+        # normalisation constraint: the equation's own unless a field or derivative is given
+        if norm_field is not None or norm_deriv is not None:
+            deriv = (self.equation == _inputs.BOUSSINESQ) if norm_deriv is None else bool(norm_deriv)
+            p.norm_kind = 2 if deriv else 1
+            p.norm_field = 0 if norm_field is None else int(norm_field)
         if fourier_B is not None:
             # host copy kept alive for gn_init (which copies it)
             self._fourier_B = np.ascontiguousarray(np.asarray(fourier_B, dtype=np.float64))
@@ -233,6 +240,8 @@ class GNProblem:
     def from_workload(cls, w, **kw):
         kw.setdefault("y_inf", getattr(w, "y_inf", None))
         kw.setdefault("c_inf", getattr(w, "c_inf", 1.0))
+        kw.setdefault("norm_field", getattr(w, "norm_field", None))
+        kw.setdefault("norm_deriv", getattr(w, "norm_deriv", None))
         return cls(w.equation, w.widths, w.y, w.y_bnd if w.y_bnd.size else None, w.rho, y_norm=w.y_norm,
                    c_norm=w.c_norm, hilbert_m=w.hilbert_m, **kw)
 

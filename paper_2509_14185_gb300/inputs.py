@@ -115,6 +115,8 @@ class Workload:
     rho: Optional[np.ndarray] = None
     y_inf: Optional[np.ndarray] = None   # (d, n_inf) decay points of the data loss, or None
     c_inf: float = 1.0
+    norm_field: Optional[int] = None     # normalisation on another field / on d/dy1 (None: the
+    norm_deriv: Optional[int] = None     # equation's own constraint)
 
     @property
     def d(self) -> int:

@@ -122,3 +122,27 @@ def test_decay_rows_graph_step_equals_eager():
     np.testing.assert_array_equal(host(tg), host(te))
     pe.close()
     pg.close()
+
+
+@pytest.mark.parametrize("name,field,deriv", [("burgers", 0, 1), ("ipm", 1, 0), ("ipm", 1, 1),
+                                              ("boussinesq", 2, 0), ("boussinesq", 1, 1)])
+def test_normalisation_on_another_field_or_derivative(name, field, deriv):
+    """The normalisation row on any field, value or d/dy1 (Methods, "Training Loss"); the decay
+    rows follow that field: rows, Jacobian columns and the adjoint vs the oracle."""
+    w = with_decay(name, seed=7)
+    w.norm_field, w.norm_deriv = field, deriv
+    p = oracle_problem(w)
+    assert p.norm_field == field and p.norm_deriv == deriv
+    r_o = p.rows(w.theta, w.lam)
+    J_o = ogn.jacobian(p, w.theta, w.lam)
+    prob = gpu_problem(w)
+    th = dev(w.theta)
+    r, _ = prob.residual(th, w.lam)
+    assert rel(host(r), r_o) <= TOL
+    assert abs(host(r)[-1] - r_o[-1]) <= TOL * max(abs(r_o[-1]), np.max(np.abs(r_o)))
+    J = host(prob.jacobian(th, w.lam))
+    assert rel(J, J_o) <= TOL
+    assert rel(J[-1], J_o[-1]) <= TOL
+    g = host(prob.gradient(th, w.lam))
+    assert rel(g, J_o.T @ r_o) <= TOL
+    prob.close()
