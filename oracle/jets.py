@@ -102,6 +102,10 @@ class Jet:
         t1 = 1.0 - t * t
         return self.chain(t, t1, -2.0 * t * t1)
 
+    def exp(self):
+        e = np.exp(self.v)
+        return self.chain(e, e, e)
+
     def cos(self):
         c, sn = np.cos(self.v), np.sin(self.v)
         return self.chain(c, -sn, -c)

@@ -109,7 +109,7 @@ class Problem:
 
     def __init__(self, equation, widths, y, y_bnd=None, rho=None, c_bnd=1.0,
                  y_norm=(1.0, 0.0), c_norm=1.0, c_norm_w=1.0, hilbert_m=1024, stage1=None, fourier=None,
-                 y_inf=None, c_inf=1.0, norm_field=None, norm_deriv=None):
+                 y_inf=None, c_inf=1.0, norm_field=None, norm_deriv=None, output_map=0):
         self.eq = int(equation)
         self.widths = list(widths)
         self.d = DIM[self.eq]
@@ -140,6 +140,11 @@ class Problem:
         self.c_inf = float(c_inf)
         self.M = int(hilbert_m)
         self.ne = N_EQ[self.eq]
+        # last activation of the network (Methods, "Solution Modeling": exponential or
+        # exponential-adjacent): 0 linear (the default reading), 1 exp; a stage-1 network of a
+        # stage-2 problem uses the same map
+        self.output_map = int(output_map)
+        assert self.output_map in (0, 1)
         # Fourier-feature network (Methods, "Multi-stage Training", item 2): fourier = B, an
         # (m' x m) array drawn by the caller; the layer after the linear input layer (widths[1]
         # = m) is the fixed map x -> [cos(B x), sin(B x)] (widths[2] = 2 m'), not trained.
@@ -179,14 +184,15 @@ class Problem:
         return out
 
     def mlp(self, theta, z, widths=None, fourier=None):
-        """tanh MLP with linear last layer applied to the input jet z (components (d_in, n)).
-        With a Fourier layer: linear input layer (no activation), then [cos(B x), sin(B x)]."""
+        """tanh MLP with a linear (or, with output_map = 1, exponential) last layer applied to
+        the input jet z (components (d_in, n)).  With a Fourier layer: linear input layer (no
+        activation), then [cos(B x), sin(B x)]."""
         h = z
         L = self.layers(theta, widths, fourier)
         for i, (W, b) in enumerate(L):
             a = h.matvec(W, b)
             if i == len(L) - 1:
-                h = a
+                h = a.exp() if self.output_map == 1 else a
             elif fourier is not None and i == 0:
                 h = a
             elif fourier is not None and i == 1:
