@@ -129,6 +129,10 @@ typedef struct gn_problem {
                                 Boussinesq d Omega / d y1), 1 the value of field norm_field,
                                 2 its d/dy1.  The decay rows take the value of the same field. */
   int norm_field;            /* field A0 for norm_kind 1 and 2 (0 .. fields - 1) */
+  int output_map;            /* last activation of the network (Methods, "Solution Modeling":
+                                exponential or exponential-adjacent): 0 linear (default), 1 exp,
+                                NN_A = exp(W_L h + b_L); a stage-1 network (gn_set_stage1) uses
+                                the same map */
 } gn_problem;
 
 /* Normalisation row (data loss) per equation, fixed by the library:

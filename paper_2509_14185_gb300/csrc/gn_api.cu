@@ -56,6 +56,7 @@ int validate(const gn_problem* p) {
   if (p->n_bnd < 0 || (p->n_bnd > 0 && !p->y_bnd)) return GN_ERR_INVALID;
   if (p->n_inf < 0 || (p->n_inf > 0 && !p->y_inf) || !(p->c_inf >= 0.0)) return GN_ERR_INVALID;
   if (p->norm_kind < 0 || p->norm_kind > 2) return GN_ERR_INVALID;
+  if (p->output_map < 0 || p->output_map > 1) return GN_ERR_INVALID;
   if (p->norm_kind > 0 && (p->norm_field < 0 || p->norm_field >= fields_of(p->equation))) return GN_ERR_INVALID;
   if (p->equation == GN_CCF) {
     if (p->hilbert_m < 8 || p->hilbert_m > 16384 || (p->hilbert_m & 1)) return GN_ERR_INVALID;
@@ -421,6 +422,7 @@ int gn_init(const gn_problem* p, void* cuda_stream, gn_handle** out) {
     if (net.w[l] > net.maxw) net.maxw = net.w[l];
   }
   net.fourier = p->fourier_m > 0 ? 1 : 0;
+  net.exp_out = p->output_map == 1 ? 1 : 0;
   for (int l = 0; l < net.L; l++) {
     net.offT[l] = offT;
     offT += (int64_t)net.w[l] * net.w[l + 1];

@@ -52,6 +52,7 @@ struct NetDesc {
   int fourier;                      // 1: layer 0 is linear (no activation) and layer 1 the fixed
                                     // Fourier map [cos(B x), sin(B x)] (not in theta; its rows
                                     // are [B; B], its transposed copy sits at offT[1] in wt)
+  int exp_out;                      // 1: the outputs are exp of the last layer (else linear)
 };
 
 // Arguments of one jet-kernel launch (one point kind).

@@ -132,19 +132,74 @@ template <int D> __device__ YJ<D> envelope(const double* y, double u, int m, Dl 
   return ymul<D>(Y, Wj);
 }
 
+// Exponential output map on one field's jet components a[0 .. CF) (value, q, (b,) the second
+// orders, the q-direction third orders the lambda column needs): N = exp(a) by the chain rule,
+// every component exp(a_v) times the complete Bell polynomial of the a-derivatives.
+template <int D, int CF>
+__device__ __forceinline__ void exp_jet(const double* a, double* N) {
+  const double E = exp(a[0]);
+  N[0] = E;
+  if constexpr (D == 1) {
+    N[1] = E * a[1];
+    if constexpr (CF > 2) N[2] = E * (a[2] + a[1] * a[1]);
+  } else {
+    const double q = a[1], b = a[2];
+    N[1] = E * q;
+    N[2] = E * b;
+    N[3] = E * (a[3] + q * q);
+    N[4] = E * (a[4] + q * b);
+    N[5] = E * (a[5] + b * b);
+    if constexpr (CF > 6) {
+      N[6] = E * (a[6] + 3.0 * q * a[3] + q * q * q);
+      N[7] = E * (a[7] + b * a[3] + 2.0 * q * a[4] + q * q * b);
+      N[8] = E * (a[8] + q * a[5] + 2.0 * b * a[4] + q * b * b);
+    }
+  }
+}
+
+// Its adjoint on the components the reverse pass carries (c < C_R): nb holds dN-bar on entry
+// and the pre-activation adjoints a-bar_c = sum_k N-bar_k dN_k / da_c on exit.
+template <int D>
+__device__ __forceinline__ void exp_jet_adjoint(const double* a, double* nb) {
+  const double E = exp(a[0]);
+  if constexpr (D == 1) {
+    const double a0 = nb[0] * E + nb[1] * (E * a[1]);
+    nb[1] = nb[1] * E;
+    nb[0] = a0;
+  } else {
+    const double q = a[1], b = a[2];
+    const double N[6] = {E, E * q, E * b, E * (a[3] + q * q), E * (a[4] + q * b), E * (a[5] + b * b)};
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 6; c++) s = fma(nb[c], N[c], s);
+    const double a1 = E * (nb[1] + 2.0 * q * nb[3] + b * nb[4]);
+    const double a2 = E * (nb[2] + q * nb[4] + 2.0 * b * nb[5]);
+    nb[0] = s;
+    nb[1] = a1;
+    nb[2] = a2;
+    nb[3] *= E;
+    nb[4] *= E;
+    nb[5] *= E;
+  }
+}
+
 // Per-warp shared-memory layout (doubles).  H[j][c][ldw] for c < C_R: j = 0 network
 // input, j = 1..L-1 outputs of hidden layers (the reverse pass reads them); the forward-only
 // components c >= C_R (the third order the lambda column needs) of layer j live in a
 // two-layer ping-pong X[j & 1][c - C_R][ldw]; AS[l][c-1][ldw] derivative components of
-// hidden pre-activations; BA, BB [C_R][ldw] adjoint ping-pong; NN [NF][CF].
+// hidden pre-activations; BA, BB [C_R][ldw] adjoint ping-pong; NN [NF][CF]; with the exponential
+// output map NA [NF][CF], the last layer's own jets.
 __host__ __device__ inline int64_t jet_smem_doubles(const NetDesc& net, int CF, int CR, int NF) {
   const int64_t ldw = net.maxw;
   return (int64_t)net.L * CR * ldw + 2 * (int64_t)(CF - CR) * ldw + (int64_t)(net.L - 1) * (CR - 1) * ldw +
-         2 * (int64_t)CR * ldw + (int64_t)NF * CF + 2;
+         2 * (int64_t)CR * ldw + (int64_t)NF * CF + (net.exp_out ? (int64_t)NF * CF : 0) + 2;
 }
 
-template <int EQ, int MODE>
-__global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
+// XO: the exponential output map (a separate instantiation, so the linear map's kernels carry
+// none of its registers).  Occupancy is set by the per-warp shared memory: two blocks of eight
+// warps per SM in 1D, one block in 2D, which the register budget states (<= 128 / 255).
+template <int EQ, int MODE, bool XO>
+__global__ void __launch_bounds__(256, Eq<EQ>::D == 1 ? 2 : 1) jet_kernel(const JetArgs A) {
   constexpr int D = Eq<EQ>::D, NF = Eq<EQ>::NF, NE = Eq<EQ>::NE;
   constexpr int CR = JT<D>::CR;
   constexpr int CF = (MODE == MODE_RESIDUAL) ? CR : JT<D>::CF;
@@ -166,6 +221,7 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
   double* BA = AS + (int64_t)(L - 1) * (CR - 1) * ldw;
   double* BB = BA + CR * ldw;
   double* NN = BB + CR * ldw;
+  double* NA = NN + NF * CF;   // the last layer's own jets under the exponential output map
 
   const int kind = A.kind;
   const int nrow = (kind == KIND_INTERIOR) ? NE : 1;
@@ -267,6 +323,17 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
 #pragma unroll
           for (int c = 0; c < CF; c++) NN[o * CF + c] = acc[c];
         }
+      }
+      __syncwarp();
+    }
+
+    // exponential output map: NN becomes exp of the last layer's jets, which NA keeps for the
+    // reverse pass
+    if constexpr (XO) {
+      if (lane < NF) {
+#pragma unroll
+        for (int c = 0; c < CF; c++) NA[lane * CF + c] = NN[lane * CF + c];
+        exp_jet<D, CF>(NA + lane * CF, NN + lane * CF);
       }
       __syncwarp();
     }
@@ -487,6 +554,17 @@ __global__ void __launch_bounds__(256) jet_kernel(const JetArgs A) {
         BA[c * ldw + f] = sd;
       }
       __syncwarp();
+      if constexpr (XO) {   // through the output map to the last layer's own jets
+        if (lane < NF) {
+          double nb[CR];
+#pragma unroll
+          for (int c = 0; c < CR; c++) nb[c] = BA[c * ldw + lane];
+          exp_jet_adjoint<D>(NA + lane * CF, nb);
+#pragma unroll
+          for (int c = 0; c < CR; c++) BA[c * ldw + lane] = nb[c];
+        }
+        __syncwarp();
+      }
       double* ab = BA;
       double* hb = BB;
       for (int l = L - 1; l >= 0; l--) {
@@ -586,7 +664,7 @@ __global__ void gpart_reduce_kernel(const double* __restrict__ gpart, int64_t wa
   }
 }
 
-template <int EQ, int MODE>
+template <int EQ, int MODE, bool XO>
 cudaError_t launch_eq(const JetArgs& a, cudaStream_t st, int64_t* warps_used) {
   constexpr int D = Eq<EQ>::D, NF = Eq<EQ>::NF;
   constexpr int CR = JT<D>::CR;
@@ -599,7 +677,7 @@ cudaError_t launch_eq(const JetArgs& a, cudaStream_t st, int64_t* warps_used) {
   const size_t smem = (size_t)per_warp * wpb;
   // the opt-in limit is the same for every launch: handles stepped from several host
   // threads must not lower it under one another's launches
-  cudaError_t err = cudaFuncSetAttribute(jet_kernel<EQ, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t err = cudaFuncSetAttribute(jet_kernel<EQ, MODE, XO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmemCap);
   if (err != cudaSuccess) return err;
   int64_t blocks = (a.n + wpb - 1) / wpb;
@@ -608,18 +686,23 @@ cudaError_t launch_eq(const JetArgs& a, cudaStream_t st, int64_t* warps_used) {
   if (blocks < 1) blocks = 1;
   if (warps_used) *warps_used = blocks * wpb;
   if (a.n == 0) return cudaSuccess;
-  jet_kernel<EQ, MODE><<<(unsigned)blocks, wpb * 32, smem, st>>>(a);
+  jet_kernel<EQ, MODE, XO><<<(unsigned)blocks, wpb * 32, smem, st>>>(a);
   count_launch();
   return cudaGetLastError();
 }
 
+template <int EQ, bool XO>
+cudaError_t launch_map(const JetArgs& a, cudaStream_t st, int64_t* w) {
+  switch (a.mode) {
+    case MODE_RESIDUAL: return launch_eq<EQ, MODE_RESIDUAL, XO>(a, st, w);
+    case MODE_JACOBIAN: return launch_eq<EQ, MODE_JACOBIAN, XO>(a, st, w);
+    default: return launch_eq<EQ, MODE_GRADIENT, XO>(a, st, w);
+  }
+}
+
 template <int EQ>
 cudaError_t launch_mode(const JetArgs& a, cudaStream_t st, int64_t* w) {
-  switch (a.mode) {
-    case MODE_RESIDUAL: return launch_eq<EQ, MODE_RESIDUAL>(a, st, w);
-    case MODE_JACOBIAN: return launch_eq<EQ, MODE_JACOBIAN>(a, st, w);
-    default: return launch_eq<EQ, MODE_GRADIENT>(a, st, w);
-  }
+  return a.net.exp_out ? launch_map<EQ, true>(a, st, w) : launch_map<EQ, false>(a, st, w);
 }
 
 }  // namespace

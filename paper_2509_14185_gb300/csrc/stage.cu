@@ -42,6 +42,7 @@ int gn_set_stage1(gn_handle* h, int n_layers1, const int* widths1, const double*
   NetDesc net1;
   memset(&net1, 0, sizeof(net1));
   net1.L = n_layers1;
+  net1.exp_out = h->net.exp_out;   // stage 1 was trained with the handle's output map
   net1.maxw = 2;
   for (int l = 0; l <= n_layers1; l++) {
     net1.w[l] = widths1[l];

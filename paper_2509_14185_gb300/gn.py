@@ -61,6 +61,7 @@ class gn_problem(ctypes.Structure):
         ("c_inf", ctypes.c_double),
         ("norm_kind", ctypes.c_int),
         ("norm_field", ctypes.c_int),
+        ("output_map", ctypes.c_int),
     ]
 
 
@@ -177,7 +178,7 @@ class GNProblem:
 
     def __init__(self, equation, widths, y, y_bnd=None, rho=None, c_bnd=1.0, y_norm=(1.0, 0.0), c_norm=1.0,
                  c_norm_w=1.0, hilbert_m=1024, precision=GN_PREC_FP64, n_slices=4, device="cuda", stream=None,
-                 fourier_B=None, y_inf=None, c_inf=1.0, norm_field=None, norm_deriv=None):
+                 fourier_B=None, y_inf=None, c_inf=1.0, norm_field=None, norm_deriv=None, output_map=0):
         lib()
         self.device = torch.device(device)
         self.equation = int(equation)
@@ -214,6 +215,7 @@ class GNProblem:
         p.n_inf = self.n_inf
         p.y_inf = self.y_inf.data_ptr() if self.y_inf is not None else None
         p.c_inf = float(c_inf)
+        p.output_map = int(output_map)   # 0 linear, 1 exp
         # normalisation constraint: the equation's own unless a field or derivative is given
         if norm_field is not None or norm_deriv is not None:
             deriv = (self.equation == _inputs.BOUSSINESQ) if norm_deriv is None else bool(norm_deriv)
@@ -242,6 +244,7 @@ class GNProblem:
         kw.setdefault("c_inf", getattr(w, "c_inf", 1.0))
         kw.setdefault("norm_field", getattr(w, "norm_field", None))
         kw.setdefault("norm_deriv", getattr(w, "norm_deriv", None))
+        kw.setdefault("output_map", getattr(w, "output_map", 0))
         return cls(w.equation, w.widths, w.y, w.y_bnd if w.y_bnd.size else None, w.rho, y_norm=w.y_norm,
                    c_norm=w.c_norm, hilbert_m=w.hilbert_m, **kw)
 

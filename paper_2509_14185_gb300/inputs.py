@@ -117,6 +117,7 @@ class Workload:
     c_inf: float = 1.0
     norm_field: Optional[int] = None     # normalisation on another field / on d/dy1 (None: the
     norm_deriv: Optional[int] = None     # equation's own constraint)
+    output_map: int = 0                  # last activation: 0 linear, 1 exp
 
     @property
     def d(self) -> int:

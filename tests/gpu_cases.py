@@ -20,7 +20,8 @@ def oracle_problem(w):
     return Pb.Problem(w.equation, w.widths, w.y, w.y_bnd if w.y_bnd.size else None, w.rho,
                       y_norm=w.y_norm, c_norm=w.c_norm, hilbert_m=w.hilbert_m,
                       y_inf=getattr(w, "y_inf", None), c_inf=getattr(w, "c_inf", 1.0),
-                      norm_field=getattr(w, "norm_field", None), norm_deriv=getattr(w, "norm_deriv", None))
+                      norm_field=getattr(w, "norm_field", None), norm_deriv=getattr(w, "norm_deriv", None),
+                      output_map=getattr(w, "output_map", 0))
 
 
 def gpu_problem(w, **kw):
