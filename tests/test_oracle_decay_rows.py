@@ -153,3 +153,41 @@ def test_normalisation_derivative_is_d_dy1_of_the_value(eq, widths, f):
     # and the defaults are the equation's own constraint (Boussinesq: d1 Omega; others: the value)
     p0 = Pb.Problem(eq, widths, w.y, w.y_bnd, y_norm=yn)
     assert p0.norm_field == 0 and p0.norm_deriv == (1 if eq == Pb.BOUSSINESQ else 0)
+
+
+# planted mistakes (on the CPU only): each pin above must fail when the oracle is wrong
+
+def test_planted_wrong_field_breaks_decay_pin(monkeypatch):
+    """Decay rows built from field 1 instead of the constrained field 0."""
+    def wrong(self, theta, lam):
+        return self.fields(theta, lam, self.y_inf)[min(1, N_FIELDS_OF[self.eq] - 1)].v
+    monkeypatch.setattr(Pb.Problem, "inf_values", wrong)
+    with pytest.raises(AssertionError):
+        test_decay_rows_of_constant_network(Pb.IPM, [2, 5, 2])
+
+
+def test_planted_missing_weight_breaks_decay_pin(monkeypatch):
+    """The decay rows without their sqrt(2 c_inf) weight (rows of c_inf / 2 times the loss)."""
+    orig = Pb.Problem.rows
+
+    def wrong(self, theta, lam):
+        r = orig(self, theta, lam).copy()
+        lo = self.n * self.ne + self.nb
+        r[lo:lo + self.ninf] /= np.sqrt(2.0 * self.c_inf)
+        return r
+    monkeypatch.setattr(Pb.Problem, "rows", wrong)
+    with pytest.raises(AssertionError):
+        test_decay_rows_of_constant_network(Pb.BURGERS, [1, 5, 1])
+
+
+def test_planted_value_for_derivative_breaks_normalisation_pin(monkeypatch):
+    """A normalisation row that ignores norm_deriv (always the value)."""
+    def wrong(self, theta, lam):
+        ys = np.array(self.y_norm[:self.d], dtype=np.float64).reshape(self.d, 1)
+        return self.fields(theta, lam, ys)[self.norm_field].v[0]
+    monkeypatch.setattr(Pb.Problem, "norm_value", wrong)
+    with pytest.raises(AssertionError):
+        test_normalisation_derivative_is_d_dy1_of_the_value(Pb.IPM, [2, 6, 2], 1)
+
+
+N_FIELDS_OF = {Pb.BURGERS: 1, Pb.CCF: 1, Pb.IPM: 2, Pb.BOUSSINESQ: 3}

@@ -83,3 +83,35 @@ def test_exp_field_jets_vs_complex_step(eq, widths):
             for f in range(widths[-1]):
                 fd = (out[0][f] - out[1][f]) / (2 * e)
                 np.testing.assert_allclose(F[f].h[i][j], fd, rtol=1e-6, atol=1e-8 * np.max(np.abs(fd)))
+
+
+# planted mistakes (on the CPU only): each pin above must fail when the oracle is wrong
+
+def test_planted_wrong_second_derivative_breaks_jet_pin(monkeypatch):
+    """exp with its second derivative dropped (the chain rule's f'' term set to 0)."""
+    from oracle.jets import Jet
+
+    def wrong(self):
+        e = np.exp(self.v)
+        return self.chain(e, e, 0.0 * e)
+    monkeypatch.setattr(Jet, "exp", wrong)
+    with pytest.raises(AssertionError):
+        test_exp_field_jets_vs_complex_step(Pb.BOUSSINESQ, [2, 6, 6, 3])
+
+
+def test_planted_exp_on_hidden_layer_breaks_two_path_pin(monkeypatch):
+    """exp applied before the last linear layer instead of after it."""
+    orig = Pb.Problem.mlp
+
+    def wrong(self, theta, z, widths=None, fourier=None):
+        if self.output_map != 1:
+            return orig(self, theta, z, widths, fourier)
+        h = z
+        L = self.layers(theta, widths, fourier)
+        for i, (W, b) in enumerate(L):
+            a = h.matvec(W, b)
+            h = a if i == len(L) - 1 else (a.tanh().exp() if i == len(L) - 2 else a.tanh())
+        return h
+    monkeypatch.setattr(Pb.Problem, "mlp", wrong)
+    with pytest.raises(AssertionError):
+        test_exp_field_is_exp_of_linear_network(Pb.IPM, [2, 5, 2])
