@@ -699,6 +699,14 @@ def micro_chol(args):
     return 0
 
 
+def step_iqr(per):
+    """Interquartile range of per-step times (0 for fewer than four steps)."""
+    if len(per) < 4:
+        return 0.0
+    q = statistics.quantiles(per, n=4)
+    return q[2] - q[0]
+
+
 def measured_peak(key, default):
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -991,16 +999,19 @@ def main():
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
     if flush is None:
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        for _ in range(args.steps):
+        # one event between consecutive steps (each step synchronises anyway): the mean over the
+        # timed region, plus the per-step median and interquartile range
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        evs[0].record(stream)
+        for k in range(args.steps):
             rc, lam, gam, info = gn_step(theta, lam, gam)
+            evs[k + 1].record(stream)
             if rc < 0:
                 raise RuntimeError(f"gn_step failed: {rc}")
             infos.append(info)
-        ev1.record(stream)
         torch.cuda.synchronize()
-        ms = ev0.elapsed_time(ev1) / args.steps
+        ms = evs[0].elapsed_time(evs[-1]) / args.steps
+        per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
         launches = L.gn_kernel_launches() - launches0
     else:
         per = []
@@ -1079,7 +1090,8 @@ def main():
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": ms, "ms_step_median": statistics.median(per),
+                "ms_step_iqr": step_iqr(per), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": dict(workload_config(w, args.precision, args.slices),
                                **({"l2": "L2 flushed (256 MB write) between timed steps"} if flush is not None
