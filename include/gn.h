@@ -133,6 +133,9 @@ typedef struct gn_problem {
                                 exponential or exponential-adjacent): 0 linear (default), 1 exp,
                                 NN_A = exp(W_L h + b_L); a stage-1 network (gn_set_stage1) uses
                                 the same map */
+  int64_t row_block;         /* rows per Jacobian block of a step (0: automatic, the whole J~ when
+                                it fits 32 GiB, else the largest block that does); smaller blocks
+                                stream J~ through a smaller buffer, the Gram accumulating over them */
 } gn_problem;
 
 /* Normalisation row (data loss) per equation, fixed by the library:

@@ -57,6 +57,7 @@ int validate(const gn_problem* p) {
   if (p->n_inf < 0 || (p->n_inf > 0 && !p->y_inf) || !(p->c_inf >= 0.0)) return GN_ERR_INVALID;
   if (p->norm_kind < 0 || p->norm_kind > 2) return GN_ERR_INVALID;
   if (p->output_map < 0 || p->output_map > 1) return GN_ERR_INVALID;
+  if (p->row_block < 0) return GN_ERR_INVALID;
   if (p->norm_kind > 0 && (p->norm_field < 0 || p->norm_field >= fields_of(p->equation))) return GN_ERR_INVALID;
   if (p->equation == GN_CCF) {
     if (p->hilbert_m < 8 || p->hilbert_m > 16384 || (p->hilbert_m & 1)) return GN_ERR_INVALID;
@@ -444,6 +445,7 @@ int gn_init(const gn_problem* p, void* cuda_stream, gn_handle** out) {
   const double jbytes = (double)h->n_rows * h->ldJ * 8.0;
   const double jcap = 32.0 * (1ull << 30);
   h->jrows = jbytes <= jcap ? h->n_rows : (int64_t)(jcap / (h->ldJ * 8.0));
+  if (p->row_block > 0 && p->row_block < h->jrows) h->jrows = p->row_block;   // the caller's block
   h->precision = p->precision;
   h->n_slices = p->n_slices > 0 ? p->n_slices : 4;
   h->gpart_warps = jet_gpart_warps(net, h->d, h->nf, p->n_pts);

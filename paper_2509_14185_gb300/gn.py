@@ -62,6 +62,7 @@ class gn_problem(ctypes.Structure):
         ("norm_kind", ctypes.c_int),
         ("norm_field", ctypes.c_int),
         ("output_map", ctypes.c_int),
+        ("row_block", ctypes.c_int64),
     ]
 
 
@@ -178,7 +179,8 @@ class GNProblem:
 
     def __init__(self, equation, widths, y, y_bnd=None, rho=None, c_bnd=1.0, y_norm=(1.0, 0.0), c_norm=1.0,
                  c_norm_w=1.0, hilbert_m=1024, precision=GN_PREC_FP64, n_slices=4, device="cuda", stream=None,
-                 fourier_B=None, y_inf=None, c_inf=1.0, norm_field=None, norm_deriv=None, output_map=0):
+                 fourier_B=None, y_inf=None, c_inf=1.0, norm_field=None, norm_deriv=None, output_map=0,
+                 row_block=0):
         lib()
         self.device = torch.device(device)
         self.equation = int(equation)
@@ -216,6 +218,7 @@ class GNProblem:
         p.y_inf = self.y_inf.data_ptr() if self.y_inf is not None else None
         p.c_inf = float(c_inf)
         p.output_map = int(output_map)   # 0 linear, 1 exp
+        p.row_block = int(row_block)     # 0: automatic
         # normalisation constraint: the equation's own unless a field or derivative is given
         if norm_field is not None or norm_deriv is not None:
             deriv = (self.equation == _inputs.BOUSSINESQ) if norm_deriv is None else bool(norm_deriv)
