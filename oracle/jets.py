@@ -114,6 +114,9 @@ class Jet:
         c, sn = np.cos(self.v), np.sin(self.v)
         return self.chain(sn, c, -sn)
 
+    def ones_like(self):
+        return Jet.const(np.ones_like(self.v), self.d)
+
     @staticmethod
     def vconcat(a, b):
         """Rows of a on top of rows of b (components (rows, n))."""

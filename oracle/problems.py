@@ -41,6 +41,7 @@ import numpy as np
 
 from . import hilbert
 from .jets import Jet
+from .taylor import Taylor
 
 BURGERS, CCF, IPM, BOUSSINESQ = 0, 1, 2, 3
 DIM = {BURGERS: 1, CCF: 1, IPM: 2, BOUSSINESQ: 2}
@@ -96,7 +97,7 @@ def _prefactor(kind, ys, u):
     if kind == "odd":
         return y1 / u.sqrt()
     if kind == "even":
-        return Jet.const(np.ones_like(y1.v), y1.d)
+        return y1.ones_like()
     if kind == "ccf":
         return (y1 * y1) / u
     if kind == "g":
@@ -109,7 +110,8 @@ class Problem:
 
     def __init__(self, equation, widths, y, y_bnd=None, rho=None, c_bnd=1.0,
                  y_norm=(1.0, 0.0), c_norm=1.0, c_norm_w=1.0, hilbert_m=1024, stage1=None, fourier=None,
-                 y_inf=None, c_inf=1.0, norm_field=None, norm_deriv=None, output_map=0):
+                 y_inf=None, c_inf=1.0, norm_field=None, norm_deriv=None, output_map=0,
+                 y_d1=None, rho_d1=None, c_d1=1.0, y_d2=None, rho_d2=None, c_d2=1.0):
         self.eq = int(equation)
         self.widths = list(widths)
         self.d = DIM[self.eq]
@@ -138,6 +140,14 @@ class Problem:
                       else np.asarray(y_inf, dtype=np.float64).reshape(self.d, -1))
         self.ninf = self.y_inf.shape[1]
         self.c_inf = float(c_inf)
+        # derivative losses (Methods, "Training Loss", d1 and d2): batches Y1, Y2 with per-point
+        # weights rho and loss coefficients c_d1, c_d2
+        self.y_d1 = np.zeros((self.d, 0)) if y_d1 is None else np.asarray(y_d1, np.float64).reshape(self.d, -1)
+        self.y_d2 = np.zeros((self.d, 0)) if y_d2 is None else np.asarray(y_d2, np.float64).reshape(self.d, -1)
+        self.n_d1, self.n_d2 = self.y_d1.shape[1], self.y_d2.shape[1]
+        self.rho_d1 = np.ones(self.n_d1) if rho_d1 is None else np.asarray(rho_d1, np.float64)
+        self.rho_d2 = np.ones(self.n_d2) if rho_d2 is None else np.asarray(rho_d2, np.float64)
+        self.c_d1, self.c_d2 = float(c_d1), float(c_d2)
         self.M = int(hilbert_m)
         self.ne = N_EQ[self.eq]
         # last activation of the network (Methods, "Solution Modeling": exponential or
@@ -153,7 +163,8 @@ class Problem:
             assert self.fourier.shape == (self.widths[2] // 2, self.widths[1]) and self.widths[2] % 2 == 0
         self.P = sum(self.widths[i] * self.widths[i + 1] + self.widths[i + 1]
                      for i in range(len(self.widths) - 1) if not (self.fourier is not None and i == 1))
-        self.n_rows = self.n * self.ne + self.nb + self.ninf + 1
+        self.n_rows = (self.n * self.ne + self.n_d1 * self.ne * self.d + self.n_d2 * self.ne * self.d ** 2
+                       + self.nb + self.ninf + 1)
         # Multi-stage training (Methods, "Multi-stage Training"): stage1 = (widths1, theta1, eps)
         # makes every field Phi = Phi_1 + eps Phi_2 with Phi_1 the frozen stage-1 network and
         # Phi_2 this problem's network, and divides every row by eps (the normalised stage-2
@@ -196,35 +207,41 @@ class Problem:
             elif fourier is not None and i == 0:
                 h = a
             elif fourier is not None and i == 1:
-                h = Jet.vconcat(a.cos(), a.sin())
+                h = type(a).vconcat(a.cos(), a.sin())
             else:
                 h = a.tanh()
         return h
 
     # -- ansatz -------------------------------------------------------------
-    def fields(self, theta, lam, ys, extra_g=False):
+    def fields(self, theta, lam, ys, extra_g=False, order=None):
         """Field jets Phi_A at points ys (d, n); for CCF optionally also g = Theta / y.
-        In a stage-2 problem: Phi_1 + eps Phi_2 (and g_1 + eps g_2)."""
-        out = self.network_fields(theta, lam, ys, extra_g)
+        In a stage-2 problem: Phi_1 + eps Phi_2 (and g_1 + eps g_2).  order: None for the
+        second-order Jet, else truncated Taylor series of that total order in y."""
+        out = self.network_fields(theta, lam, ys, extra_g, order=order)
         if self.stage1 is None:
             return out
         w1, th1, eps = self.stage1
-        base = self.network_fields(th1, lam, ys, extra_g, widths=w1)
+        base = self.network_fields(th1, lam, ys, extra_g, widths=w1, order=order)
         return [b + f * eps for b, f in zip(base, out)]
 
-    def network_fields(self, theta, lam, ys, extra_g=False, widths=None):
-        """The ansatz fields of one network (widths, theta) at points ys."""
+    def network_fields(self, theta, lam, ys, extra_g=False, widths=None, order=None):
+        """The ansatz fields of one network (widths, theta) at points ys (second-order jets,
+        or Taylor series of the given order in y)."""
         d = self.d
-        yj = [Jet.variable(ys[i], i, d) for i in range(d)]
-        u = Jet.const(np.ones(ys.shape[1]), d)
+        if order is None:
+            yj = [Jet.variable(ys[i], i, d) for i in range(d)]
+            u = Jet.const(np.ones(ys.shape[1]), d)
+        else:
+            yj = [Taylor.variable(ys[i], i, d, order) for i in range(d)]
+            u = Taylor.const(np.ones(ys.shape[1]), d, order, like=ys[0])
         for i in range(d):
             u = u + yj[i] * yj[i]
         q = u.pow(-1.0 / (2.0 * (1.0 + lam)))
         if d == 1:
-            z = Jet.stack([q])
+            z = type(q).stack([q])
         else:
             beta = yj[1] / u.sqrt()
-            z = Jet.stack([q, beta])
+            z = type(q).stack([q, beta])
         nn = self.mlp(theta, z, widths, self.fourier if widths is None else None)
         out = []
         for a, (kind, k) in enumerate(field_specs(self.eq, lam)):
@@ -256,6 +273,39 @@ class Problem:
                                        Psi.h[0][0], Psi.h[1][1])
         raise ValueError(self.eq)
 
+    def residual_series(self, theta, lam, ys, order):
+        """The residuals R_k at the points ys as Taylor series in y: the operators applied to
+        the fields' series of the given total order (the residuals lose one order per
+        derivative they take: one in 1D, two in 2D).  CCF is refused: its velocity is the
+        discrete Hilbert operator, whose y-derivative the paper does not define."""
+        d = self.d
+        Y = [Taylor.variable(ys[i], i, d, order) for i in range(d)]
+        if self.eq == BURGERS:
+            (U,) = self.fields(theta, lam, ys, order=order)
+            return residual_burgers(lam, Y[0], U, U.diff(0))
+        if self.eq == IPM:
+            P, Psi = self.fields(theta, lam, ys, order=order)
+            return residual_ipm(lam, Y[0], Y[1], P, P.diff(0), P.diff(1), Psi.diff(0), Psi.diff(1),
+                                Psi.diff(0).diff(0), Psi.diff(1).diff(1))
+        if self.eq == BOUSSINESQ:
+            Om, Th, Psi = self.fields(theta, lam, ys, order=order)
+            return residual_boussinesq(lam, Y[0], Y[1], Om, Om.diff(0), Om.diff(1), Th, Th.diff(0), Th.diff(1),
+                                       Psi.diff(0), Psi.diff(1), Psi.diff(0).diff(0), Psi.diff(1).diff(1))
+        raise NotImplementedError("derivative losses of CCF need the y-derivative of the discrete Hilbert "
+                                  "operator, which the paper does not define")
+
+    def d1_residuals(self, theta, lam, ys=None):
+        """d R_k / d y_i at the points: array (N_E, d, n)."""
+        ys = self.y_d1 if ys is None else ys
+        Rs = self.residual_series(theta, lam, ys, 3)
+        return np.array([[R.diff(i).v for i in range(self.d)] for R in Rs])
+
+    def d2_residuals(self, theta, lam, ys=None):
+        """d^2 R_k / d y_i d y_j at the points, every ordered pair (i, j): array (N_E, d, d, n)."""
+        ys = self.y_d2 if ys is None else ys
+        Rs = self.residual_series(theta, lam, ys, 4)
+        return np.array([[[R.diff(i).diff(j).v for j in range(self.d)] for i in range(self.d)] for R in Rs])
+
     def wall_values(self, theta, lam):
         """No-penetration on the wall y2 = 0: the stream function vanishes there."""
         if self.nb == 0:
@@ -280,14 +330,24 @@ class Problem:
 
     # -- weighted rows ------------------------------------------------------
     def rows(self, theta, lam):
-        """r~ such that h = 1/2 |r~|^2 is the paper's d0 loss plus data loss:
-        h = (1/(N N_E)) sum rho R^2 + (c_bnd/N_b) sum R_b^2 + c_inf sum_{Y_inf} Phi(y)^2
-            + c_norm_w (Phi(y_norm) - C)^2
-        (rows in that order: interior point-major, wall, decay, normalisation last)."""
+        """r~ such that h = 1/2 |r~|^2 is the paper's equation loss plus data loss:
+        h = (1/(N N_E)) sum rho R^2 + c_d1 L_d1 + c_d2 L_d2 + (c_bnd/N_b) sum R_b^2
+            + c_inf sum_{Y_inf} Phi(y)^2 + c_norm_w (Phi(y_norm) - C)^2
+        (rows in that order: interior point-major, d1, d2, wall, decay, normalisation last)."""
         R = self.interior_residuals(theta, lam)
         w = np.sqrt(2.0 * self.rho / (self.n * self.ne))
         inner = np.stack([w * Rk for Rk in R], axis=1).reshape(-1)   # point-major
         parts = [inner]
+        # derivative losses: c_d1 / (N_d1 N_E d) sum rho (d_i R_k)^2 and c_d2 / (N_d2 N_E d^2) sum
+        # rho (d_i d_j R_k)^2, rows point-major, then k, then i (and j)
+        if self.n_d1:
+            D1 = self.d1_residuals(theta, lam)                   # (ne, d, n)
+            w1 = np.sqrt(2.0 * self.c_d1 * self.rho_d1 / (self.n_d1 * self.ne * self.d))
+            parts.append((np.moveaxis(D1, -1, 0) * w1[:, None, None]).reshape(-1))
+        if self.n_d2:
+            D2 = self.d2_residuals(theta, lam)                   # (ne, d, d, n)
+            w2 = np.sqrt(2.0 * self.c_d2 * self.rho_d2 / (self.n_d2 * self.ne * self.d ** 2))
+            parts.append((np.moveaxis(D2, -1, 0) * w2[:, None, None, None]).reshape(-1))
         if self.nb:
             parts.append(np.sqrt(2.0 * self.c_bnd / self.nb) * self.wall_values(theta, lam))
         if self.ninf:

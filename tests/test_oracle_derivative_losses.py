@@ -1,0 +1,163 @@
+"""Pins for the oracle's derivative losses (Methods, "Training Loss": the d1 and d2 losses
+differentiate the residuals in y; rows sqrt(2 c rho / (N N_E d^n)) d^n R).
+
+* Closed forms: Burgers at lambda = 1/2 (U^3 + U + y = 0) and lambda = 1/4 (U^5 + U + y = 0)
+  solve R = 0 for every y, so every y-derivative of R vanishes.  U's Taylor series comes from
+  implicit differentiation (sympy), not from the network or the jet code.
+* The network path: d1 values equal the complex-step y-derivative of the d0 residual function
+  (no Taylor code involved); d2 values equal central differences of those.
+* The Taylor field series agree with the second-order Jet fields (two implementations).
+* The loss gains exactly c_d1 / (N N_E d) sum rho (d R)^2 (with d R by complex step), and
+  g = J~^T r~ stays the gradient of h (complex step of h in theta through the series).
+* CCF is refused (the discrete Hilbert operator's y-derivative is not defined).
+"""
+from math import factorial
+
+import numpy as np
+import pytest
+import sympy as sp
+
+from oracle import gn
+from oracle import problems as Pb
+from oracle.taylor import Taylor
+from paper_2509_14185_gb300 import inputs as I
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def implicit_series(power, ys, K):
+    """U(y) with U^power + U + y = 0 (the real root) as a Taylor series of order K at ys."""
+    U_, y_ = sp.symbols("U y")
+    F = U_ ** power + U_ + y_
+    Uv = np.array([np.real([r for r in np.roots([1.0] + [0.0] * (power - 2) + [1.0, y0])
+                            if abs(r.imag) < 1e-9][0]) for y0 in ys])
+    c = {(0,): Uv}
+    for n in range(1, K + 1):
+        dn = sp.lambdify([U_, y_], sp.idiff(F, U_, y_, n), "numpy")
+        c[(n,)] = np.asarray(dn(Uv, ys), dtype=np.float64) / factorial(n)
+    return Taylor(c, 1, K)
+
+
+@pytest.mark.parametrize("power,lam", [(3, 0.5), (5, 0.25)])
+def test_burgers_closed_forms_have_flat_residuals(power, lam):
+    ys = np.array([-3.0, -1.2, -0.4, 0.3, 0.9, 2.5])
+    U = implicit_series(power, ys, 4)
+    Y = Taylor.variable(ys, 0, 1, 4)
+    (R,) = Pb.residual_burgers(lam, Y, U, U.diff(0))
+    scale = np.max(np.abs(U.v)) + np.max(np.abs(ys))
+    for n, S in enumerate([R, R.diff(0), R.diff(0).diff(0)]):
+        assert np.max(np.abs(S.v)) <= 1e-13 * scale ** 2, n
+    # and a slightly wrong lambda leaves them visibly non-zero
+    (Rw,) = Pb.residual_burgers(lam + 1e-3, Y, U, U.diff(0))
+    assert np.max(np.abs(Rw.diff(0).v)) > 1e-6
+
+
+CASES = [(Pb.BURGERS, [1, 6, 6, 1]), (Pb.IPM, [2, 5, 5, 2]), (Pb.BOUSSINESQ, [2, 5, 5, 3])]
+
+
+@pytest.mark.parametrize("eq,widths", CASES)
+def test_d1_is_the_y_derivative_of_the_residual(eq, widths):
+    w = I.small_case(eq, widths, 7, n_bnd=2, m=16, seed=2)
+    p = Pb.Problem(eq, widths, w.y, w.y_bnd, hilbert_m=16, output_map=0)
+    ys = w.y
+    D1 = p.d1_residuals(w.theta, w.lam, ys)          # (ne, d, n)
+    h = 1e-30
+    for i in range(p.d):
+        yc = ys.astype(np.complex128)
+        yc[i] += 1j * h
+        Rc = p.interior_residuals(w.theta, w.lam, yc)
+        for k in range(p.ne):
+            want = Rc[k].imag / h
+            np.testing.assert_allclose(D1[k, i], want, rtol=1e-11, atol=1e-12 * np.max(np.abs(want)))
+
+
+@pytest.mark.parametrize("eq,widths", CASES)
+def test_d2_is_the_second_y_derivative(eq, widths):
+    w = I.small_case(eq, widths, 5, n_bnd=2, m=16, seed=3)
+    p = Pb.Problem(eq, widths, w.y, w.y_bnd, hilbert_m=16)
+    ys = w.y
+    D2 = p.d2_residuals(w.theta, w.lam, ys)          # (ne, d, d, n)
+    e = 1e-5
+    for j in range(p.d):
+        out = []
+        for s in (1.0, -1.0):
+            yj = ys.copy()
+            yj[j] += s * e
+            out.append(p.d1_residuals(w.theta, w.lam, yj))
+        fd = (out[0] - out[1]) / (2 * e)                # d/dy_j of d R / d y_i: (ne, d, n)
+        for k in range(p.ne):
+            for i in range(p.d):
+                np.testing.assert_allclose(D2[k, i, j], fd[k, i], rtol=1e-6, atol=1e-7 * np.max(np.abs(fd[k, i])))
+    # symmetric in (i, j)
+    if p.d == 2:
+        np.testing.assert_allclose(D2[:, 0, 1], D2[:, 1, 0], rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("eq,widths", CASES + [(Pb.CCF, [1, 5, 1])])
+def test_taylor_fields_match_the_jet_fields(eq, widths):
+    w = I.small_case(eq, widths, 6, m=16, seed=4)
+    p = Pb.Problem(eq, widths, w.y, hilbert_m=16)
+    FJ = p.fields(w.theta, w.lam, w.y)
+    FT = p.fields(w.theta, w.lam, w.y, order=2)
+    for a, b in zip(FJ, FT):
+        np.testing.assert_allclose(b.v, a.v, rtol=1e-13, atol=1e-300)
+        for i in range(p.d):
+            e_i = tuple(1 if k == i else 0 for k in range(p.d))
+            np.testing.assert_allclose(b.deriv(e_i), a.g[i], rtol=1e-12, atol=1e-13 * np.max(np.abs(a.g[i])))
+            for j in range(p.d):
+                e_ij = tuple((1 if k == i else 0) + (1 if k == j else 0) for k in range(p.d))
+                np.testing.assert_allclose(b.deriv(e_ij), a.h[i][j], rtol=1e-11,
+                                           atol=1e-12 * np.max(np.abs(a.h[i][j])))
+
+
+@pytest.mark.parametrize("eq,widths", CASES)
+def test_loss_gains_the_d1_term_and_gradient(eq, widths):
+    w = I.small_case(eq, widths, 6, n_bnd=2, m=16, seed=6)
+    y1 = w.y[:, :4] * 1.3
+    rho1 = np.array([0.5, 1.0, 2.0, 1.5])
+    p0 = Pb.Problem(eq, widths, w.y, w.y_bnd, hilbert_m=16)
+    p1 = Pb.Problem(eq, widths, w.y, w.y_bnd, hilbert_m=16, y_d1=y1, rho_d1=rho1, c_d1=0.7, y_d2=y1[:, :3], c_d2=0.2)
+    assert p1.n_rows == p0.n_rows + 4 * p1.ne * p1.d + 3 * p1.ne * p1.d ** 2
+    # d1 part of the loss from complex-step y-derivatives of the d0 residual (no Taylor code)
+    h = 1e-30
+    s1 = 0.0
+    for i in range(p1.d):
+        yc = y1.astype(np.complex128)
+        yc[i] += 1j * h
+        for Rk in p1.interior_residuals(w.theta, w.lam, yc):
+            s1 += np.sum(rho1 * (Rk.imag / h) ** 2)
+    D2 = p1.d2_residuals(w.theta, w.lam)
+    want = p0.loss(w.theta, w.lam) + 0.7 * s1 / (4 * p1.ne * p1.d) + 0.2 * np.sum(D2 ** 2) / (3 * p1.ne * p1.d ** 2)
+    assert p1.loss(w.theta, w.lam) == pytest.approx(want, rel=1e-11)
+    # g = J~^T r~ is the gradient of h with the derivative rows (complex step of h in theta)
+    J = gn.jacobian(p1, w.theta, w.lam)
+    g = J.T @ p1.rows(w.theta, w.lam)
+    x = np.concatenate([w.theta, [w.lam]]).astype(np.complex128)
+    for j in [0, p1.P // 2, p1.P]:
+        xc = x.copy()
+        xc[j] += 1j * 1e-30
+        r = p1.rows(xc[:-1], xc[-1])
+        dh = (0.5 * np.sum(r * r)).imag / 1e-30
+        assert abs(dh - g[j]) <= 1e-10 * (abs(g[j]) + 1e-3 * np.max(np.abs(g)))
+
+
+def test_ccf_derivative_losses_are_refused():
+    w = I.small_case(Pb.CCF, [1, 5, 1], 6, m=16)
+    p = Pb.Problem(Pb.CCF, [1, 5, 1], w.y, hilbert_m=16, y_d1=w.y[:, :2])
+    with pytest.raises(NotImplementedError):
+        p.rows(w.theta, w.lam)
+
+
+def test_planted_wrong_diff_factor_breaks_closed_form_pin(monkeypatch):
+    """Taylor.diff without the (a_i + 1) factor: the flat-residual pin must fail."""
+    def wrong(self, i):
+        K = self.K - 1
+        c = {}
+        from oracle.taylor import multi_indices
+        for a in multi_indices(self.d, K):
+            b = tuple(a[k] + (1 if k == i else 0) for k in range(self.d))
+            c[a] = self.c[b]
+        return Taylor(c, self.d, K)
+    monkeypatch.setattr(Taylor, "diff", wrong)
+    with pytest.raises(AssertionError):
+        test_burgers_closed_forms_have_flat_residuals(3, 0.5)
