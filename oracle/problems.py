@@ -111,7 +111,8 @@ class Problem:
     def __init__(self, equation, widths, y, y_bnd=None, rho=None, c_bnd=1.0,
                  y_norm=(1.0, 0.0), c_norm=1.0, c_norm_w=1.0, hilbert_m=1024, stage1=None, fourier=None,
                  y_inf=None, c_inf=1.0, norm_field=None, norm_deriv=None, output_map=0,
-                 y_d1=None, rho_d1=None, c_d1=1.0, y_d2=None, rho_d2=None, c_d2=1.0):
+                 y_d1=None, rho_d1=None, c_d1=1.0, y_d2=None, rho_d2=None, c_d2=1.0,
+                 y_relu=None, c_relu=1.0, relu_bound=0.0, relu_sign=1):
         self.eq = int(equation)
         self.widths = list(widths)
         self.d = DIM[self.eq]
@@ -148,6 +149,13 @@ class Problem:
         self.rho_d1 = np.ones(self.n_d1) if rho_d1 is None else np.asarray(rho_d1, np.float64)
         self.rho_d2 = np.ones(self.n_d2) if rho_d2 is None else np.asarray(rho_d2, np.float64)
         self.c_d1, self.c_d2 = float(c_d1), float(c_d2)
+        # bound constraints of the data loss (Methods, "Training Loss": a constraint acted on by
+        # a relu before squaring): relu(s (Phi_A0(y) - b)) at the points, s = +1 an upper bound
+        # b on the constrained field, s = -1 a lower bound
+        self.y_relu = np.zeros((self.d, 0)) if y_relu is None else np.asarray(y_relu, np.float64).reshape(self.d, -1)
+        self.nrelu = self.y_relu.shape[1]
+        self.c_relu, self.relu_bound, self.relu_sign = float(c_relu), float(relu_bound), int(relu_sign)
+        assert self.relu_sign in (1, -1)
         self.M = int(hilbert_m)
         self.ne = N_EQ[self.eq]
         # last activation of the network (Methods, "Solution Modeling": exponential or
@@ -164,7 +172,7 @@ class Problem:
         self.P = sum(self.widths[i] * self.widths[i + 1] + self.widths[i + 1]
                      for i in range(len(self.widths) - 1) if not (self.fourier is not None and i == 1))
         self.n_rows = (self.n * self.ne + self.n_d1 * self.ne * self.d + self.n_d2 * self.ne * self.d ** 2
-                       + self.nb + self.ninf + 1)
+                       + self.nb + self.ninf + self.nrelu + 1)
         # Multi-stage training (Methods, "Multi-stage Training"): stage1 = (widths1, theta1, eps)
         # makes every field Phi = Phi_1 + eps Phi_2 with Phi_1 the frozen stage-1 network and
         # Phi_2 this problem's network, and divides every row by eps (the normalised stage-2
@@ -319,6 +327,14 @@ class Problem:
             return np.zeros(0)
         return self.fields(theta, lam, self.y_inf)[self.norm_field].v
 
+    def relu_values(self, theta, lam):
+        """relu(s (Phi_A0(y) - b)) at the bound points; the relu decides on the real part, so a
+        complex step passes through active rows and vanishes on inactive ones."""
+        if self.nrelu == 0:
+            return np.zeros(0)
+        x = self.relu_sign * (self.fields(theta, lam, self.y_relu)[self.norm_field].v - self.relu_bound)
+        return np.where(np.real(x) > 0.0, x, 0.0 * x)
+
     def norm_value(self, theta, lam):
         """Normalisation constraint value Phi_{A0}(y_norm), or its d/dy1 (the Boussinesq
         default: d1 Omega there)."""
@@ -332,8 +348,8 @@ class Problem:
     def rows(self, theta, lam):
         """r~ such that h = 1/2 |r~|^2 is the paper's equation loss plus data loss:
         h = (1/(N N_E)) sum rho R^2 + c_d1 L_d1 + c_d2 L_d2 + (c_bnd/N_b) sum R_b^2
-            + c_inf sum_{Y_inf} Phi(y)^2 + c_norm_w (Phi(y_norm) - C)^2
-        (rows in that order: interior point-major, d1, d2, wall, decay, normalisation last)."""
+            + c_inf sum_{Y_inf} Phi(y)^2 + c_relu sum relu(s (Phi(y) - b))^2 + c_norm_w (Phi(y_norm) - C)^2
+        (rows in that order: interior point-major, d1, d2, wall, decay, bounds, normalisation last)."""
         R = self.interior_residuals(theta, lam)
         w = np.sqrt(2.0 * self.rho / (self.n * self.ne))
         inner = np.stack([w * Rk for Rk in R], axis=1).reshape(-1)   # point-major
@@ -352,6 +368,8 @@ class Problem:
             parts.append(np.sqrt(2.0 * self.c_bnd / self.nb) * self.wall_values(theta, lam))
         if self.ninf:
             parts.append(np.sqrt(2.0 * self.c_inf) * self.inf_values(theta, lam))
+        if self.nrelu:
+            parts.append(np.sqrt(2.0 * self.c_relu) * self.relu_values(theta, lam))
         parts.append(np.array([np.sqrt(2.0 * self.c_norm_w) * (self.norm_value(theta, lam) - self.c_norm)]))
         r = np.concatenate(parts)
         return r / self.stage1[2] if self.stage1 is not None else r

@@ -191,3 +191,51 @@ def test_planted_value_for_derivative_breaks_normalisation_pin(monkeypatch):
 
 
 N_FIELDS_OF = {Pb.BURGERS: 1, Pb.CCF: 1, Pb.IPM: 2, Pb.BOUSSINESQ: 3}
+
+
+# bound constraints: relu(s (Phi_A0(y) - b)) before squaring (Methods, "Training Loss")
+
+@pytest.mark.parametrize("eq,widths", CASES)
+@pytest.mark.parametrize("sign", [1, -1])
+def test_relu_bound_rows_of_constant_network(eq, widths, sign):
+    w = I.small_case(eq, widths, 6, n_bnd=2, m=16)
+    yb = far_points(w.d, 6, 5) * 0.01            # points near the origin: field values O(1)
+    b = np.array([1.3, -0.4, 0.9])[: widths[-1]]
+    lam = 0.37
+    phi = closed_form_field0(eq, yb, lam, b[0])
+    bound = float(np.median(phi))                 # half the points on each side
+    p = Pb.Problem(eq, widths, w.y, w.y_bnd, y_norm=w.y_norm, hilbert_m=16, y_inf=far_points(w.d, 2, 1),
+                   y_relu=yb, c_relu=0.8, relu_bound=bound, relu_sign=sign)
+    theta = np.zeros(p.P)
+    theta[-widths[-1]:] = b
+    r = p.rows(theta, lam)
+    lo = p.n * p.ne + p.nb + p.ninf
+    want = np.sqrt(1.6) * np.maximum(sign * (phi - bound), 0.0)
+    np.testing.assert_allclose(r[lo:lo + 6], want, rtol=1e-13, atol=1e-300)
+    assert np.sum(want > 0) >= 2 and np.sum(want == 0) >= 2
+    assert len(r) == p.n_rows and r[-1] == Pb.Problem(eq, widths, w.y, w.y_bnd, y_norm=w.y_norm,
+                                                      hilbert_m=16).rows(theta, lam)[-1]
+
+
+@pytest.mark.parametrize("eq,widths", [(Pb.BURGERS, [1, 6, 1]), (Pb.IPM, [2, 5, 2])])
+def test_relu_rows_gradient_and_inactive_rows(eq, widths):
+    w = I.small_case(eq, widths, 8, n_bnd=2, m=16, seed=2)
+    yb = far_points(w.d, 6, 9) * 0.02
+    p0 = Pb.Problem(eq, widths, w.y, w.y_bnd, y_norm=w.y_norm, hilbert_m=16, y_relu=yb)
+    vals = p0.fields(w.theta, w.lam, yb)[0].v
+    p = Pb.Problem(eq, widths, w.y, w.y_bnd, y_norm=w.y_norm, hilbert_m=16, y_relu=yb, c_relu=0.5,
+                   relu_bound=float(np.median(vals)), relu_sign=1)
+    J = gn.jacobian(p, w.theta, w.lam)
+    r = p.rows(w.theta, w.lam)
+    lo = p.n * p.ne + p.nb + p.ninf
+    inactive = r[lo:lo + 6] == 0.0
+    assert inactive.any() and (~inactive).any()
+    assert np.all(J[lo:lo + 6][inactive] == 0.0)          # no gradient through an inactive bound
+    g = J.T @ r
+    x = np.concatenate([w.theta, [w.lam]]).astype(np.complex128)
+    for j in [0, p.P // 2, p.P]:
+        xc = x.copy()
+        xc[j] += 1j * 1e-30
+        rc = p.rows(xc[:-1], xc[-1])
+        dh = (0.5 * np.sum(rc * rc)).imag / 1e-30
+        assert abs(dh - g[j]) <= 1e-11 * (abs(g[j]) + 1e-3 * np.max(np.abs(g)))
