@@ -136,6 +136,13 @@ typedef struct gn_problem {
   int64_t row_block;         /* rows per Jacobian block of a step (0: automatic, the whole J~ when
                                 it fits 32 GiB, else the largest block that does); smaller blocks
                                 stream J~ through a smaller buffer, the Gram accumulating over them */
+  int64_t n_relu;            /* bound points of the data loss (Methods, "Training Loss": a constraint
+                                acted on by a relu before squaring): rows sqrt(2 c_relu)
+                                relu(s (Phi_A0(y) - relu_bound)) after the decay rows; 0: none */
+  const double* y_relu;      /* device, SoA [d][n_relu]. Borrowed: must stay valid until gn_destroy. */
+  double c_relu;             /* weight of the bound rows */
+  double relu_bound;         /* the bound b on the constrained field */
+  int relu_sign;             /* s: >= 0 an upper bound (Phi_A0 <= b), < 0 a lower bound (Phi_A0 >= b) */
 } gn_problem;
 
 /* Normalisation row (data loss) per equation, fixed by the library:

@@ -58,6 +58,8 @@ int validate(const gn_problem* p) {
   if (p->norm_kind < 0 || p->norm_kind > 2) return GN_ERR_INVALID;
   if (p->output_map < 0 || p->output_map > 1) return GN_ERR_INVALID;
   if (p->row_block < 0) return GN_ERR_INVALID;
+  if (p->n_relu < 0 || (p->n_relu > 0 && !p->y_relu) || !(p->c_relu >= 0.0) || !std::isfinite(p->relu_bound))
+    return GN_ERR_INVALID;
   if (p->norm_kind > 0 && (p->norm_field < 0 || p->norm_field >= fields_of(p->equation))) return GN_ERR_INVALID;
   if (p->equation == GN_CCF) {
     if (p->hilbert_m < 8 || p->hilbert_m > 16384 || (p->hilbert_m & 1)) return GN_ERR_INVALID;
@@ -81,7 +83,7 @@ void free_all(gn_handle* h) {
   void* ptrs[] = {h->ema_ws, h->wt, h->theta_t, h->r, h->J, h->G, h->A, h->Linv, h->g, h->delta, h->vtmp, h->red,
                   h->flag, h->gpart, h->kf, h->dcoef, h->snode, h->gnode, h->Jg, h->ug, h->sU, h->tnode,
                   h->split_ws, h->chol_ws, h->base_int, h->base_wall, h->base_norm, h->base_node, h->fourierW,
-                  h->base_inf};
+                  h->base_inf, h->base_relu};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->hpin) cudaFreeHost(h->hpin);
@@ -167,6 +169,27 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
       b.base = h->staged ? h->base_inf : nullptr;
       b.c_norm = 0.0;
       b.row0 = n * h->ne + h->p.n_bnd;
+      b.r = ps.r;
+      b.J = ps.J;
+      b.ldJ = ps.ldJ;
+      b.jrow_lo = ps.jlo;
+      b.jrow_hi = ps.jhi;
+      b.seed = ps.seed;
+      GN_TRY_CUDA(launch_jet(b, sx, nullptr));
+    }
+    // bound rows of the data loss: sqrt(2 c_relu) relu(s (Phi_A0 - b)) at their points
+    if (h->p.n_relu > 0) {
+      JetArgs b = a;
+      b.kind = KIND_RELU;
+      b.mode = ps.mode;
+      b.n = h->p.n_relu;
+      b.y = h->p.y_relu;
+      b.ystride = h->p.n_relu;
+      b.wscale = rs * sqrt(2.0 * h->p.c_relu);
+      b.base = h->staged ? h->base_relu : nullptr;
+      b.c_norm = h->p.relu_bound;
+      b.rsign = h->p.relu_sign < 0 ? -1 : 1;
+      b.row0 = n * h->ne + h->p.n_bnd + h->p.n_inf;
       b.r = ps.r;
       b.J = ps.J;
       b.ldJ = ps.ldJ;
@@ -440,7 +463,7 @@ int gn_init(const gn_problem* p, void* cuda_stream, gn_handle** out) {
   net.P = off;
   h->P = off;
   h->Pp = off + 1;
-  h->n_rows = p->n_pts * h->ne + (h->d == 2 ? p->n_bnd : 0) + p->n_inf + 1;
+  h->n_rows = p->n_pts * h->ne + (h->d == 2 ? p->n_bnd : 0) + p->n_inf + p->n_relu + 1;
   h->ldJ = round_up(h->Pp, 16);
   const double jbytes = (double)h->n_rows * h->ldJ * 8.0;
   const double jcap = 32.0 * (1ull << 30);

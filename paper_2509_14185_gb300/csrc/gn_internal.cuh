@@ -32,7 +32,8 @@ enum PointKind : int {
   KIND_NORM = 2,      // normalisation point: one row
   KIND_NODE = 3,      // CCF Hilbert node: one row, g = Theta / y at the node
   KIND_PROBE = 4,     // field jets at a point: per field value, gradient, Hessian (2D) into r
-  KIND_INF = 5        // decay point of the data loss: one row, the value of field 0
+  KIND_INF = 5,       // decay point of the data loss: one row, the value of field 0
+  KIND_RELU = 6       // bound point of the data loss: one row, relu(s (Phi_A0 - b))
 };
 
 enum JetMode : int { MODE_RESIDUAL = 0, MODE_JACOBIAN = 1, MODE_GRADIENT = 2 };
@@ -72,6 +73,7 @@ struct JetArgs {
   double wscale;         // row weight factor (see jet.cu)
   double c_norm;         // normalisation target (KIND_NORM)
   int nfield, nderiv;    // KIND_NORM / KIND_INF: the constrained field, and d/dy1 (NORM only)
+  int rsign;             // KIND_RELU: +1 an upper bound (c_norm holds b), -1 a lower bound
   int64_t row0;          // row of point 0, first equation
   double* r;             // r~ output (may be null)
   double* J;             // Jacobian output (MODE_JACOBIAN)
@@ -172,6 +174,7 @@ struct gn_handle {
   double* base_wall = nullptr;    // [n_bnd][base_ld]
   double* base_norm = nullptr;    // [base_ld]
   double* base_inf = nullptr;     // [n_inf][base_ld]
+  double* base_relu = nullptr;    // [n_relu][base_ld]
   double* base_node = nullptr;    // [Mh] (CCF)
   double* fourierW = nullptr;     // Fourier layer rows [B; B] (2m' x m), when the network has one
 };

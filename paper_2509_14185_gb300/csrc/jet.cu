@@ -490,8 +490,9 @@ __global__ void __launch_bounds__(256, Eq<EQ>::D == 1 ? 2 : 1) jet_kernel(const 
       }
     } else if (kind == KIND_WALL) {
       R[0] = F[NF - 1].v;
-    } else if (kind == KIND_NORM || kind == KIND_INF) {
-      // normalisation: Phi_A0 or its d/dy1 minus the target; decay: Phi_A0 itself
+    } else if (kind == KIND_NORM || kind == KIND_INF || kind == KIND_RELU) {
+      // normalisation: Phi_A0 or its d/dy1 minus the target; decay: Phi_A0 itself; bound:
+      // relu(s (Phi_A0 - b)), zero (with a zero derivative) while the bound holds
       Dl val = F[0].v, dy1 = F[0].g[0];
 #pragma unroll
       for (int f = 1; f < NF; f++)   // constant register indices only
@@ -501,6 +502,10 @@ __global__ void __launch_bounds__(256, Eq<EQ>::D == 1 ? 2 : 1) jet_kernel(const 
         }
       R[0] = (kind == KIND_NORM && A.nderiv) ? dy1 : val;
       R[0].v -= A.c_norm;
+      if (kind == KIND_RELU) {
+        R[0] = (double)A.rsign * R[0];
+        if (!(R[0].v > 0.0)) R[0] = Dl{0.0, 0.0};
+      }
     } else {  // KIND_NODE (CCF): g = y/u * NN * q^{-lambda}
       const YJ<D> Eg = envelope<D>(y, u, 1, dconst(-1.0) + 0.5 * (lamd * a));
       R[0] = Eg.v * nn[0][0];

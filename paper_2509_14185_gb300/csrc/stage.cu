@@ -70,7 +70,7 @@ int gn_set_stage1(gn_handle* h, int n_layers1, const int* widths1, const double*
       return GN_NOTE(cudaMalloc((void**)p, (size_t)(count > 0 ? count : 1) * sizeof(double))) == cudaSuccess;
     };
     if (!grow(&h->base_int, h->p.n_pts * ld) || !grow(&h->base_wall, h->p.n_bnd * ld) || !grow(&h->base_norm, ld) ||
-        !grow(&h->base_inf, h->p.n_inf * ld) ||
+        !grow(&h->base_inf, h->p.n_inf * ld) || !grow(&h->base_relu, h->p.n_relu * ld) ||
         (h->eq == GN_CCF && !grow(&h->base_node, h->Mh))) {
       cudaFree(wt1);
       return GN_ERR_OOM;
@@ -110,6 +110,14 @@ int gn_set_stage1(gn_handle* h, int n_layers1, const int* widths1, const double*
       b.y = h->p.y_inf;
       b.ystride = h->p.n_inf;
       b.r = h->base_inf;
+      GN_S_TRY(launch_jet(b, st, nullptr));
+    }
+    if (h->p.n_relu > 0) {
+      JetArgs b = a;
+      b.n = h->p.n_relu;
+      b.y = h->p.y_relu;
+      b.ystride = h->p.n_relu;
+      b.r = h->base_relu;
       GN_S_TRY(launch_jet(b, st, nullptr));
     }
     {

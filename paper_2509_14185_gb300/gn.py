@@ -63,6 +63,11 @@ class gn_problem(ctypes.Structure):
         ("norm_field", ctypes.c_int),
         ("output_map", ctypes.c_int),
         ("row_block", ctypes.c_int64),
+        ("n_relu", ctypes.c_int64),
+        ("y_relu", ctypes.c_void_p),
+        ("c_relu", ctypes.c_double),
+        ("relu_bound", ctypes.c_double),
+        ("relu_sign", ctypes.c_int),
     ]
 
 
@@ -180,7 +185,7 @@ class GNProblem:
     def __init__(self, equation, widths, y, y_bnd=None, rho=None, c_bnd=1.0, y_norm=(1.0, 0.0), c_norm=1.0,
                  c_norm_w=1.0, hilbert_m=1024, precision=GN_PREC_FP64, n_slices=4, device="cuda", stream=None,
                  fourier_B=None, y_inf=None, c_inf=1.0, norm_field=None, norm_deriv=None, output_map=0,
-                 row_block=0):
+                 row_block=0, y_relu=None, c_relu=1.0, relu_bound=0.0, relu_sign=1):
         lib()
         self.device = torch.device(device)
         self.equation = int(equation)
@@ -219,6 +224,12 @@ class GNProblem:
         p.c_inf = float(c_inf)
         p.output_map = int(output_map)   # 0 linear, 1 exp
         p.row_block = int(row_block)     # 0: automatic
+        # bound points of the data loss (SoA [d][n_relu]); rows after the decay rows
+        yr = np.zeros((self.d, 0)) if y_relu is None else np.asarray(y_relu, dtype=np.float64).reshape(self.d, -1)
+        self.y_relu = torch.from_numpy(np.ascontiguousarray(yr)).to(self.device) if yr.size else None
+        p.n_relu = yr.shape[1] if yr.size else 0
+        p.y_relu = self.y_relu.data_ptr() if self.y_relu is not None else None
+        p.c_relu, p.relu_bound, p.relu_sign = float(c_relu), float(relu_bound), int(relu_sign)
         # normalisation constraint: the equation's own unless a field or derivative is given
         if norm_field is not None or norm_deriv is not None:
             deriv = (self.equation == _inputs.BOUSSINESQ) if norm_deriv is None else bool(norm_deriv)
@@ -248,6 +259,8 @@ class GNProblem:
         kw.setdefault("norm_field", getattr(w, "norm_field", None))
         kw.setdefault("norm_deriv", getattr(w, "norm_deriv", None))
         kw.setdefault("output_map", getattr(w, "output_map", 0))
+        for k, dflt in (("y_relu", None), ("c_relu", 1.0), ("relu_bound", 0.0), ("relu_sign", 1)):
+            kw.setdefault(k, getattr(w, k, dflt))
         return cls(w.equation, w.widths, w.y, w.y_bnd if w.y_bnd.size else None, w.rho, y_norm=w.y_norm,
                    c_norm=w.c_norm, hilbert_m=w.hilbert_m, **kw)
 

@@ -118,6 +118,10 @@ class Workload:
     norm_field: Optional[int] = None     # normalisation on another field / on d/dy1 (None: the
     norm_deriv: Optional[int] = None     # equation's own constraint)
     output_map: int = 0                  # last activation: 0 linear, 1 exp
+    y_relu: Optional[np.ndarray] = None  # (d, n_relu) bound points of the data loss, or None
+    c_relu: float = 1.0
+    relu_bound: float = 0.0
+    relu_sign: int = 1                   # +1 upper bound, -1 lower bound
 
     @property
     def d(self) -> int:

@@ -21,7 +21,9 @@ def oracle_problem(w):
                       y_norm=w.y_norm, c_norm=w.c_norm, hilbert_m=w.hilbert_m,
                       y_inf=getattr(w, "y_inf", None), c_inf=getattr(w, "c_inf", 1.0),
                       norm_field=getattr(w, "norm_field", None), norm_deriv=getattr(w, "norm_deriv", None),
-                      output_map=getattr(w, "output_map", 0))
+                      output_map=getattr(w, "output_map", 0), y_relu=getattr(w, "y_relu", None),
+                      c_relu=getattr(w, "c_relu", 1.0), relu_bound=getattr(w, "relu_bound", 0.0),
+                      relu_sign=getattr(w, "relu_sign", 1))
 
 
 def gpu_problem(w, **kw):

@@ -146,3 +146,33 @@ def test_normalisation_on_another_field_or_derivative(name, field, deriv):
     g = host(prob.gradient(th, w.lam))
     assert rel(g, J_o.T @ r_o) <= TOL
     prob.close()
+
+
+@pytest.mark.parametrize("name,sign", [("burgers", 1), ("ipm", -1), ("boussinesq", 1), ("ccf", -1)])
+def test_relu_bound_rows_match_oracle(name, sign):
+    """Bound rows relu(s (Phi_A0 - b)) (Methods, "Training Loss"): the bound sits between two
+    points' field values (no point at the kink), so about half the rows are active; rows,
+    Jacobian columns (zero rows where inactive) and the adjoint vs the oracle."""
+    w = with_decay(name, seed=13)
+    yb = (w.y_inf * 0.01)[:, :29]
+    vals = np.sort(oracle_problem(w).fields(w.theta, w.lam, yb)[0].v)
+    w.y_relu, w.c_relu, w.relu_bound, w.relu_sign = yb, 0.9, float(0.5 * (vals[14] + vals[15])), sign
+    p = oracle_problem(w)
+    assert p.nrelu == 29
+    r_o = p.rows(w.theta, w.lam)
+    J_o = ogn.jacobian(p, w.theta, w.lam)
+    lo = p.n * p.ne + p.nb + p.ninf
+    active = r_o[lo:lo + 29] != 0.0
+    assert 10 <= active.sum() <= 19
+    prob = gpu_problem(w)
+    th = dev(w.theta)
+    r, _ = prob.residual(th, w.lam)
+    r = host(r)
+    assert rel(r, r_o) <= TOL
+    np.testing.assert_array_equal(r[lo:lo + 29] != 0.0, active)
+    J = host(prob.jacobian(th, w.lam))
+    assert rel(J, J_o) <= TOL
+    assert np.all(J[lo:lo + 29][~active] == 0.0)
+    g = host(prob.gradient(th, w.lam))
+    assert rel(g, J_o.T @ r_o) <= TOL
+    prob.close()
