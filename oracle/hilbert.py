@@ -46,6 +46,24 @@ def velocity(x, g_at_x, g_nodes, M: int):
     return x * (conj - c0)
 
 
+def velocity_series(X, gX, g_nodes, M: int):
+    """The same discrete U(x) as a Taylor series in the collocation point x (oracle.taylor).
+
+    With x = tan(phi/2) and s_j = tan(psi_j/2) the kernel is rational in x,
+    cot((phi - psi_j)/2) = (1 + x s_j) / (x - s_j), so
+      U(x) = x [ (1/M) sum_j (g_j - g(x)) (1 + x s_j) / (x - s_j) - c0 ]
+    is the function velocity() evaluates, here differentiated exactly in x: X is the series of
+    the coordinate, gX the series of g at the points, g_nodes the node values (independent of x)."""
+    from .taylor import Taylor
+    _, s = nodes(M)
+    Xb = Taylor({m: c[:, None] + 0.0 * s[None, :] for m, c in X.c.items()}, X.d, X.K)    # (n, M)
+    gb = Taylor({m: c[:, None] + 0.0 * s[None, :] for m, c in gX.c.items()}, gX.d, gX.K)
+    terms = (gb * (-1.0) + g_nodes[None, :]) * (Xb * s[None, :] + 1.0) / (Xb - s[None, :])
+    conj = Taylor({m: c.sum(axis=1) / M for m, c in terms.c.items()}, terms.d, terms.K)
+    c0 = (g_nodes * s).sum() / M
+    return X * (conj - c0)
+
+
 def hilbert_decaying(x, f, M: int):
     """H f(x) for a decaying f (no s*g factorisation): C[F](phi) - c0_f with the same rule.
     Used only by the tests that pin the quadrature to known transform pairs."""

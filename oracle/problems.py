@@ -284,8 +284,9 @@ class Problem:
     def residual_series(self, theta, lam, ys, order):
         """The residuals R_k at the points ys as Taylor series in y: the operators applied to
         the fields' series of the given total order (the residuals lose one order per
-        derivative they take: one in 1D, two in 2D).  CCF is refused: its velocity is the
-        discrete Hilbert operator, whose y-derivative the paper does not define."""
+        derivative they take: one in 1D, two in 2D).  For CCF the velocity is the discrete
+        Hilbert operator differentiated in the collocation point (the paper leaves its
+        derivative undefined; this is the derivative of the operator the d0 residual uses)."""
         d = self.d
         Y = [Taylor.variable(ys[i], i, d, order) for i in range(d)]
         if self.eq == BURGERS:
@@ -299,8 +300,15 @@ class Problem:
             Om, Th, Psi = self.fields(theta, lam, ys, order=order)
             return residual_boussinesq(lam, Y[0], Y[1], Om, Om.diff(0), Om.diff(1), Th, Th.diff(0), Th.diff(1),
                                        Psi.diff(0), Psi.diff(1), Psi.diff(0).diff(0), Psi.diff(1).diff(1))
-        raise NotImplementedError("derivative losses of CCF need the y-derivative of the discrete Hilbert "
-                                  "operator, which the paper does not define")
+        if self.eq == CCF:
+            # the discrete velocity differentiated in the collocation point (the node values
+            # do not move): the derivative of the operator that defines the d0 residual
+            Th, g = self.fields(theta, lam, ys, extra_g=True, order=order)
+            _, s = hilbert.nodes(self.M)
+            g_nodes = self.fields(theta, lam, s.reshape(1, -1), extra_g=True)[1].v
+            Uvel = hilbert.velocity_series(Y[0], g, g_nodes, self.M)
+            return residual_ccf(lam, Y[0], Th, Th.diff(0), Uvel)
+        raise ValueError(self.eq)
 
     def d1_residuals(self, theta, lam, ys=None):
         """d R_k / d y_i at the points: array (N_E, d, n)."""

@@ -9,7 +9,8 @@ differentiate the residuals in y; rows sqrt(2 c rho / (N N_E d^n)) d^n R).
 * The Taylor field series agree with the second-order Jet fields (two implementations).
 * The loss gains exactly c_d1 / (N N_E d) sum rho (d R)^2 (with d R by complex step), and
   g = J~^T r~ stays the gradient of h (complex step of h in theta through the series).
-* CCF is refused (the discrete Hilbert operator's y-derivative is not defined).
+* CCF: the discrete Hilbert velocity differentiated in the collocation point; its rational
+  form has the circle-map form's value, and d1 / d2 match central differences of the d0 residual.
 """
 from math import factorial
 
@@ -141,11 +142,44 @@ def test_loss_gains_the_d1_term_and_gradient(eq, widths):
         assert abs(dh - g[j]) <= 1e-10 * (abs(g[j]) + 1e-3 * np.max(np.abs(g)))
 
 
-def test_ccf_derivative_losses_are_refused():
-    w = I.small_case(Pb.CCF, [1, 5, 1], 6, m=16)
-    p = Pb.Problem(Pb.CCF, [1, 5, 1], w.y, hilbert_m=16, y_d1=w.y[:, :2])
-    with pytest.raises(NotImplementedError):
-        p.rows(w.theta, w.lam)
+def test_ccf_velocity_series_is_the_discrete_operator():
+    """The rational form of the discrete Hilbert velocity (Taylor series in x) has the value
+    of the circle-map form the d0 residual uses, at every point."""
+    from oracle import hilbert
+    w = I.small_case(Pb.CCF, [1, 6, 1], 9, m=32, seed=3)
+    p = Pb.Problem(Pb.CCF, [1, 6, 1], w.y, hilbert_m=32)
+    Th, g = p.fields(w.theta, w.lam, w.y, extra_g=True)
+    _, s = hilbert.nodes(32)
+    gn_ = p.fields(w.theta, w.lam, s.reshape(1, -1), extra_g=True)[1].v
+    U0 = hilbert.velocity(w.y[0], g.v, gn_, 32)
+    _, gT = p.fields(w.theta, w.lam, w.y, extra_g=True, order=2)
+    UT = hilbert.velocity_series(Taylor.variable(w.y[0], 0, 1, 2), gT, gn_, 32)
+    # the two forms round the near-singular kernel terms differently: bound the difference by
+    # rounding of the sum of the terms' magnitudes, |x| (1/M) sum_j |g_j - g(x)| |cot|
+    x = w.y[0]
+    phi = 2.0 * np.arctan(x)
+    psi, _ = hilbert.nodes(32)
+    mag = np.abs(x) * (np.abs(gn_[None, :] - g.v[:, None]) / np.abs(np.tan(0.5 * (phi[:, None] - psi[None, :])))
+                       ).sum(axis=1) / 32
+    assert np.all(np.abs(UT.v - U0) <= 1e-14 * (mag + np.abs(U0)))
+
+
+def test_ccf_d1_and_d2_are_y_derivatives_of_the_d0_residual():
+    """CCF's d1 / d2 values against central differences of the d0 residual function (whose
+    velocity casts x to real, so no complex step here)."""
+    w = I.small_case(Pb.CCF, [1, 6, 1], 7, m=32, seed=5)
+    p = Pb.Problem(Pb.CCF, [1, 6, 1], w.y, hilbert_m=32)
+    ys = w.y
+    D1 = p.d1_residuals(w.theta, w.lam, ys)[0, 0]
+    D2 = p.d2_residuals(w.theta, w.lam, ys)[0, 0, 0]
+    e = 1e-5 * np.maximum(1.0, np.abs(ys[0]))
+    Rp = p.interior_residuals(w.theta, w.lam, ys + e)[0]
+    Rm = p.interior_residuals(w.theta, w.lam, ys - e)[0]
+    R0 = p.interior_residuals(w.theta, w.lam, ys)[0]
+    fd1 = (Rp - Rm) / (2 * e)
+    fd2 = (Rp - 2 * R0 + Rm) / e ** 2
+    np.testing.assert_allclose(D1, fd1, rtol=1e-6, atol=1e-7 * np.max(np.abs(fd1)))
+    np.testing.assert_allclose(D2, fd2, rtol=1e-3, atol=1e-4 * np.max(np.abs(fd2)))
 
 
 def test_planted_wrong_diff_factor_breaks_closed_form_pin(monkeypatch):
@@ -161,3 +195,20 @@ def test_planted_wrong_diff_factor_breaks_closed_form_pin(monkeypatch):
     monkeypatch.setattr(Taylor, "diff", wrong)
     with pytest.raises(AssertionError):
         test_burgers_closed_forms_have_flat_residuals(3, 0.5)
+
+
+def test_ccf_gradient_with_derivative_rows():
+    """g = J~^T r~ stays the gradient of h with CCF d1 and d2 rows (complex step of h in theta,
+    through the node values and the velocity series)."""
+    w = I.small_case(Pb.CCF, [1, 6, 1], 8, m=32, seed=7)
+    p = Pb.Problem(Pb.CCF, [1, 6, 1], w.y, hilbert_m=32, y_d1=w.y[:, :5], c_d1=0.6, y_d2=w.y[:, 2:6], c_d2=0.3)
+    assert p.n_rows == p.n + 5 + 4 + 1
+    J = gn.jacobian(p, w.theta, w.lam)
+    g = J.T @ p.rows(w.theta, w.lam)
+    x = np.concatenate([w.theta, [w.lam]]).astype(np.complex128)
+    for j in [0, p.P // 2, p.P]:
+        xc = x.copy()
+        xc[j] += 1j * 1e-30
+        r = p.rows(xc[:-1], xc[-1])
+        dh = (0.5 * np.sum(r * r)).imag / 1e-30
+        assert abs(dh - g[j]) <= 1e-10 * (abs(g[j]) + 1e-3 * np.max(np.abs(g)))
