@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--slices", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the equal-residual and batched-sweep records of the default line")
+    ap.add_argument("--extras-er-steps", type=int, default=50,
+                    help="FP64 GN steps of the default line's equal-residual record (CCF stable profile)")
     ap.add_argument("--micro", default=None, choices=[None, "gram", "chol", "jacobian"],
                     help="time one kernel family alone instead of the GN step (not the bench contract line)")
     ap.add_argument("--width", type=int, default=None,
@@ -119,23 +123,25 @@ def validation_grid_2d(n_r=512, n_a=256):
     return np.stack([r * np.cos(a), r * np.sin(a)])
 
 
-def equal_residual(args):
-    """Residual reached by the FP64 path after N GN steps, and the device time the split
-    path needs to reach 1.1x that residual from the same initialisation.  The residual
-    compared is the training loss h = |r~|^2/2 (the d0 loss the step minimises, which
-    the line search makes monotone); the max d0 residual on a 1e5-point validation grid
-    is reported beside it (evaluated outside the timed region)."""
+def equal_residual_record(workload, steps, precision="split_all", slices=6):
+    """Split precision vs FP64 at equal residual.  The FP64 path takes `steps` GN steps from
+    the seeded initialisation; the target is its final max d0 residual on the dense
+    validation grid times 1.1.  The split path then steps from the same initialisation until
+    it holds a state at least as converged as the FP64 path's final one: its own grid max d0
+    residual at or below the target and its training loss at or below 1.1 x the FP64 path's
+    final loss (the max d0 residual alone is not monotone early in a fit: a random-init
+    network can touch a low maximum after one step while its loss is still high).  At most
+    4 x steps.  The record gives both paths' device time (CUDA events around each gn_step;
+    the grid evaluations run outside those events), or the residual gap if the split path
+    never gets there."""
     import torch
-    from paper_2509_14185_gb300 import build as B
-    B.build()
     from paper_2509_14185_gb300 import gn, inputs
-    name = args.workload if args.workload in ("ccf_unstable1", "ccf_stable", "ipm") else "ccf_unstable1"
-    w = inputs.WORKLOADS[name]()
+    w = inputs.WORKLOADS[workload]()
     grid = validation_grid_1d() if w.d == 1 else validation_grid_2d()
     val = gn.GNProblem(w.equation, w.widths, grid, y_norm=w.y_norm, c_norm=w.c_norm, hilbert_m=w.hilbert_m)
 
-    def run(prec, max_steps, target=None):
-        prob = gn.GNProblem.from_workload(w, precision=prec, n_slices=args.slices)
+    def run(prec, max_steps, target=None, target_loss=None):
+        prob = gn.GNProblem.from_workload(w, precision=prec, n_slices=slices)
         theta = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
         lam, gam = w.lam, w.gamma
         t_ms, hist = 0.0, []
@@ -150,30 +156,41 @@ def equal_residual(args):
             res = val.gn_max_residual(theta, lam)
             hist.append({"step": k + 1, "ms": t_ms, "max_res": res, "lambda": lam, "loss": info["loss_after"],
                          "rc": rc})
-            if target is not None and info["loss_after"] <= target:
+            if target is not None and res <= target and info["loss_after"] <= target_loss:
                 break
         prob.close()
         return hist
 
-    h64 = run(gn.GN_PREC_FP64, args.er_steps)
-    target = h64[-1]["loss"] * 1.1
-    prec = {"split": gn.GN_PREC_SPLIT_BF16, "split_all": gn.GN_PREC_SPLIT_ALL}.get(args.precision,
-                                                                                gn.GN_PREC_SPLIT_ALL)
-    hs = run(prec, 4 * args.er_steps, target)
-    reached = hs[-1]["loss"] <= target
-    out = {"mode": "equal_residual", "workload": w.name, "grid_points": int(grid.shape[1]),
-           "compared": "training loss h (monotone under accepted GN steps); grid max d0 residual reported",
-           "fp64": {"steps": len(h64), "device_s": h64[-1]["ms"] / 1e3, "loss": h64[-1]["loss"],
-                    "max_res": h64[-1]["max_res"], "lambda": h64[-1]["lambda"]},
-           "split": {"precision": args.precision, "slices": args.slices, "reached": reached,
-                     "steps": len(hs), "device_s": hs[-1]["ms"] / 1e3, "loss": hs[-1]["loss"],
-                     "max_res": hs[-1]["max_res"], "lambda": hs[-1]["lambda"]},
-           "target_loss": target,
-           "speedup_to_equal_residual": (h64[-1]["ms"] / hs[-1]["ms"]) if reached else None,
-           "fp64_curve": [(h["step"], h["loss"], h["max_res"]) for h in h64[::5]],
-           "split_curve": [(h["step"], h["loss"], h["max_res"]) for h in hs[::5]]}
-    print(json.dumps(out))
+    h64 = run(gn.GN_PREC_FP64, steps)
+    target = h64[-1]["max_res"] * 1.1
+    target_loss = h64[-1]["loss"] * 1.1
+    prec = {"split": gn.GN_PREC_SPLIT_BF16, "split_all": gn.GN_PREC_SPLIT_ALL}.get(precision, gn.GN_PREC_SPLIT_ALL)
+    hs = run(prec, 4 * steps, target, target_loss)
+    reached = hs[-1]["max_res"] <= target and hs[-1]["loss"] <= target_loss
     val.close()
+    return {"workload": w.name, "grid_points": int(grid.shape[1]),
+            "target": "FP64 path's final max d0 residual on the validation grid x 1.1, with the training "
+                      "loss at or below 1.1 x the FP64 path's final loss",
+            "target_max_res": target, "target_loss": target_loss,
+            "fp64": {"steps": len(h64), "device_s": h64[-1]["ms"] / 1e3, "max_res": h64[-1]["max_res"],
+                     "loss": h64[-1]["loss"], "lambda": h64[-1]["lambda"]},
+            "split": {"precision": precision, "slices": slices, "reached": reached, "steps": len(hs),
+                      "device_s": hs[-1]["ms"] / 1e3, "max_res": hs[-1]["max_res"], "loss": hs[-1]["loss"],
+                      "lambda": hs[-1]["lambda"]},
+            "speedup_to_equal_residual": (h64[-1]["ms"] / hs[-1]["ms"]) if reached else None,
+            "residual_gap": None if reached else {"max_res": min(h["max_res"] for h in hs) / target,
+                                                  "loss": min(h["loss"] for h in hs) / target_loss},
+            "fp64_curve": [(h["step"], h["max_res"], h["loss"]) for h in h64[::5]],
+            "split_curve": [(h["step"], h["max_res"], h["loss"]) for h in hs[::5]]}
+
+
+def equal_residual(args):
+    """--equal-residual: the record of equal_residual_record for --workload, printed alone."""
+    from paper_2509_14185_gb300 import build as B
+    B.build()
+    name = args.workload if args.workload in ("ccf_unstable1", "ccf_stable", "ipm") else "ccf_unstable1"
+    out = dict({"mode": "equal_residual"}, **equal_residual_record(name, args.er_steps, args.precision, args.slices))
+    print(json.dumps(out))
     return 0
 
 
@@ -751,11 +768,19 @@ def kernel_report(prob, args, phases, pipe_tiles=0):
         pk, src = measured_peak("bf16_tflops_sustained", 1700.0)
         executed = gram_executed_flops(rows, Pp, S)
         tens = executed / (gram_ms * 1e-3) / 1e12
+        alg = gram_flops / (gram_ms * 1e-3) / 1e12
         # DRAM bytes of the whole-triangle launch from one ncu capture; the pipelined step's
         # chunk launches run inside a graph with conditional nodes, where ncu lists no kernels
         traffic = (GRAM_TRAFFIC_BYTES_CCF_S6 if (S == 6 and getattr(args, "workload", "") == "ccf_unstable1"
                                                  and not pipe_tiles) else None)
-        out["gram"] = {"bound": "tensor", "achieved": tens, "peak": pk, "unit": "TFLOP/s", "frac": tens / pk,
+        out["gram"] = {"bound": "tensor", "achieved": alg, "peak": pk, "unit": "TFLOP/s", "frac": alg / pk,
+                       "achieved_units": "algorithmic FLOP rows * P'(P'+1) (the symmetric half of J~^T J~, "
+                                         "FP64-equivalent) per launch / the Gram phase time; the split "
+                                         "path's extra slice products count as overhead",
+                       "tensor_pipe": {"executed_tflops": tens, "frac": tens / pk,
+                                       "executed_flops_per_launch": executed,
+                                       "note": f"{S * (S + 1) // 2} BF16 slice-pair products per FP64-accurate "
+                                               "entry, over the 128 x 128 lower tiles and 128-padded K"},
                        "traffic": traffic, "traffic_unit": "bytes per launch" if traffic else None, "ms": gram_ms,
                        "kernel": f"ozaki_kernel<{S},1,0> (split Gram: BF16 slice products on tcgen05, TMEM "
                                  "accumulators; the slicing pre-pass is inside the timed phase)",
@@ -764,8 +789,7 @@ def kernel_report(prob, args, phases, pipe_tiles=0):
                                         "stream beside the factorisation; ms is the Gram's wall time (slicing "
                                         "to its last chunk) while it shares the SMs with the factorisation"}
                           if pipe_tiles else {}),
-                       "executed_flops_per_launch": executed,
-                       "fp64_equivalent_tflops": gram_flops / (gram_ms * 1e-3) / 1e12,
+                       "fp64_equivalent_tflops": alg,
                        "algorithmic_flops_per_launch": gram_flops}
     cf = Pp ** 3 / 3.0
     c = cf / (chol_ms * 1e-3) / 1e12
@@ -838,11 +862,7 @@ def run_reference(args):
 
 
 def run_batched(args):
-    """64 uneven CCF fits (widths 16..64, depth 2-3, 2048..16384 points, lambda ~ U[0.5, 3])
-    stepped together through gn_batch_step on `--streams` CUDA streams.  value = fit-steps/s
-    (64 x steps / time).  gn_step returns only after its stream is idle, so the span between
-    two events on an otherwise idle stream, recorded before and after the K batched steps,
-    is the device-clock time of the whole batch."""
+    """--workload batched: the batched sweep's own JSON line (see batched_record)."""
     import torch
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -851,7 +871,25 @@ def run_batched(args):
         dist.init_process_group("nccl")
     from paper_2509_14185_gb300 import build as B
     B.build()
+    line = batched_record(args, args.steps, args.warmup, rank, world)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def batched_record(args, steps, warmup, rank=0, world=1):
+    """64 uneven CCF fits (widths 16..64, depth 2-3, 2048..16384 points, lambda ~ U[0.5, 3])
+    stepped together: by default as one CUDA graph launch per batched step (every fit a
+    branch; --eager: gn_batch_step on `--streams` CUDA streams).  value = fit-steps/s
+    (64 x steps / time).  Each batched step returns only after its work is done, so the span
+    between two events on an otherwise idle stream, recorded before and after the K batched
+    steps, is the device-clock time of the whole batch."""
+    import torch
     from paper_2509_14185_gb300 import gn, inputs
+    if world > 1:
+        import torch.distributed as dist
     fits = replica_workload("batched", rank)
     prec = {"fp64": gn.GN_PREC_FP64, "split": gn.GN_PREC_SPLIT_BF16, "split_all": gn.GN_PREC_SPLIT_ALL}[args.precision]
     batch = gn.GNBatch(fits, n_streams=args.streams, precision=prec, n_slices=args.slices)
@@ -866,7 +904,7 @@ def run_batched(args):
         step = lambda l, g: batch.gn_batch_graph_step(l, g)
     else:
         step = lambda l, g: batch.gn_batch_step(thetas, l, g)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         lams, gams, infos, st = step(lams, gams)
     torch.cuda.synchronize()
     if world > 1:
@@ -879,14 +917,14 @@ def run_batched(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     statuses = []
     ev0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         lams, gams, infos, st = step(lams, gams)
         statuses.append(st)
     ev1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
     launches = L.gn_kernel_launches() - launches0
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = ev0.elapsed_time(ev1) / steps
     if world > 1:
         ms = max_over_ranks(ms, "cuda")
         dist.barrier()
@@ -910,7 +948,7 @@ def run_batched(args):
                     "note": "executed Gram slice-product FLOP of all fits / whole batched step time "
                             "(a lower bound on the Gram kernels' own rate)", "peak_source": src}
         line = {"metric": "gn_fit_steps_per_s", "value": value, "unit": "fit-steps/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "steps": steps, "warmup": warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": f"batched_ccf_sweep_{n}_fits", "fits": n,
                            "gram_split": args.gram_split or "autotuned",
@@ -926,11 +964,8 @@ def run_batched(args):
                 "gpu_launches": int(launches),
                 "final": {"loss_mean": statistics.mean(i["loss_after"] for i in infos),
                           "warnings": sum(1 for st in statuses for x in st if x != 0)}}
-        print(json.dumps(line))
-    if world > 1:
-        dist.destroy_process_group()
     batch.close()
-    return 0
+    return line
 
 
 # ---------------------------------------------------------------------------
@@ -986,6 +1021,8 @@ def main():
         if rc < 0:
             raise RuntimeError(f"gn_step failed in warm-up: {rc}")
     torch.cuda.synchronize()
+    # the state the timed steps start from: the end-to-end run repeats exactly these steps
+    theta_start, lam_start, gam_start = theta.clone(), lam, gam
     if world > 1:
         dist.barrier()
     L = gn.lib()
@@ -1057,30 +1094,51 @@ def main():
     # phase is a chain of several kernels and is reported beside it under "kernels")
     roof = dict(kernels["gram"])
 
-    # end to end through the C ABI with pinned host buffers
+    # end to end through the C ABI with pinned host buffers: the same K steps again, from the
+    # state the timed steps started from.  Every step copies theta in from pinned host memory,
+    # steps, and copies theta back out with a blocking copy (the host holds the result before
+    # the next step's input is formed from it); lambda, damping and the loss are host scalars
+    # of the call.  The run must end on the timed run's final state bit for bit.
     e2e = None
     if not args.no_e2e:
-        th_host = theta.detach().cpu().pin_memory()
+        theta_dev_final, lam_dev_final, gam_dev_final = theta.clone(), lam, gam
+        th_host = theta_start.detach().cpu().pin_memory()
         out_host = torch.empty_like(th_host).pin_memory()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
-        e0.record(stream)
-        lam2, gam2 = lam, gam
+        t0 = time.perf_counter()
+        lam2, gam2 = lam_start, gam_start
         for _ in range(args.steps):
             theta.copy_(th_host, non_blocking=True)
             rc, lam2, gam2, info2 = gn_step(theta, lam2, gam2)
-            out_host.copy_(theta, non_blocking=True)
+            if rc < 0:
+                raise RuntimeError(f"gn_step failed in the end-to-end run: {rc}")
+            out_host.copy_(theta)            # blocking device-to-host copy of the step's result
             th_host.copy_(out_host)
-        e1.record(stream)
         torch.cuda.synchronize()
-        ms_e2e = e0.elapsed_time(e1) / args.steps
+        ms_e2e = (time.perf_counter() - t0) * 1e3 / args.steps
+        same = bool(torch.equal(theta, theta_dev_final)) and lam2 == lam_dev_final and gam2 == gam_dev_final
+        if not same:
+            print("bench: the end-to-end run did not reproduce the device-timed run's final state",
+                  file=sys.stderr)
         if world > 1:
             ms_e2e = max_over_ranks(ms_e2e, "cuda")
         nb = prob.P * 8
         e2e = {"value": world * 1000.0 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": nb,
-               "d2h_bytes_per_step": nb + 8,
-               "note": "theta in from pinned host memory, gn_step, theta out to pinned host memory; "
-                       "lambda/damping/loss are host scalars of the call"}
+               "d2h_bytes_per_step": nb, "ms_per_step": ms_e2e,
+               "reproduces_timed_run": same,
+               "note": "the timed run's K steps again from its starting state (host wall clock): theta in "
+                       "from pinned host memory, gn_step through the C ABI, theta out to pinned host memory "
+                       "with a blocking copy; lambda, damping and the loss are host scalars of the call"}
+
+    # split precision vs FP64 at equal residual (CCF stable profile, the survey's target), and
+    # the batched sweep of 64 uneven fits as one graph launch per step
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras["equal_residual"] = equal_residual_record("ccf_stable", args.extras_er_steps, "split_all", args.slices)
+        b = batched_record(args, 5, 2)
+        extras["batched"] = {k: b[k] for k in ("metric", "value", "unit", "ms_per_step", "steps", "warmup",
+                                                "roofline", "gpu_launches")}
+        extras["batched"]["config"] = b["config"]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1105,7 +1163,8 @@ def main():
                                                 "and factor phases run at the same time"} if pipe_tiles else {})),
                 "step_call": "gn_step_graph (captured CUDA graphs)" if use_graph else "gn_step",
                 "final": {"loss": infos[-1]["loss_after"], "lambda": lam, "damping": gam,
-                          "trials": [i["n_trials"] for i in infos]}}
+                          "trials": [i["n_trials"] for i in infos]},
+                **extras}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

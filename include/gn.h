@@ -160,6 +160,11 @@ typedef struct gn_step_info {
   double ms_phase[8];        /* device time per phase: jacobian, gram, gradient, factor,
                                 solve, line search, total, unused */
   double momentum;           /* gn_step_ema: the closed-form momentum coefficient mu (0 in gn_step) */
+  double max_abs_res;        /* gn_step and gn_step_graph: max |R_k| over the interior points and
+                                equations at the step's starting point (theta, lambda), unweighted
+                                (Methods, "Validation Metrics", max d0 residual on the collocation
+                                points), from the rows the step evaluates anyway; the accepted
+                                point's value is the next step's.  NaN if a row was not finite. */
 } gn_step_info;
 
 typedef struct gn_handle gn_handle;
@@ -437,12 +442,26 @@ int gn_max_residual(gn_handle* h, const double* theta, double lambda, double* ou
  * Scratch lives in a fixed 8 MiB device array inside the library image,
  * held by every GPU that loads the library until the process exits;
  * ncols > 16384 returns GN_ERR_TOO_LARGE.  The first call on a device looks
- * up the array's device address (make it before any stream capture).  All
+ * up the array's device address (make it before any stream capture); that
+ * address stays cached and is not valid after a cudaDeviceReset of the device,
+ * so do not call this entry point on a device after resetting it.  All
  * calls on a device share the array: calls that overlap on the GPU race, so
  * serialise them.  Returns GN_OK, GN_ERR_INVALID, GN_ERR_TOO_LARGE,
  * GN_ERR_UNSUPPORTED (device index >= 64) or GN_ERR_CUDA. */
 int gn_jtr_noalloc(const double* J, int64_t ld, int64_t nrows, int64_t ncols, const double* r, double* g_out,
                    void* cuda_stream);
+
+/* Testing hook of the failure path GN_ERR_TIMEOUT (no paper counterpart).  Every wait of the
+ * split-precision tensor-core kernels on an mbarrier (a copy landing, an MMA completing, an
+ * accumulator becoming free) is bounded in time; when one runs out, the kernel raises a
+ * status bit, lets its copies and MMAs in flight finish (again with a bound), releases its
+ * tensor memory and returns, and the calling entry point returns GN_ERR_TIMEOUT with the
+ * CUDA context still usable.  wait_ns sets that bound for later launches (0 restores the
+ * default of 4 s); starve_copies != 0 makes the kernels' producer issue no copies at all,
+ * so no copy or MMA is ever in flight and every consumer's wait runs out after wait_ns,
+ * which lets a test exercise the path without any fault.  Process-wide; not for use while
+ * other threads launch work.  Returns GN_OK. */
+int gn_test_bounded_waits(unsigned long long wait_ns, int starve_copies);
 
 /* Number of CUDA kernels this library has launched in this process so far
  * (a diagnostic counter; read it before and after a region to count its launches). */

@@ -332,6 +332,18 @@ int loss_of(gn_handle* h, const double* r, int slot) {
   return GN_OK;
 }
 
+int max_res_of(gn_handle* h, const double* r) {
+  const int64_t n = h->p.n_pts;
+  if (n == 0) {
+    GN_TRY_CUDA(cudaMemsetAsync(h->red + kMaxResSlot, 0, sizeof(double), h->st));
+    return GN_OK;
+  }
+  // interior rows carry sqrt(2 rho / (N N_E)) R_k, divided by eps in a second stage
+  const double w = sqrt(2.0 / ((double)n * h->ne)) / (h->staged ? h->stage_eps : 1.0);
+  GN_TRY_CUDA(max_abs_unweighted(r, n, h->ne, h->p.rho, w, h->red, h->red + kMaxResSlot, h->st));
+  return GN_OK;
+}
+
 int residual_loss(gn_handle* h, const double* theta, double lam, double* r, double* loss) {
   Pass ps = {MODE_RESIDUAL, r, nullptr, 0, 0, 0, nullptr};
   int rc = run_pass(h, theta, lam, ps, nullptr);
@@ -651,9 +663,12 @@ int gn_gram(gn_handle* h, const double* J, int64_t ld, int64_t nrows, const doub
   return (f & 2) ? GN_ERR_TIMEOUT : GN_OK;
 }
 
-int gn_damped_solve(gn_handle* h, const double* G, const double* g, double* gamma, double* delta_out,
-                    int* retries_out) {
-  if (!h || !G || !g || !gamma || !delta_out) return GN_ERR_INVALID;
+namespace {
+// The damped solve of gn_damped_solve.  With check_rows, a non-finite residual row seen by the
+// jet kernel since the caller cleared status bit 0 (h->flag[0]) ends the call with
+// GN_ERR_NONFINITE at the first synchronisation, before any damping escalation.
+int damped_solve(gn_handle* h, const double* G, const double* g, double* gamma, double* delta_out,
+                 int* retries_out, bool check_rows) {
   const int64_t Pp = h->Pp;
   int retries = 0;
   for (;;) {
@@ -668,15 +683,16 @@ int gn_damped_solve(gn_handle* h, const double* G, const double* g, double* gamm
     } else {
       GN_TRY_CUDA(cholesky_factor(h->A, Pp, Pp, h->Linv, h->flag + 1, h->st));
     }
-    int hflag[2] = {0, 0};
-    GN_TRY_CUDA(cudaMemcpyAsync(&h->hpin[8], h->flag + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    int hflag[3] = {0, 0, 0};
+    GN_TRY_CUDA(cudaMemcpyAsync(&h->hpin[8], h->flag, 3 * sizeof(int), cudaMemcpyDeviceToHost, h->st));
     GN_TRY_CUDA(cudaStreamSynchronize(h->st));
-    memcpy(hflag, &h->hpin[8], 2 * sizeof(int));
-    if (hflag[1] & 2) {
+    memcpy(hflag, &h->hpin[8], 3 * sizeof(int));
+    if (hflag[2] & 2) {
       set_detail(__FILE__, __LINE__, "a bounded wait in a tensor-core kernel timed out");
       return GN_ERR_TIMEOUT;
     }
-    if (!hflag[0]) break;
+    if (check_rows && (hflag[0] & 1)) return GN_ERR_NONFINITE;
+    if (!hflag[1]) break;
     if (retries == 5) {
       if (retries_out) *retries_out = retries;
       return GN_ERR_NOT_SPD;
@@ -691,6 +707,13 @@ int gn_damped_solve(gn_handle* h, const double* G, const double* g, double* gamm
   else
     GN_TRY_CUDA(cholesky_solve(h->A, Pp, Pp, h->Linv, g, delta_out, h->vtmp, h->st));
   return GN_OK;
+}
+}  // namespace
+
+int gn_damped_solve(gn_handle* h, const double* G, const double* g, double* gamma, double* delta_out,
+                    int* retries_out) {
+  if (!h || !G || !g || !gamma || !delta_out) return GN_ERR_INVALID;
+  return damped_solve(h, G, g, gamma, delta_out, retries_out, false);
 }
 
 int gn_max_residual(gn_handle* h, const double* theta, double lambda, double* out) {
@@ -720,6 +743,8 @@ int gn_step(gn_handle* h, double* theta, double* lambda, double* damping, gn_ste
   double gamma = *damping;
   Timer tm(st);
   Phases ph;
+  // status bits: [0] non-finite residual rows of this step's passes, [2] a timed-out wait
+  GN_TRY_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), st));
   GN_TRY_CUDA(cudaMemsetAsync(h->flag + 2, 0, sizeof(int), st));
   tm.mark(0);
   // 1. rows and Jacobian, Gram and gradient, streamed in row blocks
@@ -747,7 +772,9 @@ int gn_step(gn_handle* h, double* theta, double* lambda, double* damping, gn_ste
   }
   GN_TRY_CUDA(mirror_lower(h->G, Pp, Pp, st));
   rc = loss_of(h, h->r, 0);
+  if (!rc) rc = max_res_of(h, h->r);
   if (rc) return rc;
+  GN_TRY_CUDA(cudaMemcpyAsync(h->hpin + 4, h->red + kMaxResSlot, sizeof(double), cudaMemcpyDeviceToHost, st));
   tm.mark(4);
   if (nblk == 1) {
     GN_TRY_CUDA(cudaEventSynchronize(tm.ev[4]));
@@ -757,7 +784,7 @@ int gn_step(gn_handle* h, double* theta, double* lambda, double* damping, gn_ste
   // 2. damped solve
   ph.next("gn_step: damped solve");
   int retries = 0;
-  rc = gn_damped_solve(h, h->G, h->g, &gamma, h->delta, &retries);
+  rc = damped_solve(h, h->G, h->g, &gamma, h->delta, &retries, true);
   tm.mark(5);
   inf.chol_retries = retries;
   inf.gamma_used = gamma;
@@ -781,6 +808,7 @@ int gn_step(gn_handle* h, double* theta, double* lambda, double* damping, gn_ste
   const double dlam = h->hpin[3];
   inf.loss_before = h0;
   inf.loss_after = h0;
+  inf.max_abs_res = h->hpin[4];
   tm.mark(6);
   if (!std::isfinite(h0)) {
     inf.status = GN_ERR_NONFINITE;
@@ -863,6 +891,7 @@ int gn_step_ema(gn_handle* h, double* theta, double* lambda, double* damping, do
   double* JD = u + Pp;   // J~ delta
   double* Jv = JD + R;   // J~ v_prev
   Timer tm(st);
+  GN_TRY_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), st));
   GN_TRY_CUDA(cudaMemsetAsync(h->flag + 2, 0, sizeof(int), st));
   tm.mark(0);
   // 1. rows and the Jacobian
@@ -881,7 +910,7 @@ int gn_step_ema(gn_handle* h, double* theta, double* lambda, double* damping, do
   tm.mark(2);
   // 3. Delta = -(G_ema + gamma I)^{-1} g  (h->delta holds -Delta)
   int retries = 0;
-  rc = gn_damped_solve(h, G_ema, h->g, &gamma, h->delta, &retries);
+  rc = damped_solve(h, G_ema, h->g, &gamma, h->delta, &retries, true);
   tm.mark(3);
   inf.chol_retries = retries;
   inf.gamma_used = gamma;

@@ -194,6 +194,9 @@ struct Pass {
 int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, double* grad);
 // 1/2 |r|^2 reduction: the sum of squares lands in red[256 + slot] (device)
 int loss_of(gn_handle* h, const double* r, int slot);
+// max |R_k| over the interior points of rows r (unweighted) into red[kMaxResSlot] (device)
+constexpr int kMaxResSlot = 270;
+int max_res_of(gn_handle* h, const double* r);
 int gram_into(gn_handle* h, const double* J, int64_t ld, int64_t nrows, const double* r, double* G, double* g,
               int precision, int accumulate);
 // grow the split workspace to what every split contraction of a step needs, and create the
@@ -243,6 +246,9 @@ cudaError_t add_diag_band(const double* G, double* A, int64_t n, int64_t ld, int
 cudaError_t copy_add_diag(const double* G, double* A, int64_t n, int64_t ld, double gamma, cudaStream_t st);
 cudaError_t max_abs_rows(const double* r, int64_t n, int stride_valid, double* red, cudaStream_t st);
 cudaError_t finish_max(double* red, double* out_dev, cudaStream_t st);
+// max |R_k| over the interior rows r_i = w sqrt(rho_i) R_k (rho null: 1) into *out_dev
+cudaError_t max_abs_unweighted(const double* r, int64_t n_pts, int ne, const double* rho, double w, double* red,
+                               double* out_dev, cudaStream_t st);
 
 // CCF Hilbert operator construction and contractions.
 cudaError_t hilbert_build(const double* y, int64_t n, int M, double* kf, double* dcoef, double* snode,

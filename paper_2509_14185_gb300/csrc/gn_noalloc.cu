@@ -18,6 +18,9 @@
 // because every scratch entry a call reads is written earlier by the same
 // call.  Calls whose executions overlap on the GPU (different streams, or
 // different host threads on one device) race on the scratch: serialise them.
+// The looked-up address stays cached for the life of the process; it is not valid
+// across a cudaDeviceReset of that device (the module is then loaded anew), so callers
+// that reset a device must not call this entry point on it afterwards.
 #include <mutex>
 
 #include "gn_internal.cuh"
@@ -39,19 +42,19 @@ extern "C" int gn_jtr_noalloc(const double* J, int64_t ld, int64_t nrows, int64_
   if (!J || !r || !g_out || nrows < 0 || ncols < 1 || ld < ncols) return GN_ERR_INVALID;
   if (ncols > kNoAllocMaxCols) return GN_ERR_TOO_LARGE;
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return GN_ERR_CUDA;
+  if (GN_NOTE(cudaGetDevice(&dev)) != cudaSuccess) return GN_ERR_CUDA;
   if (dev < 0 || dev >= kNoAllocMaxDevices) return GN_ERR_UNSUPPORTED;
   double* scratch = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_addr[dev]) {
       void* p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GN_ERR_CUDA;
+      if (GN_NOTE(cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess || !p) return GN_ERR_CUDA;
       g_noalloc_addr[dev] = static_cast<double*>(p);
     }
     scratch = g_noalloc_addr[dev];
   }
-  const cudaError_t e =
-      gn::dgemv_t_scratch(J, ld, nrows, ncols, r, g_out, 0.0, scratch, static_cast<cudaStream_t>(cuda_stream));
+  const cudaError_t e = GN_NOTE(
+      gn::dgemv_t_scratch(J, ld, nrows, ncols, r, g_out, 0.0, scratch, static_cast<cudaStream_t>(cuda_stream)));
   return e == cudaSuccess ? GN_OK : GN_ERR_CUDA;
 }

@@ -43,6 +43,7 @@ struct StepState {
   double h0, gd, dGd, dlam; // loss and model scalars of the step
   double ht, rho;           // accepted trial loss, LM ratio
   double gamma_used;        // damping of the factorisation the step used
+  double max_res;           // max |R_k| over the interior points at the step's starting point
   int n_trials, accepted, status, pad;
 };
 
@@ -111,10 +112,11 @@ __global__ void model_kernel(const double* __restrict__ red, const double* __res
   s->gd = red[257];
   s->dGd = red[258];
   s->dlam = delta[P];
+  s->max_res = red[kMaxResSlot];
   int status = GN_OK;
   if (flag[2] & 2) status = GN_ERR_TIMEOUT;          // a bounded tensor-core wait gave up
+  else if (!isfinite(s->h0)) status = GN_ERR_NONFINITE;   // before the pivots: no retries on NaN rows
   else if (flag[1]) status = kNeedRetry;             // a pivot was not positive
-  else if (!isfinite(s->h0)) status = GN_ERR_NONFINITE;
   s->status = status;
   cudaGraphSetConditional(first, status == GN_OK ? 1u : 0u);   // run the first trial?
 }
@@ -200,7 +202,8 @@ int capture_rows_gram(gn_handle* h, const double* theta, bool marks) {
   }
   if (rc) return rc;
   GN_G_TRY(mirror_lower(h->G, h->Pp, h->Pp, st));
-  return loss_of(h, h->r, 0);
+  rc = loss_of(h, h->r, 0);
+  return rc ? rc : max_res_of(h, h->r);
 }
 
 // The second half: damped factorisation and solve, model scalars, IF(trial) x 8, commit.
@@ -335,6 +338,7 @@ int capture_pipelined(gn_handle* h, double* theta, bool marks, int64_t chunk) {
   GN_G_TRY(cudaEventRecord(join, sg));
   GN_G_TRY(dgemv_t_scratch(h->J, h->ldJ, h->n_rows, h->Pp, h->r, h->g, 0.0, h->vtmp, st));
   rc = loss_of(h, h->r, 0);
+  if (!rc) rc = max_res_of(h, h->r);
   if (rc) return rc;
   return capture_solve(h, theta, marks, gate.data(), join);
 }
@@ -459,6 +463,7 @@ int finish_step(gn_handle* h, double* lambda, double* damping, gn_step_info* inf
   gn_step_info inf;
   memset(&inf, 0, sizeof(inf));
   inf.chol_retries = retries;
+  inf.max_abs_res = s->max_res;
   int status = s->status;
   if (status == kNeedRetry) status = GN_ERR_NOT_SPD;
   // the damping of the accepted factorisation (before the LM update), as gn_step reports it

@@ -58,7 +58,7 @@ constexpr int BKS = 32;            // K per stage (64-byte rows, SWIZZLE_64B)
 constexpr int SPC = 4;             // stages per exact-accumulation chunk (K = 128)
 constexpr int SLICE_BYTES = TM * BKS * 2;   // one slice tile: 8 KB
 constexpr int NTHREADS = 320;      // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
-constexpr unsigned long long kWaitNs = 4000000000ull;   // 4 s bound on any wait
+constexpr unsigned long long kWaitNs = 4000000000ull;   // default bound on any wait: 4 s
 
 __host__ __device__ constexpr int n_stages(int S) {
   return (2 * S * SLICE_BYTES * 4 <= 200 * 1024) ? 4 : (2 * S * SLICE_BYTES * 3 <= 200 * 1024) ? 3 : 2;
@@ -99,17 +99,28 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: returns false (and raises the status flag) after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* flag) {
+// Bounded wait: returns false (and raises bit 1 of the status word) after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* flag, unsigned long long limit_ns) {
   if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = now_ns();
   while (!mbar_try(bar, parity)) {
-    if (now_ns() - t0 > kWaitNs) {
+    if (now_ns() - t0 > limit_ns) {
       atomicOr(flag, 2);
       return false;
     }
   }
   return true;
+}
+// AND of a predicate over the 256 epilogue threads (named barrier 1): every one of them takes
+// the same branch afterwards, so all run the same sequence of named-barrier syncs
+__device__ __forceinline__ bool epilogue_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.b32 p, %1, 0;\n bar.red.and.pred q, 1, 256, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
   asm volatile(
@@ -206,6 +217,8 @@ struct OzArgs {
   int64_t tile0;
   int64_t mt;
   int colmajor;
+  unsigned long long wait_ns;   // bound on every mbarrier wait
+  int starve;                   // testing: the producer issues no copy, so the waits run out
 };
 
 // Lower-triangular tile t of an mt x mt tile grid.  Row order: row ti holds tiles
@@ -294,10 +307,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {
       const int rowA = (int)(ti * TM), rowB = (int)(tj * TN);
       int issued = 0;
-      for (int kt = 0; kt < nk; kt++) {
+      for (int kt = 0; kt < (p.starve ? 0 : nk); kt++) {
         const int st = kt % NST;
         if (kt >= NST) {
-          if (!mbar_wait(&empty[st], ((kt / NST) - 1) & 1, flag)) {
+          if (!mbar_wait(&empty[st], ((kt / NST) - 1) & 1, flag, p.wait_ns)) {
             abort_cta = 1;
             break;
           }
@@ -312,20 +325,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         issued = kt + 1;
       }
-      // drain: every issued stage must land before the CTA may exit
+      // drain: every issued stage must land before the CTA may exit.  A stage that does not
+      // land within the bound raises bit 2 as well (copies may still be in flight); the CTA
+      // still releases its tensor memory below, since a CTA that exits holding it would block
+      // every later allocation on this SM, and the host fails the call with GN_ERR_TIMEOUT.
       for (int kt = (issued > NST ? issued - NST : 0); kt < issued; kt++)
-        mbar_wait(&full[kt % NST], (kt / NST) & 1, flag);
+        if (!mbar_wait(&full[kt % NST], (kt / NST) & 1, flag, p.wait_ns)) atomicOr(flag, 4);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       bool ok = true;
+      bool mma_issued = false;
       for (int c = 0; c < nchunk && ok; c++) {
         const int q_end = (nk - c * spc) < spc ? (nk - c * spc) : spc;
         for (int q = 0; q < q_end && ok; q++) {
           const int kt = c * spc + q;
           const int st = kt % NST;
-          if (!mbar_wait(&full[st], (kt / NST) & 1, flag)) { ok = false; break; }
+          if (!mbar_wait(&full[st], (kt / NST) & 1, flag, p.wait_ns)) { ok = false; break; }
           tc_fence_after();
           const uint32_t base = smem_u32(smem + st * STAGE_BYTES);
           // pass 0: tail levels (>= 5); pass 1: the exact head levels.  With one exponent
@@ -336,7 +353,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
           for (int pass = 0; pass < 2; pass++) {
             if (q == 0 && c > 0 && pass == (CH ? 0 : 1)) {
-              if (!mbar_wait(acc_empty, (c - 1) & 1, flag)) { ok = false; break; }
+              if (!mbar_wait(acc_empty, (c - 1) & 1, flag, p.wait_ns)) { ok = false; break; }
               tc_fence_after();
             }
 #pragma unroll
@@ -355,6 +372,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                   const bool first = (slot < 3) ? (q == 0 && kk == 0 && s == 0)
                                                 : ((CH ? q : kt) == 0 && kk == 0 && s == 0 && u == 3);
                   mma_bf16(tmem + slot * TN, da, db, first ? 0u : 1u);
+                  mma_issued = true;
                 }
               }
           }
@@ -364,9 +382,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (ok) mma_commit(acc_full);
       }
       if (!ok) abort_cta = 1;
-      // every issued MMA must complete before tensor memory is released
-      mma_commit(done);
-      mbar_wait(done, 0, flag);
+      // every issued MMA must complete before tensor memory is released (nothing to wait for
+      // when none was issued).  A timeout here raises bit 2 too; tensor memory is released all
+      // the same (see the producer's drain) and the host fails the call with GN_ERR_TIMEOUT.
+      if (mma_issued) {
+        mma_commit(done);
+        if (!mbar_wait(done, 0, flag, p.wait_ns)) atomicOr(flag, 4);
+      }
     }
   } else {
     // ---------------- epilogue: 8 warps, 64 columns each ----------------
@@ -392,7 +414,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         eccf[c & 1][qcol][row] = pow2f(ev);
         asm volatile("bar.sync 1, 256;" ::: "memory");
       }
-      if (!mbar_wait(acc_full, c & 1, flag)) { ok = false; break; }
+      // one decision for all 256 epilogue threads: a thread whose own bounded wait ran out
+      // while another's succeeded must not leave the loop alone (the chunked path's in-loop
+      // bar.sync and the one after the loop would then find too few partners)
+      if (!epilogue_all(mbar_wait(acc_full, c & 1, flag, p.wait_ns))) { ok = false; break; }
       tc_fence_after();
       if constexpr (CH) {
         // head levels and the tail, each scaled by this chunk's 2^e_row 2^e_col (two exact
@@ -697,6 +722,15 @@ int prep_rows(const double* X, int64_t ld, int64_t n, int64_t k, const OzOperand
   return GN_NOTE(cudaGetLastError()) == cudaSuccess ? GN_OK : GN_ERR_CUDA;
 }
 
+}  // namespace
+
+// Testing hooks of the bounded waits (gn_test_bounded_waits): the bound on every mbarrier wait
+// of the split GEMM, and whether its producer issues no copies.
+std::atomic<unsigned long long> g_oz_wait_ns{kWaitNs};
+std::atomic<int> g_oz_starve{0};
+
+namespace {
+
 template <int S, bool SYM>
 int launch_oz(const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, double* C, int64_t ldc, int mode,
               const double* rowscale, int* flag, cudaStream_t st, int ksplit, void* part, const OzRange& range) {
@@ -727,6 +761,8 @@ int launch_oz(const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, doub
   a.mode = mode;
   a.rowscale = rowscale;
   a.flag = flag;
+  a.wait_ns = g_oz_wait_ns.load(std::memory_order_relaxed);
+  a.starve = g_oz_starve.load(std::memory_order_relaxed);
   const int64_t all_tiles = SYM ? mt * (mt + 1) / 2 : mt * nt;
   a.tile0 = 0;
   a.mt = mt;
@@ -1079,3 +1115,10 @@ int split_gram_pipelined(gn_handle* h, const double* J, int64_t ld, int64_t nrow
 }
 
 }  // namespace gn
+
+// Testing hook of the bounded waits (declared in gn.h).
+extern "C" int gn_test_bounded_waits(unsigned long long wait_ns, int starve_copies) {
+  gn::g_oz_wait_ns.store(wait_ns ? wait_ns : gn::kWaitNs, std::memory_order_relaxed);
+  gn::g_oz_starve.store(starve_copies ? 1 : 0, std::memory_order_relaxed);
+  return GN_OK;
+}

@@ -47,6 +47,27 @@ __global__ void __launch_bounds__(RT) reduce_kernel(const double* __restrict__ x
   }
 }
 
+// max over rows i < n of |r_i| / (w sqrt(rho_{i / ne})) (rho null: 1), NaN propagating: the
+// largest unweighted residual |R_k| of the interior rows r_i = w sqrt(rho) R_k
+__global__ void __launch_bounds__(RT) max_unweighted_kernel(const double* __restrict__ r,
+                                                            const double* __restrict__ rho, int64_t n, int ne,
+                                                            double w, double* red) {
+  __shared__ double s[RT / 32];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < n; i += (int64_t)RB * RT) {
+    const double a = fabs(r[i]) / (rho ? w * sqrt(rho[i / ne]) : w);
+    acc = (a > acc || a != a) ? a : acc;
+  }
+  acc = warp_max(acc);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < RT / 32 ? s[threadIdx.x] : 0.0;
+    v = warp_max(v);
+    if (threadIdx.x == 0) red[blockIdx.x] = v;
+  }
+}
+
 template <int OP>
 __global__ void finish_kernel(double* red, double* out) {
   __shared__ double s[RB / 32];
@@ -205,6 +226,14 @@ cudaError_t finish_sum(double* red, double* out_dev, cudaStream_t st) {
 cudaError_t max_abs_rows(const double* r, int64_t n, int stride_valid, double* red, cudaStream_t st) {
   (void)stride_valid;
   reduce_kernel<2><<<RB, RT, 0, st>>>(r, nullptr, n, red);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t max_abs_unweighted(const double* r, int64_t n_pts, int ne, const double* rho, double w, double* red,
+                               double* out_dev, cudaStream_t st) {
+  max_unweighted_kernel<<<RB, RT, 0, st>>>(r, rho, n_pts * ne, ne, w, red);
+  count_launch();
+  finish_kernel<2><<<1, RB, 0, st>>>(red, out_dev);
   count_launch();
   return cudaGetLastError();
 }

@@ -83,6 +83,7 @@ class gn_step_info(ctypes.Structure):
         ("status", ctypes.c_int),
         ("ms_phase", ctypes.c_double * 8),
         ("momentum", ctypes.c_double),
+        ("max_abs_res", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -132,6 +133,7 @@ EXPORTS = {
     "gn_step_graph": (ctypes.c_int, [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(gn_step_info)]),
     "gn_batch_capture_graph": (ctypes.c_int, [_P, _P]),
     "gn_batch_graph_step": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "gn_test_bounded_waits": (ctypes.c_int, [ctypes.c_ulonglong, ctypes.c_int]),
     "gn_kernel_launches": (ctypes.c_int64, []),
     "gn_last_error_detail": (ctypes.c_char_p, []),
     "gn_error_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -259,6 +261,8 @@ class GNProblem:
         kw.setdefault("norm_field", getattr(w, "norm_field", None))
         kw.setdefault("norm_deriv", getattr(w, "norm_deriv", None))
         kw.setdefault("output_map", getattr(w, "output_map", 0))
+        kw.setdefault("c_bnd", getattr(w, "c_bnd", 1.0))
+        kw.setdefault("c_norm_w", getattr(w, "c_norm_w", 1.0))
         for k, dflt in (("y_relu", None), ("c_relu", 1.0), ("relu_bound", 0.0), ("relu_sign", 1)):
             kw.setdefault(k, getattr(w, k, dflt))
         return cls(w.equation, w.widths, w.y, w.y_bnd if w.y_bnd.size else None, w.rho, y_norm=w.y_norm,

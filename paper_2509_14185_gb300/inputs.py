@@ -113,6 +113,8 @@ class Workload:
     y_norm: tuple = (1.0, 0.0)
     c_norm: float = 1.0
     rho: Optional[np.ndarray] = None
+    c_bnd: float = 1.0                   # weight of the wall loss
+    c_norm_w: float = 1.0                # weight of the normalisation row
     y_inf: Optional[np.ndarray] = None   # (d, n_inf) decay points of the data loss, or None
     c_inf: float = 1.0
     norm_field: Optional[int] = None     # normalisation on another field / on d/dy1 (None: the
@@ -274,6 +276,14 @@ def small_case(equation: int, widths: Sequence[int], n_pts: int, n_bnd: int = 0,
     if lam is None:
         lam = {BURGERS: 0.5, CCF: 0.6057, IPM: 1.0 / 0.9723, BOUSSINESQ: 1.0 / 1.0863 + 1.0}[equation]
     return _wl(f"small_{EQUATION_NAMES[equation]}", equation, widths, y, yb, lam, seed, m=m)
+
+
+def weighted(w: Workload, seed: int = 31) -> Workload:
+    """The same workload with non-unit loss weights: per-point weights rho ~ U[0.25, 4] and
+    wall / normalisation weights 2.75 / 0.35 (the paper's d0 loss carries a weight per point;
+    its data loss a coefficient per constraint)."""
+    return dataclasses.replace(w, name=w.name + "_weighted", rho=0.25 + 3.75 * uniform(seed, w.n_pts),
+                               c_bnd=2.75, c_norm_w=0.35)
 
 
 WORKLOADS = {

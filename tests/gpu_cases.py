@@ -18,6 +18,7 @@ TOL = 1e-12
 
 def oracle_problem(w):
     return Pb.Problem(w.equation, w.widths, w.y, w.y_bnd if w.y_bnd.size else None, w.rho,
+                      c_bnd=getattr(w, "c_bnd", 1.0), c_norm_w=getattr(w, "c_norm_w", 1.0),
                       y_norm=w.y_norm, c_norm=w.c_norm, hilbert_m=w.hilbert_m,
                       y_inf=getattr(w, "y_inf", None), c_inf=getattr(w, "c_inf", 1.0),
                       norm_field=getattr(w, "norm_field", None), norm_deriv=getattr(w, "norm_deriv", None),
@@ -66,3 +67,8 @@ CASES = {
 def small(name, seed=11):
     eq, widths, n, nb, m = CASES[name]
     return I.small_case(eq, widths, n, n_bnd=nb, seed=seed, m=m)
+
+
+def small_weighted(name, seed=11):
+    """The same case with non-uniform rho and non-unit wall and normalisation weights."""
+    return I.weighted(small(name, seed))

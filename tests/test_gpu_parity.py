@@ -8,7 +8,8 @@ import numpy as np
 import pytest
 import torch
 
-from tests.gpu_cases import (CASES, TOL, col_rel, dev, gpu_problem, host, oracle_problem, rel, small)
+from tests.gpu_cases import (CASES, TOL, col_rel, dev, gpu_problem, host, oracle_problem, rel, small,
+                             small_weighted)
 from oracle import gn as ogn
 
 pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
@@ -16,14 +17,15 @@ pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarnin
 _cache = {}
 
 
-def oracle_rows_jac(name):
-    if name not in _cache:
-        w = small(name)
+def oracle_rows_jac(name, weighted=False):
+    key = (name, weighted)
+    if key not in _cache:
+        w = small_weighted(name) if weighted else small(name)
         p = oracle_problem(w)
         r = p.rows(w.theta, w.lam)
         J = ogn.jacobian(p, w.theta, w.lam)
-        _cache[name] = (w, p, r, J)
-    return _cache[name]
+        _cache[key] = (w, p, r, J)
+    return _cache[key]
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -117,6 +119,8 @@ def test_gn_step(name):
     assert rc == info_o["status"]
     assert info["chol_retries"] == info_o["chol_retries"]
     assert abs(info["loss_before"] - info_o["loss_before"]) <= TOL * info_o["loss_before"]
+    mr = p.max_abs_residual(w.theta, w.lam)      # max |R_k| at the starting point, unweighted
+    assert abs(info["max_abs_res"] - mr) <= TOL * mr
     if rc == 0:
         assert info["alpha"] == info_o["alpha"]
         assert gam == pytest.approx(gam_o, rel=1e-15)
@@ -133,6 +137,42 @@ def test_gn_step(name):
     else:
         np.testing.assert_array_equal(host(theta), w.theta)
         assert lam == w.lam and gam == pytest.approx(gam_o, rel=1e-15)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_weighted_rows_jacobian_gradient_step(name):
+    """Non-uniform point weights rho and non-unit wall and normalisation weights (the paper's
+    d0 loss weights each point; its data loss a coefficient per constraint): r~, J~ per column,
+    the adjoint gradient and one GN step against the oracle, whose weights are pinned to the
+    paper's loss on the CPU."""
+    w, p, r_o, J_o = oracle_rows_jac(name, weighted=True)
+    assert w.rho is not None and w.c_bnd != 1.0 and w.c_norm_w != 1.0
+    prob = gpu_problem(w)
+    r, loss = prob.residual(dev(w.theta), w.lam)
+    assert rel(host(r), r_o) <= TOL
+    assert abs(loss - 0.5 * np.dot(r_o, r_o)) <= TOL * 0.5 * np.dot(r_o, r_o)
+    J = host(prob.jacobian(dev(w.theta), w.lam))
+    assert rel(J, J_o) <= TOL
+    assert col_rel(J, J_o, floor=1e-300) <= TOL
+    g = host(prob.gradient(dev(w.theta), w.lam))
+    assert rel(g, J_o.T @ r_o) <= TOL
+    th_o, lam_o, gam_o, info_o = ogn.gn_step(p, w.theta, w.lam, w.gamma)
+    theta = dev(w.theta)
+    rc, lam, gam, info = prob.gn_step(theta, w.lam, w.gamma)
+    assert rc == info_o["status"]
+    assert abs(info["loss_before"] - info_o["loss_before"]) <= TOL * info_o["loss_before"]
+    mr = p.max_abs_residual(w.theta, w.lam)      # unweighted although rho is not 1
+    assert abs(info["max_abs_res"] - mr) <= TOL * mr
+    tg = dev(w.theta)
+    rc_g, _, _, info_g = prob.gn_step_graph(tg, w.lam, w.gamma)
+    assert rc_g == rc and info_g["max_abs_res"] == info["max_abs_res"]
+    if rc == 0:
+        assert info["alpha"] == info_o["alpha"]
+        d_gpu = np.concatenate([w.theta - host(theta), [w.lam - lam]])
+        d_o = np.concatenate([w.theta - th_o, [w.lam - lam_o]])
+        cond = np.linalg.cond(info_o["G"] + info_o["gamma_used"] * np.eye(len(d_o)))
+        assert rel(d_gpu, d_o) <= max(TOL, 1e-15 * cond)
+    prob.close()
 
 
 def test_autograd_function_backward():

@@ -5,9 +5,10 @@ all device memory through its own allocator, loops that must avoid the
 synchronisation an allocation may imply, plug-ins that only receive device
 pointers).  Its scratch is a fixed device array in the library image, so the
 test checks that two calls in a row (different sizes and data, same shared
-scratch) each match the handle-based gn_gram gradient, and that a size beyond
-the array is rejected.  The file is named to be collected last; it passes
-alone in a fresh process and after the other tests.
+scratch) each match the handle-based gn_gram gradient and J^T r formed on the
+host in FP64, and that a size beyond the array is rejected.  The file is named
+to be collected last; it passes alone in a fresh process and after the other
+tests.
 """
 import ctypes
 
@@ -50,6 +51,9 @@ def test_noalloc_jtr_matches_gram_gradient_twice():
         got = g.cpu().numpy()
         assert np.all(np.isfinite(got))
         assert np.max(np.abs(got - ref)) <= TOL * np.max(np.abs(ref))
+        # and against J^T r formed on the host in FP64 from the same buffers
+        host_ref = Jb[:, :Pp].cpu().numpy().T @ r.cpu().numpy()
+        assert np.max(np.abs(got - host_ref)) <= TOL * np.max(np.abs(host_ref))
     prob.close()
 
 
