@@ -24,13 +24,17 @@
  *     matrix W_l (out_l x in_l, row-major) followed by the bias b_l (out_l).
  *     P = sum_l (in_l*out_l + out_l).  lambda is passed separately; the
  *     Jacobian has P' = P + 1 columns and column P is d/d lambda.
- *   - Rows: r~ has n_rows = n_pts * N_E + n_bnd + 1 entries, in the order
- *     (interior point i, equation k) at row i*N_E + k, then the wall rows,
- *     then the normalisation row.  Rows are weighted so that
+ *   - Rows: r~ has n_rows = n_pts * N_E + n_d1 * N_E * d + n_d2 * N_E * d^2
+ *     + n_bnd + n_inf + n_relu + 1 entries, in the order (interior point i,
+ *     equation k) at row i*N_E + k, then the d1 rows (point, k, i), the d2
+ *     rows (point, k, i, j), the wall rows, the decay rows, the bound rows,
+ *     and the normalisation row last.  Rows are weighted so that
  *     h = 1/2 |r~|^2 = (1/(n_pts N_E)) sum_i rho_i sum_k R_k(y_i)^2
+ *                      + c_d1 L_d1 + c_d2 L_d2
  *                      + (c_bnd/n_bnd) sum_b Psi(y_b)^2
+ *                      + c_inf sum Phi_A0(y)^2 + c_relu sum relu(...)^2
  *                      + c_norm_w (Phi_A0(y_norm) - c_norm)^2,
- *     i.e. the paper's d0 equation loss plus its data loss ("Training Loss").
+ *     i.e. the paper's equation loss plus its data loss ("Training Loss").
  *     Then grad h = J~^T r~ and the Gauss-Newton matrix is G = J~^T J~.
  */
 #ifndef GN_H_
@@ -143,6 +147,22 @@ typedef struct gn_problem {
   double c_relu;             /* weight of the bound rows */
   double relu_bound;         /* the bound b on the constrained field */
   int relu_sign;             /* s: >= 0 an upper bound (Phi_A0 <= b), < 0 a lower bound (Phi_A0 >= b) */
+  int64_t n_d1;              /* points of the d1 derivative loss (Methods, "Training Loss": the
+                                residuals' first y-derivatives, its own batch Y_1): rows
+                                sqrt(2 c_d1 rho / (n_d1 N_E d)) d_{y_i} R_k(y), point-major, then k,
+                                then i, placed after the interior rows; 0: none.  For CCF the
+                                velocity is the discrete Hilbert operator differentiated in the
+                                collocation point (node values fixed).  Not with fourier_m > 0,
+                                output_map = 1 or a second stage (GN_ERR_UNSUPPORTED). */
+  const double* y_d1;        /* device, SoA [d][n_d1]. Borrowed: must stay valid until gn_destroy. */
+  const double* rho_d1;      /* device [n_d1] point weights rho, or NULL for all ones. Borrowed. */
+  double c_d1;               /* coefficient c_d1 of the d1 loss */
+  int64_t n_d2;              /* points of the d2 derivative loss: rows sqrt(2 c_d2 rho / (n_d2 N_E d^2))
+                                d_{y_i} d_{y_j} R_k(y) for every ordered pair (i, j) (the mixed pair
+                                twice in 2D, as the paper's double sum counts it), after the d1 rows */
+  const double* y_d2;        /* device, SoA [d][n_d2]. Borrowed. */
+  const double* rho_d2;      /* device [n_d2] point weights, or NULL for all ones. Borrowed. */
+  double c_d2;               /* coefficient c_d2 of the d2 loss */
 } gn_problem;
 
 /* Normalisation row (data loss) per equation, fixed by the library:

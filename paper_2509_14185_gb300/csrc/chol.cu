@@ -324,6 +324,265 @@ __global__ void __launch_bounds__(NB * TPR) potrf_inv_kernel(double* A, int64_t 
   }
 }
 
+// Blocked double-float factor of the diagonal block (the split path's critical-path kernel).
+// Same contract as potrf_inv_kernel<ArithDF>: B = A[k0:k0+kb, k0:k0+kb] - U (lower), scaled
+// B' = D B D by powers of two (D_ii = 2^-sc[i], B'_ii in [1, 4)), factored as B' = L' L'^T with
+// L'^{-1} formed alongside; writes L = D^-1 L' into A, Linv = L'^{-1} D (FP64), L'^{-1} in
+// double-float (LinvDF), the scales, and (with fw) the forward-substitution block
+// y_k = L'^{-1} D w_k.  Rows and columns kb .. 63 are padded with the identity.
+//
+// The same LDL^T elimination as potrf_inv_kernel (S: unscaled columns L_unit D; Y = L_unit^{-1}),
+// reordered into four 16-column sub-panels p so that only a 16-step chain is latency-bound:
+//  (a) one warp sweeps the 16 x 16 diagonal sub-block column by column (S and Y_pp = its
+//      unit-lower inverse share registers, as in the unblocked kernel; the pivots' reciprocals
+//      are kept);
+//  (b) every thread then forms, into registers: the sub-panel rows below, S21 = B21 Y_pp^T,
+//      with T21 = S21 diag(1/d); and the sub-panel's own Y rows for the earlier columns,
+//      Y_p,<c0 <- Y_pp Y_p,<c0 (the rows' share of the elimination within the sub-panel);
+//  (c) the trailing rank-16 update of the rows below: S22 -= T21 S21^T on the lower triangle,
+//      and Y_below -= T21 Y_p on the columns < c0 + 16.
+// Each product is the same double-float arithmetic (about 48 significant bits) as the
+// unblocked sweep; only the order of the updates changes.  1024 threads, one CTA: the
+// phases (b) and (c) give most threads one or two outputs, each a 16-term double-float dot
+// product summed in two interleaved partial sums (two dependent chains of 8).
+constexpr int kPbThreads = 1024;
+constexpr int kPbB = 16;                       // sub-panel width
+constexpr int kPbLd = NB + 1;                  // row stride of the shared S and Y (DF elements)
+constexpr size_t kPbSmem = (size_t)(2 * NB * kPbLd + (NB - kPbB) * kPbB + 4 * kPbB + 2 * NB) * sizeof(DF) +
+                           (size_t)(NB + 4) * sizeof(int);
+
+__global__ void __launch_bounds__(kPbThreads) potrf_blk_kernel(double* A, int64_t lda, int64_t k0, int kb,
+                                                               const float2* __restrict__ U, int64_t ldu,
+                                                               double* Linv, float2* LinvDF, int* scOut,
+                                                               const double* fw, double* fy, float2* fyDF,
+                                                               int* flag) {
+  using AR = ArithDF;
+  using T = DF;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* Sm = reinterpret_cast<T*>(smraw);                 // [NB][kPbLd] S (lower, diagonal included)
+  T* Ym = Sm + NB * kPbLd;                             // [NB][kPbLd] Y (lower, unit diagonal)
+  T* Tm = Ym + NB * kPbLd;                             // [NB - 16][16] T21 of the current sub-panel
+  T* colbuf = Tm + (NB - kPbB) * kPbB;                 // [2][16] the sweep's column j of S
+  T* rowbuf = colbuf + 2 * kPbB;                       // [2][16] the sweep's row j of Y
+  T* rd = rowbuf + 2 * kPbB;                           // [NB] 1 / d_j
+  T* rsd = rd + NB;                                    // [NB] 1 / sqrt(d_j)
+  int* sc = reinterpret_cast<int*>(rsd + NB);          // [NB] scales
+  int* bad = sc + NB;
+  auto S = [&](int i, int c) -> T& { return Sm[i * kPbLd + c]; };
+  auto Y = [&](int i, int c) -> T& { return Ym[i * kPbLd + c]; };
+  if (*flag) return;
+  const int t = threadIdx.x;
+  if (t < NB) {
+    int e = 0;
+    if (t < kb) {
+      double d = A[(k0 + t) * lda + k0 + t];
+      if (U) {
+        const float2 u = U[(k0 + t) * ldu + k0 + t];
+        d -= (double)u.x + (double)u.y;
+      }
+      if (d > 0.0 && isfinite(d)) e = ilogb(d) >> 1;   // floor(log2(d) / 2)
+    }
+    sc[t] = e;
+  }
+  if (t == 0) *bad = 0;
+  // load S = D (A - U) D on the lower triangle (identity on the padding), Y = I; the block's
+  // global loads are all issued before the scales are known
+  constexpr int kPer = NB * NB / kPbThreads;
+  double av[kPer];
+  float2 uv[kPer];
+#pragma unroll
+  for (int m = 0; m < kPer; m++) {
+    const int idx = t + m * kPbThreads, i = idx / NB, c = idx % NB;
+    const bool in = c <= i && i < kb;
+    av[m] = in ? A[(k0 + i) * lda + k0 + c] : 0.0;
+    uv[m] = (in && U) ? U[(k0 + i) * ldu + k0 + c] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < kPer; m++) {
+    const int idx = t + m * kPbThreads, i = idx / NB, c = idx % NB;
+    if (c > i) continue;
+    T v = (i == c) ? AR::one() : AR::zero();
+    if (i < kb) {
+      const float2 u = uv[m];
+      v = AR::load_scaled(av[m], U ? &u : nullptr, -(sc[i] + sc[c]));
+    }
+    S(i, c) = v;
+    Y(i, c) = (i == c) ? AR::one() : AR::zero();
+  }
+  __syncthreads();
+
+  for (int p = 0; p < NB / kPbB; p++) {
+    const int c0 = p * kPbB;
+    // ---- (a) the 16 x 16 diagonal sub-block, by the first 256 threads (8 warps, one named
+    //      barrier per column): thread (r, cl) holds element (c0 + r, c0 + cl), S until column
+    //      cl is published, then Y.  One element per thread keeps each step's dependent chain
+    //      (pivot reciprocal, multiplier, one fused update) short in every warp.
+    if (t < kPbB * kPbB) {
+      const int r = t / kPbB, cl = t % kPbB, i = c0 + r;
+      T X = (cl <= r) ? S(i, c0 + cl) : AR::zero();
+      bool ok = true;
+      for (int jj = 0; jj < kPbB; jj++) {
+        T* cb = colbuf + (jj & 1) * kPbB;
+        T* rb = rowbuf + (jj & 1) * kPbB;
+        if (cl == jj && r >= jj) {        // the owner of column jj publishes it
+          cb[r] = X;
+          S(i, c0 + jj) = X;
+          X = AR::zero();                 // from here on the register accumulates Y[i][c0 + jj]
+        }
+        if (r == jj && cl < jj) rb[cl] = X;
+        asm volatile("bar.sync 1, %0;" ::"r"(kPbB * kPbB) : "memory");
+        const T d = cb[jj];
+        if (!AR::positive(d)) {   // every thread reads the same pivot: the exit is uniform
+          ok = false;
+          break;
+        }
+        const T rcpd = AR::rcp(d);
+        if (t == 0) rd[c0 + jj] = rcpd;
+        if (r > jj && cl <= r) {
+          const T a = AR::mul(cb[r], rcpd);
+          const T v = (cl > jj) ? cb[cl] : (cl == jj ? AR::one() : rb[cl]);
+          X = AR::fnma(X, a, v);
+        }
+      }
+      if (!ok) {
+        if (t == 0) *bad = 1;
+      } else if (cl < r) {
+        Y(i, c0 + cl) = X;
+      }
+    }
+    __syncthreads();
+    if (*bad) {
+      if (t == 0) atomicExch(flag, 1);
+      return;
+    }
+    // ---- (b) into registers: S21 = B21 Y_pp^T (rows below, sub-panel columns) and the
+    //      sub-panel rows' Y on the earlier columns, Y_pp Y_old
+    const int nb_rows = NB - c0 - kPbB;                // rows below the sub-panel
+    const int n21 = nb_rows * kPbB, nya = kPbB * c0;
+    constexpr int kRegs = (3 * kPbB * kPbB + kPbThreads - 1) / kPbThreads;   // outputs per thread, at most
+    T vb[kRegs];
+#pragma unroll
+    for (int q = 0; q < kRegs; q++) {
+      const int o = t + q * kPbThreads;
+      vb[q] = AR::zero();
+      if (o < n21) {
+        const int i = c0 + kPbB + o / kPbB, j = o % kPbB;
+        T acc0 = AR::zero(), acc1 = AR::zero();
+        for (int c = 0; c <= j; c += 2) {   // Y_pp[j][c] (unit diagonal)
+          const T y0 = (c == j) ? AR::one() : Y(c0 + j, c0 + c);
+          acc0 = AR::fnma(acc0, S(i, c0 + c), y0);
+          if (c + 1 <= j) {
+            const T y1 = (c + 1 == j) ? AR::one() : Y(c0 + j, c0 + c + 1);
+            acc1 = AR::fnma(acc1, S(i, c0 + c + 1), y1);
+          }
+        }
+        const T acc = AR::add(acc0, acc1);
+        vb[q] = {-acc.h, -acc.l};
+      } else if (o < n21 + nya) {
+        const int oo = o - n21;
+        const int i = c0 + oo / c0, c = oo % c0;
+        T acc0 = AR::zero(), acc1 = AR::zero();
+        for (int j = c0; j <= i; j += 2) {  // sum_j Y_pp[i][j] Y_old[j][c]
+          const T y0 = (j == i) ? AR::one() : Y(i, j);
+          acc0 = AR::fnma(acc0, y0, Y(j, c));
+          if (j + 1 <= i) {
+            const T y1 = (j + 1 == i) ? AR::one() : Y(i, j + 1);
+            acc1 = AR::fnma(acc1, y1, Y(j + 1, c));
+          }
+        }
+        const T acc = AR::add(acc0, acc1);
+        vb[q] = {-acc.h, -acc.l};
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kRegs; q++) {
+      const int o = t + q * kPbThreads;
+      if (o < n21) {
+        const int ii = o / kPbB, j = o % kPbB;
+        S(c0 + kPbB + ii, c0 + j) = vb[q];
+        Tm[ii * kPbB + j] = AR::mul(vb[q], rd[c0 + j]);
+      } else if (o < n21 + nya) {
+        const int oo = o - n21;
+        Y(c0 + oo / c0, oo % c0) = vb[q];
+      }
+    }
+    __syncthreads();
+    if (nb_rows == 0) break;
+    // ---- (c) trailing rank-16 update of the rows below: S22 -= T21 S21^T (lower), and
+    //      Y_below[:, < c0 + 16] -= T21 Y_p
+    const int cw = c0 + kPbB;                          // Y columns touched
+    const int nS = nb_rows * (nb_rows + 1) / 2, nY = nb_rows * cw;
+    for (int o = t; o < nS + nY; o += kPbThreads) {
+      if (o < nS) {
+        // lower-triangle index o -> (ii, cc), cc <= ii (o < 1176: the float root is exact enough)
+        int ii = (int)((sqrtf(8.0f * (float)o + 1.0f) - 1.0f) * 0.5f);
+        while ((ii + 1) * (ii + 2) / 2 <= o) ii++;
+        while (ii * (ii + 1) / 2 > o) ii--;
+        const int cc = o - ii * (ii + 1) / 2;
+        const int i = c0 + kPbB + ii, c = c0 + kPbB + cc;
+        T acc0 = S(i, c), acc1 = AR::zero();
+#pragma unroll
+        for (int j = 0; j < kPbB; j += 2) {
+          acc0 = AR::fnma(acc0, Tm[ii * kPbB + j], S(c, c0 + j));
+          acc1 = AR::fnma(acc1, Tm[ii * kPbB + j + 1], S(c, c0 + j + 1));
+        }
+        S(i, c) = AR::add(acc0, acc1);
+      } else {
+        const int oo = o - nS;
+        const int ii = oo / cw, c = oo % cw;
+        const int i = c0 + kPbB + ii;
+        T acc0 = Y(i, c), acc1 = AR::zero();
+        const int j0 = (c > c0) ? c - c0 : 0;          // Y[c0 + j][c] = 0 for c > c0 + j
+        for (int j = j0; j < kPbB; j += 2) {
+          const T y0 = (c0 + j == c) ? AR::one() : Y(c0 + j, c);
+          acc0 = AR::fnma(acc0, Tm[ii * kPbB + j], y0);
+          if (j + 1 < kPbB) acc1 = AR::fnma(acc1, Tm[ii * kPbB + j + 1], Y(c0 + j + 1, c));
+        }
+        Y(i, c) = AR::add(acc0, acc1);
+      }
+    }
+    __syncthreads();
+  }
+  // ---- outputs: L' = S diag(1/sqrt(d)), L'^{-1} = diag(1/sqrt(d)) Y, unscaled by D
+  if (t < NB) rsd[t] = AR::rsqrt(S(t, t));
+  __syncthreads();
+  double* Lk = Linv + (k0 / NB) * NB * NB;
+  float2* Lf2 = LinvDF ? LinvDF + (k0 / NB) * NB * NB : nullptr;
+  for (int idx = t; idx < NB * NB; idx += kPbThreads) {
+    const int i = idx / NB, c = idx % NB;
+    const bool in = i < kb && c <= i;
+    T v = AR::zero();
+    if (in) v = (c == i) ? rsd[i] : AR::mul(Y(i, c), rsd[i]);   // L'^{-1}[i][c] = Y[i][c] / sqrt(d_i)
+    Lk[idx] = in ? AR::store_scaled(v, -sc[c]) : 0.0;
+    if (Lf2) Lf2[idx] = make_float2(v.h, v.l);                    // without D, for the panel solve
+    if (in) A[(k0 + i) * lda + k0 + c] = AR::store_scaled(AR::mul(S(i, c), rsd[c]), sc[i]);
+  }
+  if (Lf2 && t < NB) scOut[(k0 / NB) * NB + t] = sc[t];
+  if (fw) {
+    // forward substitution, block k: y_k = L'^{-1} (D w_k); 16 threads per row, combined by shuffles
+    constexpr int kTpr = kPbThreads / NB;
+    const int i = t / kTpr, g = t % kTpr;
+    T acc = AR::zero();
+    if (i < kb) {
+      for (int c = g; c <= i; c += kTpr) {
+        const T v = (c == i) ? rsd[i] : AR::mul(Y(i, c), rsd[i]);
+        acc = AR::add(acc, AR::mul(v, AR::load_scaled(fw[k0 + c], nullptr, -sc[c])));
+      }
+    }
+#pragma unroll
+    for (int o = 1; o < kTpr; o <<= 1) {
+      const T other = {__shfl_xor_sync(0xffffffffu, acc.h, o), __shfl_xor_sync(0xffffffffu, acc.l, o)};
+      acc = AR::add(acc, other);
+    }
+    if (g == 0 && i < kb) {
+      fy[k0 + i] = AR::store_scaled(acc, 0);
+      fyDF[i] = make_float2(acc.h, acc.l);
+    }
+  }
+}
+
 // Panel solve L21 = A21 Linv_k^T in FP64 on the CUDA cores (the FP64 path), in
 // place, for the rows [k1, n) of the panel columns [k0, k0 + kb).  32 rows per
 // CTA, 128 threads, 4 x 4 outputs per thread (rows ty + 8a, columns tx + 16b);
@@ -387,18 +646,20 @@ __global__ void __launch_bounds__(128) panel_solve_kernel(double* A, int64_t lda
 // The split path's panel solve in double-float arithmetic on the FP32 pipe
 // (about 48 significant bits, the precision of U and of the split GEMM):
 // L21 = (A21 - U21) D L'^{-T}, with L'^{-1} (LkDF) and the power-of-two scales
-// D = diag(2^-sc) from the diagonal factor.  32 rows per CTA, 256 threads, 2 x 4 outputs
-// per thread (rows ty + 16a, columns tx + 16b), the same K segments as the FP64 kernel;
+// D = diag(2^-sc) from the diagonal factor.  16 rows per CTA (enough CTAs for about three per
+// SM, whose warps hide each other's latency), 256 threads, 1 x 4 outputs per thread (row ty,
+// columns tx + 16b), the same K segments as the FP64 kernel;
 // each product is the exact FP32 product of the high parts plus the cross
 // terms, its high part added exactly (TwoSum) and the low parts accumulated
 // in FP32, renormalised at the end.  Writes L21 in FP64 and its S BF16 slices
 // into the strip operand (row r at r - row_base, columns kofs + j), with each
 // row's own exponent over this panel's 64 columns in eout[r - row_base] (the
 // strip operand keeps one exponent array per panel).
-constexpr size_t kPanelDFSmem = (size_t)(kPanelRows + NB) * (NB + 1) * sizeof(float2);
-constexpr int kPanelDFThreads = 256;                       // 16 x 16: 2 rows x 4 columns per thread
+constexpr int kPanelDFRowsCTA = 16;                       // rows per CTA: about three CTAs per SM
+constexpr size_t kPanelDFSmem = (size_t)(kPanelDFRowsCTA + NB) * (NB + 1) * sizeof(float2);
+constexpr int kPanelDFThreads = 256;                       // 16 x 16: 1 row x 4 columns per thread
 constexpr int kPanelDFRowStride = kPanelDFThreads / 16;    // rows ty + 16 a
-constexpr int kPanelDFRows = kPanelRows / kPanelDFRowStride;
+constexpr int kPanelDFRows = kPanelDFRowsCTA / kPanelDFRowStride;
 
 template <int S>
 __global__ void __launch_bounds__(kPanelDFThreads) panel_df_kernel(double* A, int64_t lda, int64_t k0, int kb, int64_t k1,
@@ -409,36 +670,57 @@ __global__ void __launch_bounds__(kPanelDFThreads) panel_df_kernel(double* A, in
                                                        const float2* __restrict__ fyDF, double* fw, const int* flag) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float2 (*As)[NB + 1] = reinterpret_cast<float2 (*)[NB + 1]>(smraw);
-  float2 (*Lt)[NB + 1] = As + kPanelRows;   // Lt[q][j] = L'^{-1}[j][q]
+  float2 (*Lt)[NB + 1] = As + kPanelDFRowsCTA;   // Lt[q][j] = L'^{-1}[j][q]
   __shared__ float colscale[NB];   // 2^-sc[q]; 0 marks a scale outside FP32's range
   if (*flag) return;
   const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-  const int64_t rb = k1 + (int64_t)blockIdx.x * kPanelRows;
+  const int64_t rb = k1 + (int64_t)blockIdx.x * kPanelDFRowsCTA;
+  // every global load of the CTA is issued before any is consumed (the panel is latency-bound):
+  // L'^{-1} (16 values per thread) and the panel rows A, U (8 values per thread)
+  constexpr int kLtPer = NB * NB / kPanelDFThreads, kAsPer = kPanelDFRowsCTA * NB / kPanelDFThreads;
+  float2 ltv[kLtPer];
+  double av[kAsPer];
+  float2 uv[kAsPer];
+#pragma unroll
+  for (int m = 0; m < kLtPer; m++) {
+    const int idx = t + m * kPanelDFThreads, j = idx / NB, q = idx % NB;
+    ltv[m] = (j < kb && q < kb) ? LkDF[j * NB + q] : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int m = 0; m < kAsPer; m++) {
+    const int idx = t + m * kPanelDFThreads, rr = idx / NB, q = idx % NB;
+    const int64_t r = rb + rr;
+    const bool in = r < n && q < kb;
+    av[m] = in ? A[r * lda + k0 + q] : 0.0;
+    uv[m] = (in && U) ? U[r * ldu + k0 + q] : make_float2(0.f, 0.f);
+  }
   if (t < NB) colscale[t] = (t < kb && sck[t] >= -120 && sck[t] <= 120) ? ldexpf(1.0f, -sck[t]) : 0.0f;
-  for (int idx = t; idx < NB * NB; idx += blockDim.x) {
-    const int j = idx / NB, q = idx % NB;
-    Lt[q][j] = (j < kb && q < kb) ? LkDF[j * NB + q] : make_float2(0.f, 0.f);
+#pragma unroll
+  for (int m = 0; m < kLtPer; m++) {
+    const int idx = t + m * kPanelDFThreads;
+    Lt[idx % NB][idx / NB] = ltv[m];
   }
   __syncthreads();
-  for (int idx = t; idx < kPanelRows * NB; idx += blockDim.x) {
-    const int rr = idx / NB, q = idx % NB;
+#pragma unroll
+  for (int m = 0; m < kAsPer; m++) {
+    const int idx = t + m * kPanelDFThreads, rr = idx / NB, q = idx % NB;
     const int64_t r = rb + rr;
     float h = 0.f, l = 0.f;
     if (r < n && q < kb && colscale[q] == 0.0f) {   // extreme scale: subtract and scale in FP64
-      double a = A[r * lda + k0 + q];
+      double a = av[m];
       if (U) {
-        const float2 u = U[r * ldu + k0 + q];
+        const float2 u = uv[m];
         a -= (double)u.x + (double)u.y;
       }
       a *= p2(-sck[q]);
       h = __double2float_rn(a);
       l = __double2float_rn(a - (double)h);
     } else if (r < n && q < kb) {
-      const double a = A[r * lda + k0 + q];
+      const double a = av[m];
       h = __double2float_rn(a);
       l = __double2float_rn(a - (double)h);
       if (U) {   // (h, l) -= (u.x, u.y): TwoSum of the high parts, low parts added
-        const float2 u = U[r * ldu + k0 + q];
+        const float2 u = uv[m];
         const float s1 = __fsub_rn(h, u.x);
         const float bb = __fsub_rn(s1, h);
         const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s1, bb)), __fsub_rn(-u.x, bb));
@@ -633,12 +915,22 @@ cudaError_t launch_potrf(double* A, int64_t lda, int64_t k0, int kb, const float
   return cudaGetLastError();
 }
 
+cudaError_t launch_potrf_blk(double* A, int64_t lda, int64_t k0, int kb, const float2* U, int64_t ldu,
+                             double* Linv, float2* LinvDF, int* scOut, const double* fw, double* fy, float2* fyDF,
+                             int* flag, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(potrf_blk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPbSmem);
+  if (e != cudaSuccess) return e;
+  potrf_blk_kernel<<<1, kPbThreads, kPbSmem, st>>>(A, lda, k0, kb, U, ldu, Linv, LinvDF, scOut, fw, fy, fyDF, flag);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_panel(double* A, int64_t lda, int64_t k0, int kb, int64_t k1, int64_t n, const double* Lk,
                          const int* flag, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(panel_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kPanelSmem);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = (n - k1 + kPanelRows - 1) / kPanelRows;
+  const int64_t blocks = (n - k1 + kPanelDFRowsCTA - 1) / kPanelDFRowsCTA;
   if (blocks <= 0) return cudaSuccess;
   panel_solve_kernel<<<(unsigned)blocks, 128, kPanelSmem, st>>>(A, lda, k0, kb, k1, n, Lk, flag);
   count_launch();
@@ -653,7 +945,7 @@ cudaError_t launch_panel_df(double* A, int64_t lda, int64_t k0, int kb, int64_t 
   cudaError_t e = cudaFuncSetAttribute(panel_df_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)kPanelDFSmem);
   if (e != cudaSuccess) return e;
-  const int64_t blocks = (n - k1 + kPanelRows - 1) / kPanelRows;
+  const int64_t blocks = (n - k1 + kPanelDFRowsCTA - 1) / kPanelDFRowsCTA;
   if (blocks <= 0) return cudaSuccess;
   panel_df_kernel<S><<<(unsigned)blocks, kPanelDFThreads, kPanelDFSmem, st>>>(A, lda, k0, kb, k1, n, U, ldu, LkDF, sck,
                                                                   static_cast<__nv_bfloat16*>(op.slices), eout,
@@ -866,7 +1158,7 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
         if (rc) return fail(rc);
       }
       const float2* Uk = (k0 > 0) ? U : nullptr;
-      err = launch_potrf<ArithDF>(A, lda, k0, kb, Uk, n, Linv, LinvDF, scales, b ? w : nullptr, y, yDF, flag, sh);
+      err = launch_potrf_blk(A, lda, k0, kb, Uk, n, Linv, LinvDF, scales, b ? w : nullptr, y, yDF, flag, sh);
       if (err != cudaSuccess) return err;
       const int64_t k1 = k0 + kb;
       if (k1 >= n) break;

@@ -69,8 +69,14 @@ int validate(const gn_problem* p) {
   if (p->fourier_m > 0 && (p->n_layers < 3 || p->widths[2] != 2 * p->fourier_m || !p->fourier_B))
     return GN_ERR_INVALID;
   if (p->precision != GN_PREC_FP64 && (p->n_slices < 1 || p->n_slices > 6)) return GN_ERR_INVALID;
+  if (p->n_d1 < 0 || (p->n_d1 > 0 && !p->y_d1) || !(p->c_d1 >= 0.0)) return GN_ERR_INVALID;
+  if (p->n_d2 < 0 || (p->n_d2 > 0 && !p->y_d2) || !(p->c_d2 >= 0.0)) return GN_ERR_INVALID;
+  // the derivative rows' kernel covers tanh networks with a linear output layer
+  if ((p->n_d1 > 0 || p->n_d2 > 0) && (p->fourier_m > 0 || p->output_map == 1)) return GN_ERR_UNSUPPORTED;
   return GN_OK;
 }
+
+int64_t dpow(int d, int k) { return k == 0 ? 1 : (k == 1 ? d : (int64_t)d * d); }
 
 template <typename T>
 cudaError_t dalloc(T** p, size_t count) {
@@ -83,7 +89,8 @@ void free_all(gn_handle* h) {
   void* ptrs[] = {h->ema_ws, h->wt, h->theta_t, h->r, h->J, h->G, h->A, h->Linv, h->g, h->delta, h->vtmp, h->red,
                   h->flag, h->gpart, h->kf, h->dcoef, h->snode, h->gnode, h->Jg, h->ug, h->sU, h->tnode,
                   h->split_ws, h->chol_ws, h->base_int, h->base_wall, h->base_norm, h->base_node, h->fourierW,
-                  h->base_inf, h->base_relu};
+                  h->base_inf, h->base_relu, h->kd[0], h->kd[1], h->dd[0], h->dd[1], h->ugd[0], h->ugd[1],
+                  h->sUd[0], h->sUd[1]};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->hpin) cudaFreeHost(h->hpin);
@@ -99,6 +106,16 @@ void destroy_side(gn_handle* h) {
 
 // Device copy of the normalisation point: red[512 .. 513].
 double* norm_point(gn_handle* h) { return h->red + 512; }
+
+// Rows of the derivative-loss batches (ord 1: d1, 2: d2) and the first of each; the wall,
+// decay and bound rows follow them.
+int64_t n_drows(const gn_handle* h, int ord) {
+  return (ord == 1 ? h->p.n_d1 : h->p.n_d2) * h->ne * dpow(h->d, ord);
+}
+int64_t drow0(const gn_handle* h, int ord) {
+  return h->p.n_pts * h->ne + (ord == 2 ? n_drows(h, 1) : 0);
+}
+int64_t edge_row0(const gn_handle* h) { return h->p.n_pts * h->ne + n_drows(h, 1) + n_drows(h, 2); }
 
 }  // namespace
 
@@ -148,7 +165,7 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
       b.ystride = h->p.n_bnd;
       b.wscale = rs * sqrt(2.0 * h->p.c_bnd / (double)h->p.n_bnd);
       b.base = h->staged ? h->base_wall : nullptr;
-      b.row0 = n * h->ne;
+      b.row0 = edge_row0(h);
       b.r = ps.r;
       b.J = ps.J;
       b.ldJ = ps.ldJ;
@@ -168,7 +185,7 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
       b.wscale = rs * sqrt(2.0 * h->p.c_inf);
       b.base = h->staged ? h->base_inf : nullptr;
       b.c_norm = 0.0;
-      b.row0 = n * h->ne + h->p.n_bnd;
+      b.row0 = edge_row0(h) + h->p.n_bnd;
       b.r = ps.r;
       b.J = ps.J;
       b.ldJ = ps.ldJ;
@@ -189,7 +206,7 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
       b.base = h->staged ? h->base_relu : nullptr;
       b.c_norm = h->p.relu_bound;
       b.rsign = h->p.relu_sign < 0 ? -1 : 1;
-      b.row0 = n * h->ne + h->p.n_bnd + h->p.n_inf;
+      b.row0 = edge_row0(h) + h->p.n_bnd + h->p.n_inf;
       b.r = ps.r;
       b.J = ps.J;
       b.ldJ = ps.ldJ;
@@ -246,6 +263,13 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
     b.base_ld = 1;
     GN_TRY_CUDA(launch_jet(b, st, nullptr));
     GN_TRY_CUDA(dgemv_n(h->kf, h->Mh, n, h->Mh, h->gnode, h->ug, 0.0, st));
+    // the derivative batches' K part, one coefficient of the series in y at a time
+    for (int od = 1; od <= 2; od++) {
+      const int64_t nd = od == 1 ? h->p.n_d1 : h->p.n_d2;
+      for (int m = 0; nd > 0 && m <= djet_order_y(1, od); m++)
+        GN_TRY_CUDA(dgemv_n(h->kd[od - 1] + (int64_t)m * nd * h->Mh, h->Mh, nd, h->Mh, h->gnode,
+                            h->ugd[od - 1] + (int64_t)m * nd, 0.0, st));
+    }
   }
   // interior points
   {
@@ -269,6 +293,40 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
     b.dcoef = h->dcoef;
     b.sU = h->sU;
     GN_TRY_CUDA(launch_jet(b, st, nullptr));
+  }
+  // derivative-loss rows (d1, d2)
+  for (int od = 1; od <= 2; od++) {
+    const int64_t nd = od == 1 ? h->p.n_d1 : h->p.n_d2;
+    if (nd == 0) continue;
+    JetArgs b = a;
+    b.mode = ps.mode;
+    b.n = nd;
+    b.y = od == 1 ? h->p.y_d1 : h->p.y_d2;
+    b.ystride = nd;
+    b.rho = ps.unweighted ? nullptr : (od == 1 ? h->p.rho_d1 : h->p.rho_d2);
+    const double cd = od == 1 ? h->p.c_d1 : h->p.c_d2;
+    b.wscale = ps.unweighted ? 1.0 : rs * sqrt(2.0 * cd / ((double)nd * h->ne * dpow(h->d, od)));
+    b.base = nullptr;
+    b.row0 = drow0(h, od);
+    b.r = ps.r;
+    b.J = ps.J;
+    b.ldJ = ps.ldJ;
+    b.jrow_lo = ps.jlo;
+    b.jrow_hi = ps.jhi;
+    b.seed = ps.seed;
+    b.ug = h->ugd[od - 1];
+    b.dcoef = h->dd[od - 1];
+    b.sU = h->sUd[od - 1];
+    GN_TRY_CUDA(launch_djet(b, od, st, nullptr));
+    if (h->eq == GN_CCF && ps.mode == MODE_JACOBIAN) {
+      // J[row, :] += sum_m sU_m(row) sum_j' Kd_m[row][j'] Jg[j', :] (one row per point in 1D)
+      const int64_t r0 = b.row0;
+      const int64_t lo = ps.jlo > r0 ? ps.jlo : r0, hi = ps.jhi < r0 + nd ? ps.jhi : r0 + nd;
+      for (int m = 0; hi > lo && m <= od; m++)
+        GN_TRY_CUDA(dgemm(hi - lo, h->Pp, h->Mh, 1.0, h->kd[od - 1] + ((int64_t)m * nd + (lo - r0)) * h->Mh, h->Mh,
+                          true, h->Jg, h->ldJ, false, 1.0, ps.J + (lo - ps.jlo) * ps.ldJ, ps.ldJ, false,
+                          h->sUd[od - 1] + (int64_t)m * nd + (lo - r0), st));
+    }
   }
   if (!side) {
     int rc = edge_rows(st);
@@ -306,6 +364,12 @@ int run_pass(gn_handle* h, const double* theta, double lam, const Pass& ps, doub
     if (h->eq == GN_CCF && n > 0) {
       // t_j' = sum_i Kf[i][j'] c_i (c = seed * w * dR/dU, left in sU), then node pass seeded by t
       GN_TRY_CUDA(dgemv_t_scratch(h->kf, h->Mh, n, h->Mh, h->sU, h->tnode, 0.0, h->vtmp, st));
+      for (int od = 1; od <= 2; od++) {   // the derivative rows' K parts, coefficient by coefficient
+        const int64_t nd = od == 1 ? h->p.n_d1 : h->p.n_d2;
+        for (int m = 0; nd > 0 && m <= od; m++)
+          GN_TRY_CUDA(dgemv_t_scratch(h->kd[od - 1] + (int64_t)m * nd * h->Mh, h->Mh, nd, h->Mh,
+                                      h->sUd[od - 1] + (int64_t)m * nd, h->tnode, 1.0, h->vtmp, st));
+      }
       JetArgs b = a;
       b.kind = KIND_NODE;
       b.mode = MODE_GRADIENT;
@@ -475,7 +539,8 @@ int gn_init(const gn_problem* p, void* cuda_stream, gn_handle** out) {
   net.P = off;
   h->P = off;
   h->Pp = off + 1;
-  h->n_rows = p->n_pts * h->ne + (h->d == 2 ? p->n_bnd : 0) + p->n_inf + p->n_relu + 1;
+  h->n_rows = p->n_pts * h->ne + p->n_d1 * h->ne * dpow(h->d, 1) + p->n_d2 * h->ne * dpow(h->d, 2) +
+              (h->d == 2 ? p->n_bnd : 0) + p->n_inf + p->n_relu + 1;
   h->ldJ = round_up(h->Pp, 16);
   const double jbytes = (double)h->n_rows * h->ldJ * 8.0;
   const double jcap = 32.0 * (1ull << 30);
@@ -517,6 +582,15 @@ int gn_init(const gn_problem* p, void* cuda_stream, gn_handle** out) {
     A(dalloc(&h->ug, p->n_pts));
     A(dalloc(&h->sU, p->n_pts));
     A(dalloc(&h->tnode, h->Mh));
+    for (int od = 1; od <= 2; od++) {
+      const int64_t nd = od == 1 ? p->n_d1 : p->n_d2;
+      if (nd == 0) continue;
+      const int oy = djet_order_y(1, od);
+      A(dalloc(&h->kd[od - 1], (size_t)(oy + 1) * nd * h->Mh));
+      A(dalloc(&h->dd[od - 1], (size_t)(oy + 1) * nd));
+      A(dalloc(&h->ugd[od - 1], (size_t)(oy + 1) * nd));
+      A(dalloc(&h->sUd[od - 1], (size_t)(od + 1) * nd));
+    }
   }
   if (!ok) {
     cudaGetLastError();
@@ -540,6 +614,12 @@ int gn_init(const gn_problem* p, void* cuda_stream, gn_handle** out) {
   double yn[2] = {p->y_norm[0], p->y_norm[1]};
   if (e == cudaSuccess) e = cudaMemcpyAsync(norm_point(h), yn, 2 * sizeof(double), cudaMemcpyHostToDevice, h->st);
   if (e == cudaSuccess && h->eq == GN_CCF) e = hilbert_build(p->y, p->n_pts, h->M, h->kf, h->dcoef, h->snode, h->st);
+  for (int od = 1; od <= 2 && e == cudaSuccess && h->eq == GN_CCF; od++) {
+    const int64_t nd = od == 1 ? p->n_d1 : p->n_d2;
+    if (nd > 0)
+      e = hilbert_series_build(od == 1 ? p->y_d1 : p->y_d2, nd, h->M, djet_order_y(1, od), h->kd[od - 1],
+                               h->dd[od - 1], h->st);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   // the side stream of the wall and normalisation passes (highest priority: a one-CTA pass
   // should not queue behind the interior pass's CTAs)

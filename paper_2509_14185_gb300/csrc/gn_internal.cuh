@@ -176,6 +176,12 @@ struct gn_handle {
   double* base_inf = nullptr;     // [n_inf][base_ld]
   double* base_relu = nullptr;    // [n_relu][base_ld]
   double* base_node = nullptr;    // [Mh] (CCF)
+  // CCF derivative-loss batches (index 0: d1, 1: d2): series of the folded Hilbert rows and of
+  // D in the collocation point, the K part's coefficients at the node values, the row seeds
+  double* kd[2] = {nullptr, nullptr};    // [order_y + 1][n_d][Mh]
+  double* dd[2] = {nullptr, nullptr};    // [order_y + 1][n_d]
+  double* ugd[2] = {nullptr, nullptr};   // [order_y + 1][n_d]
+  double* sUd[2] = {nullptr, nullptr};   // [ord + 1][n_d]
   double* fourierW = nullptr;     // Fourier layer rows [B; B] (2m' x m), when the network has one
 };
 
@@ -211,6 +217,13 @@ void graph_release(gn_handle* h);
 // ---- launchers (host functions implemented in the .cu files) -----------
 cudaError_t launch_transpose_weights(const NetDesc& net, const double* theta, double* wt, cudaStream_t st);
 cudaError_t launch_jet(const JetArgs& a, cudaStream_t st, int64_t* warps_used);
+// derivative-loss rows of order ord (1: d1, 2: d2) at the a.n points (djet.cu); a.row0 is the
+// first row, a.wscale sqrt(2 c_d / (N_d N_E d^ord)).  CCF: a.ug / a.dcoef hold the K part's
+// and D's Taylor coefficients in y ([m][n], m <= order_y), a.sU receives d row / d U_m ([m][n],
+// m <= ord; times the combined seed in gradient mode)
+cudaError_t launch_djet(const JetArgs& a, int ord, cudaStream_t st, int64_t* warps_used);
+// degree in y of the field series of the derivative rows of order ord in d dimensions
+inline int djet_order_y(int d, int ord) { return (d == 1 ? 1 : 2) + ord; }
 int jet_gpart_warps(const NetDesc& net, int d, int nf, int64_t n_max);
 cudaError_t launch_gpart_reduce(const double* gpart, int64_t warps, int64_t ldg, int64_t n,
                                 double* out, int accumulate, cudaStream_t st);
@@ -253,6 +266,10 @@ cudaError_t max_abs_unweighted(const double* r, int64_t n_pts, int ne, const dou
 // CCF Hilbert operator construction and contractions.
 cudaError_t hilbert_build(const double* y, int64_t n, int M, double* kf, double* dcoef, double* snode,
                           cudaStream_t st);
+// Taylor coefficients m = 0..order in the collocation point x of the folded K row and of D:
+// kd[m][i][j'] (n x M/2 each), dd[m][i]
+cudaError_t hilbert_series_build(const double* y, int64_t n, int M, int order, double* kd, double* dd,
+                                 cudaStream_t st);
 
 // Cholesky (FP64, blocked, lower, in place on A row-major) and solves.
 constexpr int kCholNB = 64;

@@ -36,6 +36,10 @@ int gn_set_stage1(gn_handle* h, int n_layers1, const int* widths1, const double*
   if (!h || !widths1 || !theta1 || n_layers1 < 1 || n_layers1 > GN_MAX_LAYERS) return GN_ERR_INVALID;
   if (!(eps > 0.0) || !std::isfinite(eps) || !std::isfinite(lambda)) return GN_ERR_INVALID;
   if (widths1[0] != h->d || widths1[n_layers1] != h->nf) return GN_ERR_INVALID;
+  if (h->p.n_d1 > 0 || h->p.n_d2 > 0) {   // the derivative rows' kernel has no second stage
+    set_detail(__FILE__, __LINE__, "derivative-loss rows with a second stage");
+    return GN_ERR_UNSUPPORTED;
+  }
   for (int l = 1; l < n_layers1; l++)
     if (widths1[l] < 1 || widths1[l] > 256) return GN_ERR_INVALID;
   // the stage-1 network's layout (as gn_init lays out theta)

@@ -68,6 +68,14 @@ class gn_problem(ctypes.Structure):
         ("c_relu", ctypes.c_double),
         ("relu_bound", ctypes.c_double),
         ("relu_sign", ctypes.c_int),
+        ("n_d1", ctypes.c_int64),
+        ("y_d1", ctypes.c_void_p),
+        ("rho_d1", ctypes.c_void_p),
+        ("c_d1", ctypes.c_double),
+        ("n_d2", ctypes.c_int64),
+        ("y_d2", ctypes.c_void_p),
+        ("rho_d2", ctypes.c_void_p),
+        ("c_d2", ctypes.c_double),
     ]
 
 
@@ -187,7 +195,8 @@ class GNProblem:
     def __init__(self, equation, widths, y, y_bnd=None, rho=None, c_bnd=1.0, y_norm=(1.0, 0.0), c_norm=1.0,
                  c_norm_w=1.0, hilbert_m=1024, precision=GN_PREC_FP64, n_slices=4, device="cuda", stream=None,
                  fourier_B=None, y_inf=None, c_inf=1.0, norm_field=None, norm_deriv=None, output_map=0,
-                 row_block=0, y_relu=None, c_relu=1.0, relu_bound=0.0, relu_sign=1):
+                 row_block=0, y_relu=None, c_relu=1.0, relu_bound=0.0, relu_sign=1,
+                 y_d1=None, rho_d1=None, c_d1=1.0, y_d2=None, rho_d2=None, c_d2=1.0):
         lib()
         self.device = torch.device(device)
         self.equation = int(equation)
@@ -232,6 +241,19 @@ class GNProblem:
         p.n_relu = yr.shape[1] if yr.size else 0
         p.y_relu = self.y_relu.data_ptr() if self.y_relu is not None else None
         p.c_relu, p.relu_bound, p.relu_sign = float(c_relu), float(relu_bound), int(relu_sign)
+        # derivative-loss batches (SoA [d][n]); their rows follow the interior rows
+        self._dkeep = []
+        for k, (yd, rd, cd) in enumerate(((y_d1, rho_d1, c_d1), (y_d2, rho_d2, c_d2))):
+            ya = np.zeros((self.d, 0)) if yd is None else np.asarray(yd, dtype=np.float64).reshape(self.d, -1)
+            nd = ya.shape[1] if ya.size else 0
+            yt = torch.from_numpy(np.ascontiguousarray(ya)).to(self.device) if nd else None
+            rt = (None if rd is None or not nd
+                  else torch.as_tensor(rd, dtype=torch.float64, device=self.device).contiguous())
+            self._dkeep += [yt, rt]
+            setattr(p, f"n_d{k + 1}", nd)
+            setattr(p, f"y_d{k + 1}", yt.data_ptr() if yt is not None else None)
+            setattr(p, f"rho_d{k + 1}", rt.data_ptr() if rt is not None else None)
+            setattr(p, f"c_d{k + 1}", float(cd))
         # normalisation constraint: the equation's own unless a field or derivative is given
         if norm_field is not None or norm_deriv is not None:
             deriv = (self.equation == _inputs.BOUSSINESQ) if norm_deriv is None else bool(norm_deriv)
@@ -262,6 +284,9 @@ class GNProblem:
         kw.setdefault("norm_deriv", getattr(w, "norm_deriv", None))
         kw.setdefault("output_map", getattr(w, "output_map", 0))
         kw.setdefault("c_bnd", getattr(w, "c_bnd", 1.0))
+        for k, dflt in (("y_d1", None), ("rho_d1", None), ("c_d1", 1.0), ("y_d2", None), ("rho_d2", None),
+                        ("c_d2", 1.0)):
+            kw.setdefault(k, getattr(w, k, dflt))
         kw.setdefault("c_norm_w", getattr(w, "c_norm_w", 1.0))
         for k, dflt in (("y_relu", None), ("c_relu", 1.0), ("relu_bound", 0.0), ("relu_sign", 1)):
             kw.setdefault(k, getattr(w, k, dflt))

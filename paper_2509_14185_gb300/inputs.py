@@ -124,6 +124,12 @@ class Workload:
     c_relu: float = 1.0
     relu_bound: float = 0.0
     relu_sign: int = 1                   # +1 upper bound, -1 lower bound
+    y_d1: Optional[np.ndarray] = None    # (d, n_d1) points of the d1 derivative loss, or None
+    rho_d1: Optional[np.ndarray] = None
+    c_d1: float = 1.0
+    y_d2: Optional[np.ndarray] = None    # (d, n_d2) points of the d2 derivative loss, or None
+    rho_d2: Optional[np.ndarray] = None
+    c_d2: float = 1.0
 
     @property
     def d(self) -> int:
@@ -284,6 +290,20 @@ def weighted(w: Workload, seed: int = 31) -> Workload:
     its data loss a coefficient per constraint)."""
     return dataclasses.replace(w, name=w.name + "_weighted", rho=0.25 + 3.75 * uniform(seed, w.n_pts),
                                c_bnd=2.75, c_norm_w=0.35)
+
+
+def with_derivative_batches(w: Workload, n1: int, n2: int, seed: int = 41, c_d1: float = 0.3,
+                            c_d2: float = 0.05) -> Workload:
+    """The same workload with batches Y_1, Y_2 for the d1 and d2 derivative losses (the paper
+    assigns each loss its own batch; its batches are in its Supplementary Information): seeded
+    subsets of the collocation points with point weights rho ~ U[0.5, 2]."""
+    n = w.n_pts
+    pick1 = np.argsort(uniform(seed, n))[:n1]
+    pick2 = np.argsort(uniform(seed + 1, n))[:n2]
+    return dataclasses.replace(w, name=w.name + "_dloss", y_d1=np.ascontiguousarray(w.y[:, pick1]),
+                               rho_d1=0.5 + 1.5 * uniform(seed + 2, n1), c_d1=c_d1,
+                               y_d2=np.ascontiguousarray(w.y[:, pick2]), rho_d2=0.5 + 1.5 * uniform(seed + 3, n2),
+                               c_d2=c_d2)
 
 
 WORKLOADS = {

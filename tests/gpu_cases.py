@@ -24,7 +24,9 @@ def oracle_problem(w):
                       norm_field=getattr(w, "norm_field", None), norm_deriv=getattr(w, "norm_deriv", None),
                       output_map=getattr(w, "output_map", 0), y_relu=getattr(w, "y_relu", None),
                       c_relu=getattr(w, "c_relu", 1.0), relu_bound=getattr(w, "relu_bound", 0.0),
-                      relu_sign=getattr(w, "relu_sign", 1))
+                      relu_sign=getattr(w, "relu_sign", 1),
+                      y_d1=getattr(w, "y_d1", None), rho_d1=getattr(w, "rho_d1", None), c_d1=getattr(w, "c_d1", 1.0),
+                      y_d2=getattr(w, "y_d2", None), rho_d2=getattr(w, "rho_d2", None), c_d2=getattr(w, "c_d2", 1.0))
 
 
 def gpu_problem(w, **kw):
