@@ -19,6 +19,7 @@ import pytest
 import sympy as sp
 
 from oracle import gn
+from oracle import hilbert
 from oracle import problems as Pb
 from oracle.taylor import Taylor
 from paper_2509_14185_gb300 import inputs as I
@@ -212,3 +213,61 @@ def test_ccf_gradient_with_derivative_rows():
         r = p.rows(xc[:-1], xc[-1])
         dh = (0.5 * np.sum(r * r)).imag / 1e-30
         assert abs(dh - g[j]) <= 1e-10 * (abs(g[j]) + 1e-3 * np.max(np.abs(g)))
+
+
+# ---------------------------------------------------------------------------
+# the CCF velocity's Taylor series against a closed-form Hilbert pair, near the nodes too
+
+def _node_distance(x, M):
+    """Smallest distance from the points x to the circle nodes s_j, relative to 1 + |s_j|."""
+    _, s = hilbert.nodes(M)
+    return float(np.min(np.abs(np.asarray(x)[:, None] - s[None, :]) / (1.0 + np.abs(s[None, :]))))
+
+
+@pytest.mark.parametrize("M", [16, 64])
+def test_ccf_velocity_series_matches_a_hilbert_pair_near_nodes(M):
+    """g(s) = s/(1+s^2) (Theta = s^2/(1+s^2)) has U(x) = x H[g](x) = -x/(1+x^2), which the discrete
+    operator reproduces to rounding for M >= 8 (a trigonometric polynomial under the circle map).
+    Its Taylor coefficients in x, differentiated analytically by sympy, pin velocity_series to
+    order 4 at generic points and at points 1e-2, 1e-4 and 1e-6 (relative) from a node.  Near a node
+    the k-th coefficient loses accuracy like eps / dist^(k+1) (the difference g_j - g(x), small
+    there, carries an absolute rounding error that 1/(x - s_j)^(k+1) amplifies): the bound below says
+    so, and the distances are reported in the assertion."""
+    sp = pytest.importorskip("sympy")
+    psi, s = hilbert.nodes(M)
+    mid = np.tan(0.5 * (psi[[3, M // 2 - 2, M // 2 + 1, M - 5]] + np.pi / M))   # half-way between nodes
+    generic = np.concatenate([np.linspace(-4.0, 4.0, 9), [0.37, 12.5, -130.0], mid])
+    near = np.concatenate([s[[1, M // 3, M // 2]] + 1e-2 * (1 + np.abs(s[[1, M // 3, M // 2]])),
+                           s[[2, M // 2 + 1]] - 1e-4 * (1 + np.abs(s[[2, M // 2 + 1]])),
+                           s[[M // 4]] + 1e-6 * (1 + np.abs(s[[M // 4]]))])
+    x = np.concatenate([generic, near])
+    K = 4
+    X = Taylor.variable(x, 0, 1, K)
+    gX = X / (X * X + 1.0)
+    g_nodes = s / (1.0 + s * s)
+    U = hilbert.velocity_series(X, gX, g_nodes, M)
+    t = sp.symbols("t")
+    f = -t / (1 + t * t)
+    coef = [sp.lambdify(t, sp.diff(f, t, k) / sp.factorial(k), "numpy") for k in range(K + 1)]
+    dist = np.min(np.abs(x[:, None] - s[None, :]) / (1.0 + np.abs(s[None, :])), axis=1)
+    for k in range(K + 1):
+        want = np.asarray(coef[k](x), dtype=np.float64)
+        got = U.c[(k,)]
+        bound = 1e-14 * np.sqrt(M) * (1.0 + np.abs(x)) ** 2 * (1.0 + dist ** (-(k + 1)))
+        err = np.abs(got - want)
+        assert np.all(err <= bound), (k, float(np.max(err / bound)), float(np.min(dist)))
+    # points at least 0.04 (relative) from every node keep 1e-11 through order 4
+    far = dist >= 0.04
+    assert np.count_nonzero(far) >= 6
+    ferr = max(float(np.max(np.abs(U.c[(k,)][far] - np.asarray(coef[k](x[far]), dtype=np.float64))))
+               for k in range(K + 1))
+    assert ferr <= 1e-11, ferr
+
+
+def test_ccf_derivative_test_points_stay_away_from_nodes():
+    """The GPU parity cases of the CCF derivative rows (M = 32) keep their points at least 1e-2
+    (relative) from every node, where both sides' orders of summation agree to far below 1e-12."""
+    from paper_2509_14185_gb300 import inputs as I
+    w = I.with_derivative_batches(I.small_case(I.CCF, [1, 40, 40, 1], 60, seed=13, m=32), 11, 9)
+    assert _node_distance(w.y_d1[0], 32) > 1e-2
+    assert _node_distance(w.y_d2[0], 32) > 1e-2
