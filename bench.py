@@ -795,7 +795,7 @@ def kernel_report(prob, args, phases, pipe_tiles=0):
     c = cf / (chol_ms * 1e-3) / 1e12
     if args.precision == "split_all":
         out["cholesky"] = {"bound": "mixed", "fp64_equivalent_tflops": c, "ms": chol_ms,
-                           "kernel": "potrf_inv_kernel<ArithDF> (double-float 64 x 64 diagonal factor and "
+                           "kernel": "potrf_blk_kernel (blocked double-float 64 x 64 diagonal factor and "
                                      "inverse, one CTA) + panel_df_kernel (double-float panel solve writing the "
                                      f"split operand) + ozaki_kernel<{args.slices},0> (in-strip updates) + "
                                      f"ozaki_kernel<{args.slices},1> (K = 256 bulk updates, double-FP32 "
