@@ -931,6 +931,16 @@ def batched_record(args, steps, warmup, rank=0, world=1):
     n = len(fits)
     value = world * n * 1000.0 / ms
     rows = [w.n_pts + 1 for w in fits]
+    # the Gram tile shape and split-K factor the autotuner chose for each fit's shape
+    import ctypes
+    tiles, splits = {}, {}
+    for f in range(n):
+        t, k = ctypes.c_int(0), ctypes.c_int(0)
+        hf = batch.handle(f)
+        gn.lib().gn_gram_tile_choice(hf, rows[f], ctypes.byref(t))
+        gn.lib().gn_gram_split_choice(hf, rows[f], ctypes.byref(k))
+        tiles[t.value] = tiles.get(t.value, 0) + 1
+        splits[k.value] = splits.get(k.value, 0) + 1
     Pps = [w.n_params + 1 for w in fits]
     gram_flops = sum(r * p * (p + 1.0) for r, p in zip(rows, Pps))
     chol_flops = sum(p ** 3 / 3.0 for p in Pps)
@@ -952,6 +962,8 @@ def batched_record(args, steps, warmup, rank=0, world=1):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": f"batched_ccf_sweep_{n}_fits", "fits": n,
                            "gram_split": args.gram_split or "autotuned",
+                           "gram_choices": {"tile_width_fits": {str(k): v for k, v in sorted(tiles.items())},
+                                            "split_k_fits": {str(k): v for k, v in sorted(splits.items())}},
                            "launch": "one CUDA graph launch per batched step (every fit a branch)"
                            if (args.graph or not args.eager)
                            else f"{args.streams} streams, one host worker thread each",

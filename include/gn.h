@@ -221,6 +221,19 @@ int gn_set_precision(gn_handle* h, int precision, int n_slices);
 int gn_set_gram_split(gn_handle* h, int ksplit);
 int gn_gram_split_choice(const gn_handle* h, int64_t nrows, int* ksplit);
 
+/* Output tile shape of the split-precision Gram (the batched sweep's configuration asks for Gram
+ * tile shapes picked by an autotuner): 128 x 128 tiles, or 128 x 64 tiles (twice the CTAs, each
+ * with half the B operand and half the tensor memory; more parallelism for a small P').
+ * tile_n = 0 (default): autotuned together with the split-K factor on the first split Gram of a
+ * shape, over every (tile width, split-K) candidate, the default kept unless another is at least
+ * 3 % faster; tile_n = 128 or 64 forces one (with a forced width or split-K the other is not
+ * tuned).  The tile shape changes only which CTA computes an entry, not its arithmetic: results
+ * are bit for bit the same.  The pipelined step (gn_set_pipeline) uses 128-column tiles only.
+ * gn_gram_tile_choice reports the width a Gram over nrows rows uses (0: not tuned yet).
+ * GN_ERR_INVALID for other values. */
+int gn_set_gram_tile(gn_handle* h, int tile_n);
+int gn_gram_tile_choice(const gn_handle* h, int64_t nrows, int* tile_n);
+
 /* Pipelined Gram and factorisation in gn_step_graph (precision GN_PREC_SPLIT_ALL, one row
  * block, split-K factor 1).  The lower tiles of G = J~^T J~ are computed column by column in
  * chunks of at most `tiles` 128 x 128 tiles (one launch each, on a stream of the lowest

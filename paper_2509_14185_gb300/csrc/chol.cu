@@ -1150,11 +1150,11 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
       const int kb = (int)((n - k0) < NB ? (n - k0) : NB);
       const int kofs = (int)(k0 - s0);
       if (kofs > 0) {
-        // U[k0:, k0:k0+kb] += L[k0:, s0:k0] L[k0:k0+kb, s0:k0]^T
+        // U[k0:, k0:k0+kb] += L[k0:, s0:k0] L[k0:k0+kb, s0:k0]^T (64 columns: 128 x 64 tiles)
         OzOperand v = oz_operand_rows(strip, S, k0 - s0);
         v.kuse = kofs;
         rc = oz_gemm(S, false, v, v, n - k0, kb, reinterpret_cast<double*>(U + k0 * n + k0), n, 3, nullptr,
-                     h->flag + 2, sh);
+                     h->flag + 2, sh, 1, nullptr, OzRange(), 64);
         if (rc) return fail(rc);
       }
       const float2* Uk = (k0 > 0) ? U : nullptr;

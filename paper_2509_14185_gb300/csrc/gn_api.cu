@@ -693,6 +693,18 @@ int gn_pipeline_tiles(gn_handle* h, int64_t* tiles) {
   return GN_OK;
 }
 
+int gn_set_gram_tile(gn_handle* h, int tile_n) {
+  if (!h || (tile_n != 0 && tile_n != 64 && tile_n != 128)) return GN_ERR_INVALID;
+  h->gram_tile = tile_n;
+  return GN_OK;
+}
+
+int gn_gram_tile_choice(const gn_handle* h, int64_t nrows, int* tile_n) {
+  if (!h || !tile_n || nrows < 0) return GN_ERR_INVALID;
+  *tile_n = h->gram_tile > 0 ? h->gram_tile : gram_tile_choice(h->n_slices, h->Pp, nrows);
+  return GN_OK;
+}
+
 int gn_gram_split_choice(const gn_handle* h, int64_t nrows, int* ksplit) {
   if (!h || !ksplit || nrows < 0) return GN_ERR_INVALID;
   *ksplit = h->gram_ksplit > 0 ? h->gram_ksplit : gram_split_choice(h->n_slices, h->Pp, nrows);

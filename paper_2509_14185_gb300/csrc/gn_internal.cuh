@@ -166,6 +166,7 @@ struct gn_handle {
   int capturing = 0;              // a stream capture is in progress: no workspace may grow
   int lam_frozen = 0;             // lambda held fixed (funnel inference trains at fixed lambda)
   int gram_ksplit = 0;            // split-K factor of the split Gram (0: autotuned per shape)
+  int gram_tile = 0;              // output tile width of the split Gram, 128 or 64 (0: autotuned)
   // stage 2 of multi-stage training (gn_set_stage1): the stage-1 field jets at every point
   int staged = 0;
   double stage_eps = 1.0;
@@ -209,8 +210,9 @@ int gram_into(gn_handle* h, const double* J, int64_t ld, int64_t nrows, const do
 // factorisation's streams, so that a captured step allocates nothing
 int prepare_for_capture(gn_handle* h);
 size_t chol_split_ws_bytes(int64_t n, int S);
-// split-K factor the Gram autotuner recorded for this shape (0: not tuned yet)
+// split-K factor and tile width the Gram autotuner recorded for this shape (0: not tuned yet)
 int gram_split_choice(int S, int64_t Pp, int64_t nrows);
+int gram_tile_choice(int S, int64_t Pp, int64_t nrows);
 cudaError_t ensure_chol_streams(gn_handle* h);
 void graph_release(gn_handle* h);
 
@@ -336,9 +338,10 @@ struct OzRange {
   int64_t tile0 = 0, ntiles = -1;
   int colmajor = 0;
 };
+// tile_n: output tile columns, 128 (the default) or 64 (twice the tiles of a narrow or small C)
 int oz_gemm(int S, bool sym, const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, double* C, int64_t ldc,
             int mode, const double* rowscale, int* flag, cudaStream_t st, int ksplit = 1, void* part = nullptr,
-            const OzRange& range = OzRange());
+            const OzRange& range = OzRange(), int tile_n = 128);
 // Gram through oz_gemm (lower tiles); returns GN_ERR_* codes.
 int split_gram(gn_handle* h, const double* J, int64_t ld, int64_t nrows, double* G, int accumulate);
 // Tiles per chunk of the pipelined Gram for this handle's step, 0 when the step does not

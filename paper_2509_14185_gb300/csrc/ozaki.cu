@@ -53,21 +53,24 @@ namespace gn {
 namespace {
 
 constexpr int TM = 128;            // output tile rows
-constexpr int TN = 128;            // output tile cols
+constexpr int TN = 128;            // output tile cols (the default tile; BN = 64 halves it)
 constexpr int BKS = 32;            // K per stage (64-byte rows, SWIZZLE_64B)
 constexpr int SPC = 4;             // stages per exact-accumulation chunk (K = 128)
-constexpr int SLICE_BYTES = TM * BKS * 2;   // one slice tile: 8 KB
+constexpr int SLICE_BYTES = TM * BKS * 2;   // one 128-row slice tile: 8 KB
 constexpr int NTHREADS = 320;      // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
 constexpr unsigned long long kWaitNs = 4000000000ull;   // default bound on any wait: 4 s
 
-__host__ __device__ constexpr int n_stages(int S) {
-  return (2 * S * SLICE_BYTES * 4 <= 200 * 1024) ? 4 : (2 * S * SLICE_BYTES * 3 <= 200 * 1024) ? 3 : 2;
+// one pipeline stage: S slices of A (TM rows) and S of B (BN rows), BKS wide
+__host__ __device__ constexpr int stage_bytes(int S, int BN) { return S * (TM + BN) * BKS * 2; }
+__host__ __device__ constexpr int n_stages(int S, int BN) {
+  return (stage_bytes(S, BN) * 4 <= 200 * 1024) ? 4 : (stage_bytes(S, BN) * 3 <= 200 * 1024) ? 3 : 2;
 }
 // The operand ring is reused at the end to park the (hi, lo) tile; the
 // mbarriers live after whichever of the two is larger.
-constexpr int PARK_BYTES = TM * (TN + 1) * 8;
-__host__ __device__ constexpr int bar_offset(int S) {
-  return n_stages(S) * 2 * S * SLICE_BYTES > PARK_BYTES ? n_stages(S) * 2 * S * SLICE_BYTES : PARK_BYTES;
+__host__ __device__ constexpr int park_bytes(int BN) { return TM * (BN + 1) * 8; }
+__host__ __device__ constexpr int bar_offset(int S, int BN) {
+  return n_stages(S, BN) * stage_bytes(S, BN) > park_bytes(BN) ? n_stages(S, BN) * stage_bytes(S, BN)
+                                                                : park_bytes(BN);
 }
 
 // ---------------------------------------------------------------------------
@@ -136,14 +139,17 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
          ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
-// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, N = 128, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                            ((uint32_t)(TM >> 4) << 24);
+// kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, N = BN, M = 128.
+template <int BN>
+constexpr uint32_t idesc_for() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+template <int BN>
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+      "l"(a), "l"(b), "r"(idesc_for<BN>()), "r"(acc));
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -239,17 +245,29 @@ __device__ __forceinline__ void sym_tile(int64_t t, int64_t mt, int colmajor, in
   }
 }
 
+// Tile t of the lower part of G with 128-row, 64-column tiles (row order): row tile ti holds the
+// 2 ti + 2 column tiles 0 .. 2 ti + 1 (those reaching the diagonal), so rows start at ti (ti + 1).
+__device__ __forceinline__ void sym_tile_half(int64_t t, int64_t& ti, int64_t& tj) {
+  ti = (int64_t)((sqrt(4.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((ti + 1) * (ti + 2) <= t) ti++;
+  while (ti * (ti + 1) > t) ti--;
+  tj = t - ti * (ti + 1);
+}
+
 // ---------------------------------------------------------------------------
 // main kernel
 // ---------------------------------------------------------------------------
-template <int S, bool SYM, bool CH>
+template <int S, bool SYM, bool CH, int BN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     ozaki_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const OzArgs p) {
-  constexpr int NST = n_stages(S);
-  constexpr int STAGE_BYTES = 2 * S * SLICE_BYTES;
+  static_assert(BN == TM || BN == TM / 2, "tiles are 128 x 128 or 128 x 64");
+  constexpr int NST = n_stages(S, BN);
+  constexpr int STAGE_BYTES = stage_bytes(S, BN);
+  constexpr int SLICE_B = BN * BKS * 2;          // one B slice tile
+  constexpr int TMEM_COLS = 4 * BN;              // four accumulator slots
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + bar_offset(S));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + bar_offset(S, BN));
   uint64_t* empty = full + NST;
   uint64_t* acc_full = empty + NST;
   uint64_t* acc_empty = acc_full + 1;
@@ -264,8 +282,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   int64_t ti, tj;
   const int64_t tb = p.tile0 + blockIdx.x / p.ksplit;   // output tile
   const int ksp = (int)(blockIdx.x % p.ksplit);
-  if (SYM) {  // lower-triangular tile ti >= tj
-    sym_tile(tb, p.mt, p.colmajor, ti, tj);
+  if (SYM) {  // tiles reaching the lower triangle
+    if (BN == TM) sym_tile(tb, p.mt, p.colmajor, ti, tj);
+    else sym_tile_half(tb, ti, tj);
   } else {
     ti = tb / p.nt;
     tj = tb % p.nt;
@@ -294,7 +313,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   if (warp == 1) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "n"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
@@ -305,7 +325,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      const int rowA = (int)(ti * TM), rowB = (int)(tj * TN);
+      const int rowA = (int)(ti * TM), rowB = (int)(tj * BN);
       int issued = 0;
       for (int kt = 0; kt < (p.starve ? 0 : nk); kt++) {
         const int st = kt % NST;
@@ -321,7 +341,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int s = 0; s < S; s++) {
           tma_load_2d(base + s * SLICE_BYTES, &tmA, (kt0 + kt) * BKS, (int)(s * p.rowsA) + rowA, &full[st]);
-          tma_load_2d(base + (S + s) * SLICE_BYTES, &tmB, (kt0 + kt) * BKS, (int)(s * p.rowsB) + rowB, &full[st]);
+          tma_load_2d(base + S * SLICE_BYTES + s * SLICE_B, &tmB, (kt0 + kt) * BKS, (int)(s * p.rowsB) + rowB,
+                      &full[st]);
         }
         issued = kt + 1;
       }
@@ -366,12 +387,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                 for (int kk = 0; kk < BKS / 16; kk++) {
                   const uint64_t da = smem_desc(base + s * SLICE_BYTES + kk * 32);
-                  const uint64_t db = smem_desc(base + (S + u) * SLICE_BYTES + kk * 32);
+                  const uint64_t db = smem_desc(base + S * SLICE_BYTES + u * SLICE_B + kk * 32);
                   // the first pair of a level (s = 0) resets the slot: per chunk for the
                   // exact head levels; for the tail once, or per chunk with chunked exponents
                   const bool first = (slot < 3) ? (q == 0 && kk == 0 && s == 0)
                                                 : ((CH ? q : kt) == 0 && kk == 0 && s == 0 && u == 3);
-                  mma_bf16(tmem + slot * TN, da, db, first ? 0u : 1u);
+                  mma_bf16<BN>(tmem + slot * BN, da, db, first ? 0u : 1u);
                   mma_issued = true;
                 }
               }
@@ -391,14 +412,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
     }
   } else {
-    // ---------------- epilogue: 8 warps, 64 columns each ----------------
-    constexpr int EC = 64;                      // columns per epilogue thread
+    // ---------------- epilogue: 8 warps, BN / 2 columns each ----------------
+    constexpr int EC = BN / 2;                  // columns per epilogue thread
     const int quad = warp & 3;
     const int qcol = (warp - 2) >> 2;          // column half 0..1
     const int row = quad * 32 + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(qcol * EC);
     // chunked exponents are applied at each chunk's flush, so the final scale is 2^0
-    ecs[qcol][row] = CH ? 0 : ((qcol == 0) ? p.eA[ti * TM + row] : p.eB[tj * TN + row]);
+    ecs[qcol][row] = (CH || (qcol == 1 && row >= BN)) ? 0 : ((qcol == 0) ? p.eA[ti * TM + row] : p.eB[tj * BN + row]);
     asm volatile("bar.sync 1, 256;" ::: "memory");   // the 8 epilogue warps only
     float hi[EC], lo[EC];
 #pragma unroll
@@ -410,7 +431,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         // this chunk's exponents (double buffered: every thread has passed the previous
         // chunk's barrier, so nobody still reads the buffer of chunk c - 2)
         const int ev = (qcol == 0) ? p.eA[(c0 + c) * p.estride + ti * TM + row]
-                                   : p.eB[(c0 + c) * p.estride + tj * TN + row];
+                                   : (row < BN ? p.eB[(c0 + c) * p.estride + tj * BN + row] : 0);
         eccf[c & 1][qcol][row] = pow2f(ev);
         asm volatile("bar.sync 1, 256;" ::: "memory");
       }
@@ -430,7 +451,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
           for (int part = 0; part < EC / 16; part++) {
             float v[16];
-            tmem_ld16(lane_base + (uint32_t)(slot * TN + part * 16), v);
+            tmem_ld16(lane_base + (uint32_t)(slot * BN + part * 16), v);
 #pragma unroll
             for (int i = 0; i < 16; i++)
               dd_add(hi[part * 16 + i], lo[part * 16 + i],
@@ -443,7 +464,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
           for (int part = 0; part < EC / 16; part++) {
             float v[16];
-            tmem_ld16(lane_base + (uint32_t)(slot * TN + part * 16), v);
+            tmem_ld16(lane_base + (uint32_t)(slot * BN + part * 16), v);
 #pragma unroll
             for (int i = 0; i < 16; i++) dd_add(hi[part * 16 + i], lo[part * 16 + i], v[i]);
           }
@@ -452,7 +473,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
           for (int part = 0; part < EC / 16; part++) {
             float v[16];
-            tmem_ld16(lane_base + (uint32_t)(3 * TN + part * 16), v);
+            tmem_ld16(lane_base + (uint32_t)(3 * BN + part * 16), v);
 #pragma unroll
             for (int i = 0; i < 16; i++) dd_add(hi[part * 16 + i], lo[part * 16 + i], v[i]);
           }
@@ -468,20 +489,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     float2* park = reinterpret_cast<float2*>(smem);
     if (ok) {
 #pragma unroll
-      for (int i = 0; i < EC; i++) park[row * (TN + 1) + qcol * EC + i] = make_float2(hi[i], lo[i]);
+      for (int i = 0; i < EC; i++) park[row * (BN + 1) + qcol * EC + i] = make_float2(hi[i], lo[i]);
     }
     asm volatile("bar.sync 1, 256;" ::: "memory");
     if (ok && p.part) {
       // split-K partial: the unscaled (hi, lo) tile, coalesced; oz_splitk_reduce finishes it
       const int et = (warp - 2) * 32 + lane;
-      float2* dst = p.part + (size_t)blockIdx.x * (TM * TN);
-      for (int idx = et; idx < TM * TN; idx += 256) dst[idx] = park[(idx / TN) * (TN + 1) + (idx % TN)];
+      float2* dst = p.part + (size_t)blockIdx.x * (TM * BN);
+      for (int idx = et; idx < TM * BN; idx += 256) dst[idx] = park[(idx / BN) * (BN + 1) + (idx % BN)];
     } else if (ok) {
       // 64 elements per thread, in batches of 8 whose global loads are issued
       // together (a load-modify-store loop would expose one memory latency per element)
       const int et = (warp - 2) * 32 + lane;
       constexpr int B8 = 8;
-      for (int base_i = 0; base_i < TM * TN / 256; base_i += B8) {
+      for (int base_i = 0; base_i < TM * BN / 256; base_i += B8) {
         int64_t off[B8];
         bool in[B8];
         float2 hl[B8];
@@ -491,11 +512,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
         for (int q = 0; q < B8; q++) {
           const int idx = et + (base_i + q) * 256;
-          const int r = idx / TN, cc = idx % TN;
-          const int64_t gi = ti * TM + r, gj = tj * TN + cc;
+          const int r = idx / BN, cc = idx % BN;
+          const int64_t gi = ti * TM + r, gj = tj * BN + cc;
           in[q] = (gi < p.M && gj < p.N);
           off[q] = gi * p.ldc + gj;
-          hl[q] = park[r * (TN + 1) + cc];
+          hl[q] = park[r * (BN + 1) + cc];
           if (p.mode == 3) hl[q] = make_float2(hl[q].x * pow2f(ecs[0][r] + ecs[1][cc]),
                                               hl[q].y * pow2f(ecs[0][r] + ecs[1][cc]));
           else cv[q] = ((double)hl[q].x + (double)hl[q].y) * pow2(ecs[0][r] + ecs[1][cc]);
@@ -531,30 +552,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(TMEM_COLS));
   }
 }
 
 // Split-K epilogue: C_ij op= 2^(e_i + e_j) sum_ks (hi + lo)_ks, the partial tiles summed in
 // split order (deterministic), then the same store / add / subtract as the fused epilogue.
-template <bool SYM>
+template <bool SYM, int BN>
 __global__ void __launch_bounds__(256) oz_splitk_reduce(const float2* __restrict__ part, int ksplit, OzArgs p) {
   const int64_t tb = p.tile0 + blockIdx.x;
   int64_t ti, tj;
   if (SYM) {
-    sym_tile(tb, p.mt, p.colmajor, ti, tj);
+    if (BN == TM) sym_tile(tb, p.mt, p.colmajor, ti, tj);
+    else sym_tile_half(tb, ti, tj);
   } else {
     ti = tb / p.nt;
     tj = tb % p.nt;
   }
-  const float2* src = part + (size_t)blockIdx.x * ksplit * (TM * TN);
-  for (int idx = threadIdx.x; idx < TM * TN; idx += 256) {
-    const int r = idx / TN, cc = idx % TN;
-    const int64_t gi = ti * TM + r, gj = tj * TN + cc;
+  const float2* src = part + (size_t)blockIdx.x * ksplit * (TM * BN);
+  for (int idx = threadIdx.x; idx < TM * BN; idx += 256) {
+    const int r = idx / BN, cc = idx % BN;
+    const int64_t gi = ti * TM + r, gj = tj * BN + cc;
     if (gi >= p.M || gj >= p.N) continue;
     double v = 0.0;
     for (int k = 0; k < ksplit; k++) {
-      const float2 hl = src[(size_t)k * (TM * TN) + idx];
+      const float2 hl = src[(size_t)k * (TM * BN) + idx];
       v += (double)hl.x + (double)hl.y;
     }
     const double cv = v * pow2(p.eA[gi] + p.eB[gj]);
@@ -672,7 +694,7 @@ EncodeTiledFn get_encode() {
 
 int64_t rup(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
-int encode(const OzOperand& op, int S, CUtensorMap* map) {
+int encode(const OzOperand& op, int S, CUtensorMap* map, int box_rows = TM) {
   EncodeTiledFn enc = get_encode();
   if (!enc) {
     set_detail(__FILE__, __LINE__, "cuTensorMapEncodeTiled entry point not found");
@@ -681,7 +703,7 @@ int encode(const OzOperand& op, int S, CUtensorMap* map) {
   memset(map, 0, sizeof(*map));
   cuuint64_t dims[2] = {(cuuint64_t)op.kpad, (cuuint64_t)(op.map_rows > 0 ? op.map_rows : S * op.npad)};
   cuuint64_t strides[1] = {(cuuint64_t)(op.kpad * 2)};
-  cuuint32_t box[2] = {BKS, TM};
+  cuuint32_t box[2] = {BKS, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult cr = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, op.slices, dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -731,17 +753,17 @@ std::atomic<int> g_oz_starve{0};
 
 namespace {
 
-template <int S, bool SYM>
+template <int S, bool SYM, int BN>
 int launch_oz(const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, double* C, int64_t ldc, int mode,
               const double* rowscale, int* flag, cudaStream_t st, int ksplit, void* part, const OzRange& range) {
   CUtensorMap ma, mb;
-  int rc = encode(A, S, &ma);
+  int rc = encode(A, S, &ma, TM);
   if (rc) return rc;
-  rc = encode(B, S, &mb);
+  rc = encode(B, S, &mb, BN);
   if (rc) return rc;
-  const size_t smem = (size_t)bar_offset(S) + 1024 + 256;
+  const size_t smem = (size_t)bar_offset(S, BN) + 1024 + 256;
   const bool ch = A.echunk > 0;
-  if (GN_NOTE(cudaFuncSetAttribute(ch ? ozaki_kernel<S, SYM, true> : ozaki_kernel<S, SYM, false>,
+  if (GN_NOTE(cudaFuncSetAttribute(ch ? ozaki_kernel<S, SYM, true, BN> : ozaki_kernel<S, SYM, false, BN>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
     return GN_ERR_CUDA;
   OzArgs a;
@@ -750,7 +772,7 @@ int launch_oz(const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, doub
   a.Kpad = A.kuse > 0 ? A.kuse : A.kpad;
   a.M = M;
   a.N = N;
-  const int64_t mt = (M + TM - 1) / TM, nt = (N + TN - 1) / TN;
+  const int64_t mt = (M + TM - 1) / TM, nt = (N + BN - 1) / BN;
   a.nt = (int)nt;
   a.eA = A.e;
   a.eB = B.e;
@@ -763,13 +785,16 @@ int launch_oz(const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, doub
   a.flag = flag;
   a.wait_ns = g_oz_wait_ns.load(std::memory_order_relaxed);
   a.starve = g_oz_starve.load(std::memory_order_relaxed);
-  const int64_t all_tiles = SYM ? mt * (mt + 1) / 2 : mt * nt;
+  // sym: the tiles reaching the lower triangle (square tiles: mt (mt + 1) / 2; 64-column tiles:
+  // 2 ti + 2 in row tile ti, mt (mt + 1) in all)
+  const int64_t all_tiles = SYM ? (BN == TM ? mt * (mt + 1) / 2 : mt * (mt + 1)) : mt * nt;
   a.tile0 = 0;
   a.mt = mt;
   a.colmajor = 0;
   int64_t tiles = all_tiles;
-  if (range.ntiles >= 0) {   // a range of the triangle's tiles (sym only)
-    if (!SYM || range.tile0 < 0 || range.tile0 + range.ntiles > all_tiles) return GN_ERR_INVALID;
+  if (range.ntiles >= 0) {   // a range of the triangle's tiles (sym only; column order: square tiles)
+    if (!SYM || range.tile0 < 0 || range.tile0 + range.ntiles > all_tiles || (range.colmajor && BN != TM))
+      return GN_ERR_INVALID;
     a.tile0 = range.tile0;
     a.colmajor = range.colmajor;
     tiles = range.ntiles;
@@ -785,12 +810,12 @@ int launch_oz(const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, doub
   a.part = ksplit > 1 ? static_cast<float2*>(part) : nullptr;
   const unsigned grid = (unsigned)(tiles * ksplit);
   if (ch)
-    ozaki_kernel<S, SYM, true><<<grid, NTHREADS, smem, st>>>(ma, mb, a);
+    ozaki_kernel<S, SYM, true, BN><<<grid, NTHREADS, smem, st>>>(ma, mb, a);
   else
-    ozaki_kernel<S, SYM, false><<<grid, NTHREADS, smem, st>>>(ma, mb, a);
+    ozaki_kernel<S, SYM, false, BN><<<grid, NTHREADS, smem, st>>>(ma, mb, a);
   count_launch();
   if (ksplit > 1) {
-    oz_splitk_reduce<SYM><<<(unsigned)tiles, 256, 0, st>>>(a.part, ksplit, a);
+    oz_splitk_reduce<SYM, BN><<<(unsigned)tiles, 256, 0, st>>>(a.part, ksplit, a);
     count_launch();
   }
   return GN_NOTE(cudaGetLastError()) == cudaSuccess ? GN_OK : GN_ERR_CUDA;
@@ -848,15 +873,19 @@ OzOperand oz_operand_rows(const OzOperand& op, int S, int64_t row_off) {
 
 int oz_gemm(int S, bool sym, const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, double* C, int64_t ldc,
             int mode, const double* rowscale, int* flag, cudaStream_t st, int ksplit, void* part,
-            const OzRange& range) {
+            const OzRange& range, int tile_n) {
+  if (tile_n != TM && tile_n != TM / 2) return GN_ERR_INVALID;
   if (A.kpad != B.kpad || A.kuse != B.kuse || A.kuse % BKS != 0 || A.kuse > A.kpad) return GN_ERR_INVALID;
   if (A.echunk != B.echunk || A.estride != B.estride || A.echunk % BKS != 0 || A.echunk > SPC * BKS ||
       (A.echunk > 0 && A.estride <= 0))
     return GN_ERR_INVALID;
-#define GN_OZ_CASE(s)                                                                     \
-  case s:                                                                                 \
-    return sym ? launch_oz<s, true>(A, B, M, N, C, ldc, mode, rowscale, flag, st, ksplit, part, range)   \
-               : launch_oz<s, false>(A, B, M, N, C, ldc, mode, rowscale, flag, st, ksplit, part, range);
+#define GN_OZ_CASE(s)                                                                                     \
+  case s:                                                                                                 \
+    if (tile_n == TM)                                                                                     \
+      return sym ? launch_oz<s, true, TM>(A, B, M, N, C, ldc, mode, rowscale, flag, st, ksplit, part, range) \
+                 : launch_oz<s, false, TM>(A, B, M, N, C, ldc, mode, rowscale, flag, st, ksplit, part, range); \
+    return sym ? launch_oz<s, true, TM / 2>(A, B, M, N, C, ldc, mode, rowscale, flag, st, ksplit, part, range)  \
+               : launch_oz<s, false, TM / 2>(A, B, M, N, C, ldc, mode, rowscale, flag, st, ksplit, part, range);
   switch (S) {
     GN_OZ_CASE(1)
     GN_OZ_CASE(2)
@@ -884,57 +913,87 @@ int ensure_split_ws(gn_handle* h, size_t need) {
 }
 
 // ---------------------------------------------------------------------------
-// Gram split-K autotuner.  A Gram of few 128 x 128 tiles (small P') leaves most of the 152
-// SMs idle; cutting the contraction into ksplit parts multiplies the CTAs.  The best ksplit
-// depends on the tile count, the contraction length and S, so it is measured: on the first
-// split Gram of a shape (S, tile rows, flush chunks) every candidate is launched and timed
-// with CUDA events, and the fastest is kept in a process-wide table (so every handle of that
-// shape in the process takes the same, deterministic path).  gn_set_gram_split forces one.
+// Gram autotuner: tile shape and split-K.  A Gram of few tiles (small P') leaves most of the 152
+// SMs idle; 128 x 64 tiles (twice as many CTAs, each with half the B operand and half the
+// tensor memory) and cutting the contraction into ksplit parts both multiply the CTAs.  The
+// best choice depends on the tile count, the contraction length and S, so it is measured: on
+// the first split Gram of a shape (S, tile rows, flush chunks) every candidate (tile width,
+// ksplit) is launched and timed with CUDA events, and the fastest is kept in a process-wide
+// table (so every handle of that shape in the process takes the same, deterministic path).
+// gn_set_gram_split and gn_set_gram_tile force one.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr int64_t kSplitMaxCtas = 4 * 152;   // candidates keep tiles * ksplit within 4 waves
+struct GramChoice {
+  int ks = 1, tn = TN;
+};
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int64_t, int64_t>, int> g_tune;
+std::map<std::tuple<int, int64_t, int64_t>, GramChoice> g_tune;
 
 int64_t gram_chunks(int64_t nrows) { return (rup(nrows > 0 ? nrows : 1, BKS) / BKS + SPC - 1) / SPC; }
-int64_t gram_tiles(int64_t Pp) {
+int64_t gram_tiles(int64_t Pp, int tn = TN) {
   const int64_t mt = (Pp + TM - 1) / TM;
-  return mt * (mt + 1) / 2;
+  return tn == TM ? mt * (mt + 1) / 2 : mt * (mt + 1);
 }
-std::vector<int> gram_candidates(int64_t Pp, int64_t nrows) {
-  std::vector<int> c = {1};
-  const int64_t tiles = gram_tiles(Pp), nch = gram_chunks(nrows);
-  int last = 1;
-  for (int ks : {2, 3, 4, 6, 8}) {
-    const int64_t cps = (nch + ks - 1) / ks;
-    const int eff = (int)((nch + cps - 1) / cps);   // splits actually made
-    if (tiles * eff > kSplitMaxCtas || cps < 2 || eff <= last) continue;
-    c.push_back(eff);
-    last = eff;
+std::vector<GramChoice> gram_candidates(gn_handle* h, int64_t nrows) {
+  std::vector<GramChoice> c;
+  const int64_t nch = gram_chunks(nrows);
+  for (int tn : {TN, TN / 2}) {
+    if (h->gram_tile > 0 && tn != h->gram_tile) continue;
+    const int64_t tiles = gram_tiles(h->Pp, tn);
+    if (h->gram_ksplit > 0) {
+      c.push_back({h->gram_ksplit, tn});
+      continue;
+    }
+    c.push_back({1, tn});
+    int last = 1;
+    for (int ks : {2, 3, 4, 6, 8}) {
+      const int64_t cps = (nch + ks - 1) / ks;
+      const int eff = (int)((nch + cps - 1) / cps);   // splits actually made
+      if (tiles * eff > kSplitMaxCtas || cps < 2 || eff <= last) continue;
+      c.push_back({eff, tn});
+      last = eff;
+    }
   }
   return c;
 }
 int gram_max_split(gn_handle* h, int64_t nrows) {
-  if (h->gram_ksplit > 0) return h->gram_ksplit;
   int m = 1;
-  for (int k : gram_candidates(h->Pp, nrows)) m = k > m ? k : m;
+  for (const GramChoice& k : gram_candidates(h, nrows)) m = k.ks > m ? k.ks : m;
   return m;
 }
+// split-K partial tiles: the same bytes for either tile width (twice the tiles, half the size)
 size_t gram_part_bytes(int64_t Pp, int ksplit) {
   return ksplit > 1 ? (size_t)gram_tiles(Pp) * ksplit * TM * TN * sizeof(float2) : 0;
 }
-bool lookup(int S, int64_t Pp, int64_t nrows, int* ks) {
+bool lookup(int S, int64_t Pp, int64_t nrows, GramChoice* ch) {
   std::lock_guard<std::mutex> g(g_tune_mu);
   auto it = g_tune.find(std::make_tuple(S, (Pp + TM - 1) / TM, gram_chunks(nrows)));
   if (it == g_tune.end()) return false;
-  *ks = it->second;
+  *ch = it->second;
+  return true;
+}
+// The choice a split Gram of this handle over nrows rows takes: forced, or tuned (false when the
+// shape has not been tuned yet and nothing is forced).
+bool gram_choice(gn_handle* h, int64_t nrows, GramChoice* ch) {
+  GramChoice t;
+  const bool tuned = lookup(h->n_slices, h->Pp, nrows, &t);
+  if (h->gram_ksplit > 0 && h->gram_tile > 0) {
+    *ch = {h->gram_ksplit, h->gram_tile};
+    return true;
+  }
+  if (!tuned) return false;
+  *ch = t;
+  if (h->gram_ksplit > 0) ch->ks = h->gram_ksplit;
+  if (h->gram_tile > 0) ch->tn = h->gram_tile;
   return true;
 }
 // Time every candidate on the prepared operand (mode 0 into C, which the caller overwrites
-// afterwards) and record the fastest.  Synchronises the stream.
-int tune(gn_handle* h, int S, const OzOperand& op, int64_t nrows, double* C, void* part, int* best_out) {
-  const std::vector<int> cand = gram_candidates(h->Pp, nrows);
-  int best = 1;
+// afterwards) and record the fastest; the default (128-column tiles, no split) unless another
+// wins by 3 %.  Synchronises the stream.
+int tune(gn_handle* h, int S, const OzOperand& op, int64_t nrows, double* C, void* part, GramChoice* best_out) {
+  const std::vector<GramChoice> cand = gram_candidates(h, nrows);
+  GramChoice best = cand[0];
   if (cand.size() > 1) {
     cudaEvent_t e0, e1;
     if (GN_NOTE(cudaEventCreate(&e0)) != cudaSuccess) return GN_ERR_CUDA;
@@ -944,12 +1003,15 @@ int tune(gn_handle* h, int S, const OzOperand& op, int64_t nrows, double* C, voi
     }
     float best_ms = 0.f;
     int rc = GN_OK;
-    for (int ks : cand) {
-      rc = oz_gemm(S, true, op, op, h->Pp, h->Pp, C, h->Pp, 0, nullptr, h->flag + 2, h->st, ks, part);   // warm
+    bool first = true;
+    for (const GramChoice& c : cand) {
+      rc = oz_gemm(S, true, op, op, h->Pp, h->Pp, C, h->Pp, 0, nullptr, h->flag + 2, h->st, c.ks, part, OzRange(),
+                   c.tn);   // warm
       if (rc) break;
       cudaEventRecord(e0, h->st);
       for (int r = 0; r < 3 && !rc; r++)
-        rc = oz_gemm(S, true, op, op, h->Pp, h->Pp, C, h->Pp, 0, nullptr, h->flag + 2, h->st, ks, part);
+        rc = oz_gemm(S, true, op, op, h->Pp, h->Pp, C, h->Pp, 0, nullptr, h->flag + 2, h->st, c.ks, part,
+                     OzRange(), c.tn);
       cudaEventRecord(e1, h->st);
       if (rc || GN_NOTE(cudaEventSynchronize(e1)) != cudaSuccess) {
         rc = rc ? rc : GN_ERR_CUDA;
@@ -957,16 +1019,17 @@ int tune(gn_handle* h, int S, const OzOperand& op, int64_t nrows, double* C, voi
       }
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
-      if (ks == cand[0] || ms < 0.97f * best_ms) {   // a larger split must win by 3%
+      if (first || ms < 0.97f * best_ms) {   // another choice must win by 3 %
         best_ms = ms;
-        best = ks;
+        best = c;
       }
+      first = false;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
   }
-  {
+  if (h->gram_ksplit == 0 && h->gram_tile == 0) {   // only free choices go into the table
     std::lock_guard<std::mutex> g(g_tune_mu);
     g_tune[std::make_tuple(S, (h->Pp + TM - 1) / TM, gram_chunks(nrows))] = best;
   }
@@ -976,17 +1039,21 @@ int tune(gn_handle* h, int S, const OzOperand& op, int64_t nrows, double* C, voi
 }  // namespace
 
 int gram_split_choice(int S, int64_t Pp, int64_t nrows) {
-  int ks = 0;
-  return lookup(S, Pp, nrows, &ks) ? ks : 0;
+  GramChoice ch;
+  return lookup(S, Pp, nrows, &ch) ? ch.ks : 0;
+}
+int gram_tile_choice(int S, int64_t Pp, int64_t nrows) {
+  GramChoice ch;
+  return lookup(S, Pp, nrows, &ch) ? ch.tn : 0;
 }
 
 // Tune the Gram of the handle's largest row block ahead of a capture, on a zeroed operand
 // (tensor-core time does not depend on the values).
 int pretune_gram(gn_handle* h) {
-  if (h->precision == GN_PREC_FP64 || h->gram_ksplit > 0 || h->n_rows <= 0) return GN_OK;
+  if (h->precision == GN_PREC_FP64 || h->gram_ksplit > 0 || h->gram_tile > 0 || h->n_rows <= 0) return GN_OK;
   const int S = h->n_slices;
   const int64_t nrows = h->jrows;
-  int ks = 0;
+  GramChoice ks;
   if (lookup(S, h->Pp, nrows, &ks)) return GN_OK;
   const size_t opb = oz_operand_bytes(S, h->Pp, nrows);
   unsigned char* base = static_cast<unsigned char*>(h->split_ws);
@@ -1034,16 +1101,18 @@ int split_gram(gn_handle* h, const double* J, int64_t ld, int64_t nrows, double*
   void* kpart = static_cast<unsigned char*>(h->split_ws) + opb + cmb;
   rc = oz_prepare_cols(S, J, ld, nrows, h->Pp, op, part, h->st);
   if (rc) return rc;
-  // split-K factor: forced, tuned earlier for this shape, tuned now, or none
-  int ks = h->gram_ksplit;
-  if (ks <= 0 && !lookup(S, h->Pp, nrows, &ks)) {
-    ks = 1;
-    if (!accumulate && !h->capturing) {
-      rc = tune(h, S, op, nrows, G, kpart, &ks);
+  // tile width and split-K factor: forced, tuned earlier for this shape, tuned now, or the defaults
+  GramChoice ch;
+  if (!gram_choice(h, nrows, &ch)) {
+    ch.ks = h->gram_ksplit > 0 ? h->gram_ksplit : 1;
+    ch.tn = h->gram_tile > 0 ? h->gram_tile : TN;
+    if (!accumulate && !h->capturing && h->gram_ksplit == 0 && h->gram_tile == 0) {
+      rc = tune(h, S, op, nrows, G, kpart, &ch);
       if (rc) return rc;
     }
   }
-  rc = oz_gemm(S, true, op, op, h->Pp, h->Pp, G, h->Pp, accumulate ? 1 : 0, nullptr, h->flag + 2, h->st, ks, kpart);
+  rc = oz_gemm(S, true, op, op, h->Pp, h->Pp, G, h->Pp, accumulate ? 1 : 0, nullptr, h->flag + 2, h->st, ch.ks,
+               kpart, OzRange(), ch.tn);
   if (rc) return rc;
   return GN_OK;
 }
@@ -1051,9 +1120,12 @@ int split_gram(gn_handle* h, const double* J, int64_t ld, int64_t nrows, double*
 int64_t pipeline_chunk_tiles(gn_handle* h) {
   if (h->pipe_tiles == 0 || h->precision != GN_PREC_SPLIT_ALL || h->n_rows <= 0) return 0;
   if ((h->n_rows + h->jrows - 1) / h->jrows != 1) return 0;
-  int ks = h->gram_ksplit;
-  if (ks <= 0 && !lookup(h->n_slices, h->Pp, h->n_rows, &ks)) ks = 1;
-  if (ks != 1) return 0;
+  GramChoice ch;   // the pipeline's column chunks use square tiles without split-K
+  if (!gram_choice(h, h->n_rows, &ch)) {
+    ch.ks = h->gram_ksplit > 0 ? h->gram_ksplit : 1;
+    ch.tn = h->gram_tile > 0 ? h->gram_tile : TN;
+  }
+  if (ch.ks != 1 || ch.tn != TN) return 0;
   if ((h->Pp + TM - 1) / TM < 4) return 0;   // a G this small is one strip or two
   if (h->pipe_tiles > 0) return h->pipe_tiles;
   int sms = 0;

@@ -138,6 +138,8 @@ EXPORTS = {
     "gn_signed_max_residual": (ctypes.c_int, [_P, _P, _D, _D, ctypes.POINTER(_D), ctypes.POINTER(_I64)]),
     "gn_funnel_next": (ctypes.c_int, [_P, _P, ctypes.c_int, _D, ctypes.POINTER(_D)]),
     "gn_gram_split_choice": (ctypes.c_int, [_P, _I64, ctypes.POINTER(ctypes.c_int)]),
+    "gn_set_gram_tile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gn_gram_tile_choice": (ctypes.c_int, [_P, _I64, ctypes.POINTER(ctypes.c_int)]),
     "gn_step_graph": (ctypes.c_int, [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(gn_step_info)]),
     "gn_batch_capture_graph": (ctypes.c_int, [_P, _P]),
     "gn_batch_graph_step": (ctypes.c_int, [_P, _P, _P, _P, _P]),
@@ -310,6 +312,16 @@ class GNProblem:
 
     def gn_set_gram_split(self, ksplit):
         _check(lib().gn_set_gram_split(self.h, int(ksplit)), "gn_set_gram_split")
+
+    def gn_set_gram_tile(self, tile_n):
+        """Split Gram output tiles 128 x tile_n (128 or 64; 0: autotuned)."""
+        _check(lib().gn_set_gram_tile(self.h, int(tile_n)), "gn_set_gram_tile")
+
+    def gn_gram_tile_choice(self, nrows=None):
+        k = ctypes.c_int(0)
+        _check(lib().gn_gram_tile_choice(self.h, self.n_rows if nrows is None else int(nrows), ctypes.byref(k)),
+               "gn_gram_tile_choice")
+        return k.value
 
     def gn_set_pipeline(self, tiles):
         """Tiles per Gram chunk of the pipelined graph step (0, the default: off; -1: from the SM count)."""

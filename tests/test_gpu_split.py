@@ -219,3 +219,69 @@ def test_gram_autotuner_records_a_choice_per_shape():
     assert prob2.gn_gram_split_choice(4000) == 3
     with pytest.raises(Exception):
         prob2.gn_set_gram_split(9)
+
+
+# --- 128 x 64 output tiles (the autotuner's second tile shape) ----------------------------
+
+@pytest.mark.parametrize("ksplit", [1, 3])
+def test_split_gram_half_tiles_bit_exact_on_8bit_integers(ksplit):
+    """128 x 64 tiles: the lower part of G is covered by 2 ti + 2 column tiles per row tile
+    (the last one ragged here, P' = 1762), B tiles of 64 rows, 256 tensor-memory columns and a
+    32-column epilogue per thread; on 8-bit integer J the Gram is exact bit for bit, with or
+    without split-K."""
+    w = small("ccf")
+    prob = gpu_problem(w)
+    Pp = prob.P + 1
+    rng = np.random.default_rng(17)
+    Jh = rng.integers(-200, 201, size=(1500, Pp)).astype(np.float64)
+    Jh[:, 4] = 0.0
+    Jh[:, 11] *= 2.0 ** -25
+    prob.gn_set_gram_tile(64)
+    prob.gn_set_gram_split(ksplit)
+    assert prob.gn_gram_tile_choice(1500) == 64
+    G = host(_split_gram(prob, dev(Jh), 1))
+    assert np.array_equal(np.tril(G), np.tril(Jh.T @ Jh))
+
+
+@pytest.mark.parametrize("slices", [2, 6])
+def test_split_gram_half_tiles_equal_square_tiles(slices):
+    """The tile shape changes which CTA computes an entry, not its arithmetic: a real Jacobian's
+    Gram on 128 x 64 tiles equals the one on 128 x 128 tiles bit for bit (and both obey the
+    bound), in overwrite and accumulate modes."""
+    w = small("ccf")
+    p = oracle_problem(w)
+    J = ogn.jacobian(p, w.theta, w.lam)
+    prob = gpu_problem(w)
+    prob.gn_set_gram_split(1)
+    prob.gn_set_gram_tile(128)
+    G128 = host(_split_gram(prob, dev(J), slices))
+    prob.gn_set_gram_tile(64)
+    G64 = host(_split_gram(prob, dev(J), slices))
+    np.testing.assert_array_equal(np.tril(G64), np.tril(G128))
+    bound = np.tril(split_bound(J, slices))
+    assert np.all(np.abs(np.tril(G64) - np.tril(J.T @ J)) <= 2.0 * bound + 1e-300)
+    G2 = _split_gram(prob, dev(J), slices)
+    G2 = host(_split_gram(prob, dev(J), slices, accumulate=True, G=G2))
+    assert np.all(np.tril(np.abs(G2 - 2 * (J.T @ J))) <= 4.0 * bound + 1e-300)
+
+
+def test_gram_autotuner_chooses_a_tile_shape():
+    """The autotuner times both tile widths (with their split-K candidates) and records one; a
+    second handle of the shape reuses it; forcing a width overrides the table; bad widths are
+    refused."""
+    w = small("burgers")                       # P' = 674: 6 row tiles, 21 or 42 tiles
+    prob = gpu_problem(w)
+    Pp = prob.P + 1
+    rng = np.random.default_rng(5)
+    J = dev(rng.standard_normal((3000, Pp)))
+    assert prob.gn_gram_tile_choice(3000) == 0          # not tuned yet
+    _split_gram(prob, J, 5)
+    t = prob.gn_gram_tile_choice(3000)
+    assert t in (64, 128)
+    prob2 = gpu_problem(w)
+    prob2.gn_set_precision(SPLIT, 5)
+    assert prob2.gn_gram_tile_choice(3000) == t
+    prob2.gn_set_gram_tile(64)
+    assert prob2.gn_gram_tile_choice(3000) == 64
+    with pytest.raises(Exception):
+        prob2.gn_set_gram_tile(96)
