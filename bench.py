@@ -32,10 +32,12 @@ if ROOT not in sys.path:
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one split Gram launch,
 # ozaki_kernel<6,1,0> on the CCF 1st-unstable workload (2278 tiles, S = 6), from a single-pass
-# ncu capture of `bench.py --eager --gram-split 1 --steps 1 --warmup 1` (the eager path: ncu
-# lists no kernels inside graphs with conditional nodes): 18.18 GB read + 0.31 GB written.  Valid
-# only for that kernel build and workload; re-measure when either changes.
-GRAM_TRAFFIC_BYTES_CCF_S6 = 18.18e9 + 0.31e9
+# ncu capture of `bench.py --eager --gram-split 1 --gram-tile 128 --steps 1 --warmup 1` (the eager
+# path: ncu lists no kernels inside graphs with conditional nodes; split-K and tile width forced so
+# that no tuning launch comes first) with the tiles in blocked order: 12.40 GB read + 0.31 GB
+# written (18.18 + 0.31 GB in row order).  Valid only for that kernel build and workload;
+# re-measure when either changes.
+GRAM_TRAFFIC_BYTES_CCF_S6 = 12.40e9 + 0.31e9
 
 METRIC = "gn_steps_per_s"
 UNIT = "steps/s"
@@ -92,6 +94,8 @@ def parse():
     ap.add_argument("--funnel-dlam", type=float, default=0.01)
     ap.add_argument("--gram-split", type=int, default=0,
                     help="force the split Gram's split-K factor (0: autotuned per shape)")
+    ap.add_argument("--gram-tile", type=int, default=0, choices=[0, 64, 128],
+                    help="force the split Gram's output tile width (0: autotuned)")
     ap.add_argument("--pipeline", type=int, default=None,
                     help="tiles per Gram chunk of the pipelined graph step (-1: 7/8 of the SM count; "
                          "default: the library's, off: Gram then factorisation)")
@@ -1023,6 +1027,8 @@ def main():
         prob.gn_set_pipeline(args.pipeline)
     if args.gram_split:
         prob.gn_set_gram_split(args.gram_split)
+    if args.gram_tile:
+        prob.gn_set_gram_tile(args.gram_tile)
     stream = torch.cuda.current_stream()
     theta = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
     lam, gam = w.lam, w.gamma

@@ -227,12 +227,51 @@ struct OzArgs {
   int starve;                   // testing: the producer issues no copy, so the waits run out
 };
 
+// Blocked order of a whole lower triangle (order 2): the tiles in square super-blocks of
+// kRasterSB x kRasterSB tiles, super-blocks row by row (J <= I), tiles row by row inside each
+// (the diagonal super-blocks lower-triangular).  The CTAs in flight (about one super-block) then
+// share kRasterSB row bands of A and kRasterSB of B, read at nearly the same contraction
+// position, so most band reads hit in L2 instead of DRAM (row order keeps ~2 row tiles but every
+// column band in flight).  A bijection onto the triangle: only the order of the tiles changes.
+constexpr int64_t kRasterSB = 12;
+__device__ __forceinline__ void sym_tile_blocked(int64_t t, int64_t mt, int64_t& ti, int64_t& tj) {
+  const int64_t sb = kRasterSB;
+  int64_t I = 0, base = 0;
+  for (;;) {   // super-row I: I off-diagonal blocks of hh x sb tiles, then the diagonal block
+    const int64_t hh = (mt - I * sb < sb) ? mt - I * sb : sb;
+    const int64_t cnt = I * hh * sb + hh * (hh + 1) / 2;
+    if (t < base + cnt || (I + 1) * sb >= mt) {
+      int64_t u = t - base;
+      if (u < I * hh * sb) {
+        const int64_t J = u / (hh * sb), v = u % (hh * sb);
+        ti = I * sb + v / sb;
+        tj = J * sb + v % sb;
+      } else {
+        u -= I * hh * sb;
+        int64_t r = (int64_t)((sqrt(8.0 * (double)u + 1.0) - 1.0) * 0.5);
+        while ((r + 1) * (r + 2) / 2 <= u) r++;
+        while (r * (r + 1) / 2 > u) r--;
+        ti = I * sb + r;
+        tj = I * sb + (u - r * (r + 1) / 2);
+      }
+      return;
+    }
+    base += cnt;
+    I++;
+  }
+}
+
 // Lower-triangular tile t of an mt x mt tile grid.  Row order: row ti holds tiles
-// ti (ti + 1) / 2 .. + ti.  Column order (colmajor): column tj holds the next mt - tj tiles, so
-// the first C(c) = c mt - c (c - 1) / 2 tiles are exactly the tile columns 0 .. c - 1.  It is
+// ti (ti + 1) / 2 .. + ti.  Column order (colmajor = 1): column tj holds the next mt - tj tiles,
+// so the first C(c) = c mt - c (c - 1) / 2 tiles are exactly the tile columns 0 .. c - 1.  It is
 // row order read backwards on the triangle reflected about its anti-diagonal,
-// (ti, tj) -> (mt - 1 - tj, mt - 1 - ti), which maps the lower triangle onto itself.
+// (ti, tj) -> (mt - 1 - tj, mt - 1 - ti), which maps the lower triangle onto itself.  Blocked
+// order (colmajor = 2): sym_tile_blocked.
 __device__ __forceinline__ void sym_tile(int64_t t, int64_t mt, int colmajor, int64_t& ti, int64_t& tj) {
+  if (colmajor == 2) {
+    sym_tile_blocked(t, mt, ti, tj);
+    return;
+  }
   if (colmajor) t = mt * (mt + 1) / 2 - 1 - t;
   ti = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
   while ((ti + 1) * (ti + 2) / 2 <= t) ti++;
@@ -790,7 +829,7 @@ int launch_oz(const OzOperand& A, const OzOperand& B, int64_t M, int64_t N, doub
   const int64_t all_tiles = SYM ? (BN == TM ? mt * (mt + 1) / 2 : mt * (mt + 1)) : mt * nt;
   a.tile0 = 0;
   a.mt = mt;
-  a.colmajor = 0;
+  a.colmajor = (SYM && BN == TM) ? 2 : 0;   // a whole square-tile triangle: the blocked order
   int64_t tiles = all_tiles;
   if (range.ntiles >= 0) {   // a range of the triangle's tiles (sym only; column order: square tiles)
     if (!SYM || range.tile0 < 0 || range.tile0 + range.ntiles > all_tiles || (range.colmajor && BN != TM))
