@@ -337,11 +337,14 @@ __global__ void __launch_bounds__(NB * TPR) potrf_inv_kernel(double* A, int64_t 
 }
 
 // Blocked double-float factor of the diagonal block (the split path's critical-path kernel).
-// Same contract as potrf_inv_kernel<ArithDF>: B = A[k0:k0+kb, k0:k0+kb] - U (lower), scaled
-// B' = D B D by powers of two (D_ii = 2^-sc[i], B'_ii in [1, 4)), factored as B' = L' L'^T with
-// L'^{-1} formed alongside; writes L = D^-1 L' into A, Linv = L'^{-1} D (FP64), L'^{-1} in
-// double-float (LinvDF), the scales, and (with fw) the forward-substitution block
-// y_k = L'^{-1} D w_k.  Rows and columns kb .. 63 are padded with the identity.
+// B = A[k0:k0+kb, k0:k0+kb] - U (lower), scaled B' = D B D by powers of two (D_ii = 2^-sc[i],
+// B'_ii in [1, 4)), factored as B' = L' L'^T with L'^{-1} formed alongside.  Writes only
+// double-float results: L' (LDF), L'^{-1} (LinvDF), the scales, and (with fw) the
+// forward-substitution block y_k = L'^{-1} D w_k.  The FP64 copies the triangular solves read
+// (L = D^-1 L' into A, Linv = L'^{-1} D) are formed for all blocks at once after the chain
+// (diag_to_fp64_kernel): their FP64 additions (two per element; GB300's FP64 pipe retires
+// about two per clock per SM) took a tenth of this kernel's time.  Rows and columns kb .. 63
+// are padded with the identity.
 //
 // The same LDL^T elimination as potrf_inv_kernel (S: unscaled columns L_unit D; Y = L_unit^{-1}),
 // reordered into four 16-column sub-panels p so that only a 16-step chain is latency-bound:
@@ -363,9 +366,9 @@ constexpr int kPbLd = NB + 1;                  // row stride of the shared S and
 constexpr size_t kPbSmem = (size_t)(2 * NB * kPbLd + (NB - kPbB) * kPbB + 4 * kPbB + 2 * NB) * sizeof(DF) +
                            (size_t)(NB + 4) * sizeof(int);
 
-__global__ void __launch_bounds__(kPbThreads) potrf_blk_kernel(double* A, int64_t lda, int64_t k0, int kb,
+__global__ void __launch_bounds__(kPbThreads) potrf_blk_kernel(const double* A, int64_t lda, int64_t k0, int kb,
                                                                const float2* __restrict__ U, int64_t ldu,
-                                                               double* Linv, float2* LinvDF, int* scOut,
+                                                               float2* LDF, float2* LinvDF, int* scOut,
                                                                const double* fw, double* fy, float2* fyDF,
                                                                int* flag) {
   using AR = ArithDF;
@@ -560,18 +563,20 @@ __global__ void __launch_bounds__(kPbThreads) potrf_blk_kernel(double* A, int64_
   // ---- outputs: L' = S diag(1/sqrt(d)), L'^{-1} = diag(1/sqrt(d)) Y, unscaled by D
   if (t < NB) rsd[t] = AR::rsqrt(S(t, t));
   __syncthreads();
-  double* Lk = Linv + (k0 / NB) * NB * NB;
-  float2* Lf2 = LinvDF ? LinvDF + (k0 / NB) * NB * NB : nullptr;
+  float2* Lf2 = LinvDF + (k0 / NB) * NB * NB;
+  float2* Ld2 = LDF + (k0 / NB) * NB * NB;
   for (int idx = t; idx < NB * NB; idx += kPbThreads) {
     const int i = idx / NB, c = idx % NB;
     const bool in = i < kb && c <= i;
-    T v = AR::zero();
-    if (in) v = (c == i) ? rsd[i] : AR::mul(Y(i, c), rsd[i]);   // L'^{-1}[i][c] = Y[i][c] / sqrt(d_i)
-    Lk[idx] = in ? AR::store_scaled(v, -sc[c]) : 0.0;
-    if (Lf2) Lf2[idx] = make_float2(v.h, v.l);                    // without D, for the panel solve
-    if (in) A[(k0 + i) * lda + k0 + c] = AR::store_scaled(AR::mul(S(i, c), rsd[c]), sc[i]);
+    T v = AR::zero(), l = AR::zero();
+    if (in) {
+      v = (c == i) ? rsd[i] : AR::mul(Y(i, c), rsd[i]);   // L'^{-1}[i][c] = Y[i][c] / sqrt(d_i)
+      l = AR::mul(S(i, c), rsd[c]);                       // L'[i][c] = S[i][c] / sqrt(d_c)
+    }
+    Lf2[idx] = make_float2(v.h, v.l);
+    Ld2[idx] = make_float2(l.h, l.l);
   }
-  if (Lf2 && t < NB) scOut[(k0 / NB) * NB + t] = sc[t];
+  if (t < NB) scOut[(k0 / NB) * NB + t] = sc[t];
   if (fw) {
     // forward substitution, block k: y_k = L'^{-1} (D w_k); 16 threads per row, combined by shuffles
     constexpr int kTpr = kPbThreads / NB;
@@ -591,6 +596,31 @@ __global__ void __launch_bounds__(kPbThreads) potrf_blk_kernel(double* A, int64_
     if (g == 0 && i < kb) {
       fy[k0 + i] = AR::store_scaled(acc, 0);
       fyDF[i] = make_float2(acc.h, acc.l);
+    }
+  }
+}
+
+// The FP64 copies of every diagonal block's factor, from the double-float results of
+// potrf_blk_kernel: L = D^-1 L' into A's diagonal block (lower, rows < kb) and
+// Linv = L'^{-1} D (the full 64 x 64, zero above the diagonal and on the padding).  One CTA per
+// block.
+__global__ void __launch_bounds__(256) diag_to_fp64_kernel(double* A, int64_t lda, int64_t n, const float2* LDF,
+                                                            const float2* LinvDF, const int* sc, double* Linv,
+                                                            const int* flag) {
+  if (*flag) return;
+  const int64_t k = blockIdx.x, k0 = k * NB;
+  const int kb = (int)((n - k0) < NB ? (n - k0) : NB);
+  const float2* Ld = LDF + k * NB * NB;
+  const float2* Lv = LinvDF + k * NB * NB;
+  const int* s = sc + k * NB;
+  for (int idx = threadIdx.x; idx < NB * NB; idx += blockDim.x) {
+    const int i = idx / NB, c = idx % NB;
+    const bool in = i < kb && c <= i;
+    const float2 v = Lv[idx];
+    Linv[k * NB * NB + idx] = in ? ArithDF::store_scaled({v.x, v.y}, -s[c]) : 0.0;
+    if (in) {
+      const float2 l = Ld[idx];
+      A[(k0 + i) * lda + k0 + c] = ArithDF::store_scaled({l.x, l.y}, s[i]);
     }
   }
 }
@@ -927,12 +957,12 @@ cudaError_t launch_potrf(double* A, int64_t lda, int64_t k0, int kb, const float
   return cudaGetLastError();
 }
 
-cudaError_t launch_potrf_blk(double* A, int64_t lda, int64_t k0, int kb, const float2* U, int64_t ldu,
-                             double* Linv, float2* LinvDF, int* scOut, const double* fw, double* fy, float2* fyDF,
+cudaError_t launch_potrf_blk(const double* A, int64_t lda, int64_t k0, int kb, const float2* U, int64_t ldu,
+                             float2* LDF, float2* LinvDF, int* scOut, const double* fw, double* fy, float2* fyDF,
                              int* flag, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(potrf_blk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPbSmem);
   if (e != cudaSuccess) return e;
-  potrf_blk_kernel<<<1, kPbThreads, kPbSmem, st>>>(A, lda, k0, kb, U, ldu, Linv, LinvDF, scOut, fw, fy, fyDF, flag);
+  potrf_blk_kernel<<<1, kPbThreads, kPbSmem, st>>>(A, lda, k0, kb, U, ldu, LDF, LinvDF, scOut, fw, fy, fyDF, flag);
   count_launch();
   return cudaGetLastError();
 }
@@ -1039,7 +1069,7 @@ cudaError_t cholesky_factor(double* A, int64_t n, int64_t lda, double* Linv, int
 constexpr int64_t kStrip = kCholStrip;
 
 // Split workspace of cholesky_factor_split: U (n x n double-FP32), two strip operands
-// (slices and four exponent arrays each), the double-float diagonal inverses, their
+// (slices and four exponent arrays each), the double-float diagonal factors and inverses, their
 // scales and the double-float forward-solve block.
 size_t chol_split_ws_bytes(int64_t n, int S) {
   auto rup = [](int64_t v, int64_t m) { return (v + m - 1) / m * m; };
@@ -1052,7 +1082,7 @@ size_t chol_split_ws_bytes(int64_t n, int S) {
   const size_t lb = rup(nblk * NB * NB * sizeof(float2), 256);
   const size_t cb = rup(nblk * NB * sizeof(int), 256);
   const size_t yb = rup(NB * sizeof(float2), 256);
-  return ub + 2 * (sb + eb) + lb + cb + yb + 256;
+  return ub + 2 * (sb + eb) + 2 * lb + cb + yb + 256;
 }
 
 // The look-ahead's streams: the critical path at the highest priority, the deferred bulk
@@ -1107,6 +1137,7 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
   float2* LinvDF = reinterpret_cast<float2*>(base + ub + 2 * (sb + eb));
   int* scales = reinterpret_cast<int*>(base + ub + 2 * (sb + eb) + lb);
   float2* yDF = reinterpret_cast<float2*>(base + ub + 2 * (sb + eb) + lb + cb);
+  float2* LDF = reinterpret_cast<float2*>(base + ub + 2 * (sb + eb) + lb + cb + rup(NB * sizeof(float2), 256));
   {
     const cudaError_t e = ensure_chol_streams(h);
     if (e != cudaSuccess) return e;
@@ -1170,7 +1201,7 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
         if (rc) return fail(rc);
       }
       const float2* Uk = (k0 > 0) ? U : nullptr;
-      err = launch_potrf_blk(A, lda, k0, kb, Uk, n, Linv, LinvDF, scales, b ? w : nullptr, y, yDF, flag, sh);
+      err = launch_potrf_blk(A, lda, k0, kb, Uk, n, LDF, LinvDF, scales, b ? w : nullptr, y, yDF, flag, sh);
       if (err != cudaSuccess) return err;
       const int64_t k1 = k0 + kb;
       if (k1 >= n) break;
@@ -1203,6 +1234,10 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
       launchedB[t] = 1;
     }
   }
+  // the FP64 copies of the diagonal blocks' factors for the triangular solves
+  diag_to_fp64_kernel<<<(unsigned)nblk, 256, 0, sh>>>(A, lda, n, LDF, LinvDF, scales, Linv, flag);
+  count_launch();
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if ((err = cudaEventRecord(e_hi, sh)) != cudaSuccess) return err;
   if ((err = cudaEventRecord(e_lo, sl)) != cudaSuccess) return err;
   if ((err = cudaStreamWaitEvent(st, e_hi, 0)) != cudaSuccess) return err;
