@@ -1218,7 +1218,7 @@ cudaError_t cholesky_factor_split(gn_handle* h, double* A, int64_t n, int64_t ld
     if (t >= 1 && launchedB[t - 1] && (err = cudaStreamWaitEvent(sh, evB[t - 1], 0)) != cudaSuccess) return err;
     const int64_t nn = (n - s1 < kStrip) ? n - s1 : kStrip;
     rc = oz_gemm(S, false, wb, wb, n - s1, nn, reinterpret_cast<double*>(U + s1 * n + s1), n, 3, nullptr,
-                 h->flag + 2, sh);
+                 h->flag + 2, sh, 1, nullptr, OzRange(), 64);
     if (rc) return fail(rc);
     if ((err = cudaEventRecord(evA[t], sh)) != cudaSuccess) return err;
     // (b) the rest, U[s2:, s2:] (lower tiles), deferred to sl: it overlaps the next strip's

@@ -303,14 +303,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   constexpr int NST = n_stages(S, BN);
   constexpr int STAGE_BYTES = stage_bytes(S, BN);
   constexpr int SLICE_B = BN * BKS * 2;          // one B slice tile
-  constexpr int TMEM_COLS = 4 * BN;              // four accumulator slots
+  // Chunked exponents flush all four slots after every chunk, so the next chunk's MMAs would
+  // wait for the flush; on 128 x 64 tiles two sets of slots fit the 512 tensor-memory columns
+  // and alternate between chunks (the MMAs fill one while the epilogue flushes the other).
+  constexpr int NACC = (CH && BN == TM / 2) ? 2 : 1;
+  constexpr int TMEM_COLS = 4 * BN * NACC;       // four accumulator slots per set
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + bar_offset(S, BN));
   uint64_t* empty = full + NST;
-  uint64_t* acc_full = empty + NST;
-  uint64_t* acc_empty = acc_full + 1;
-  uint64_t* done = acc_empty + 1;
+  uint64_t* acc_full = empty + NST;              // [NACC]
+  uint64_t* acc_empty = acc_full + NACC;         // [NACC]
+  uint64_t* done = acc_empty + NACC;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   __shared__ int abort_cta;
   __shared__ int ecs[2][TM];       // exponents of this tile's rows (0) and columns (1)
@@ -345,8 +349,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
     }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 8);
+    for (int b = 0; b < NACC; b++) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 8);
+    }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -399,6 +405,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       bool mma_issued = false;
       for (int c = 0; c < nchunk && ok; c++) {
         const int q_end = (nk - c * spc) < spc ? (nk - c * spc) : spc;
+        const int ab = (NACC == 2) ? (c & 1) : 0;            // this chunk's set of slots
+        const uint32_t tacc = tmem + (uint32_t)(ab * 4 * BN);
         for (int q = 0; q < q_end && ok; q++) {
           const int kt = c * spc + q;
           const int st = kt % NST;
@@ -412,8 +420,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           // both passes wait.
 #pragma unroll
           for (int pass = 0; pass < 2; pass++) {
-            if (q == 0 && c > 0 && pass == (CH ? 0 : 1)) {
-              if (!mbar_wait(acc_empty, (c - 1) & 1, flag, p.wait_ns)) { ok = false; break; }
+            // (two sets: the flush of chunk c - 2, which used the same set)
+            if (q == 0 && c >= NACC && pass == (CH ? 0 : 1)) {
+              const uint32_t par = (NACC == 2) ? (uint32_t)(((c >> 1) - 1) & 1) : (uint32_t)((c - 1) & 1);
+              if (!mbar_wait(&acc_empty[ab], par, flag, p.wait_ns)) { ok = false; break; }
               tc_fence_after();
             }
 #pragma unroll
@@ -431,7 +441,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                   // exact head levels; for the tail once, or per chunk with chunked exponents
                   const bool first = (slot < 3) ? (q == 0 && kk == 0 && s == 0)
                                                 : ((CH ? q : kt) == 0 && kk == 0 && s == 0 && u == 3);
-                  mma_bf16<BN>(tmem + slot * BN, da, db, first ? 0u : 1u);
+                  mma_bf16<BN>(tacc + slot * BN, da, db, first ? 0u : 1u);
                   mma_issued = true;
                 }
               }
@@ -439,7 +449,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (!ok) break;
           mma_commit(&empty[st]);
         }
-        if (ok) mma_commit(acc_full);
+        if (ok) mma_commit(&acc_full[ab]);
       }
       if (!ok) abort_cta = 1;
       // every issued MMA must complete before tensor memory is released (nothing to wait for
@@ -477,7 +487,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // one decision for all 256 epilogue threads: a thread whose own bounded wait ran out
       // while another's succeeded must not leave the loop alone (the chunked path's in-loop
       // bar.sync and the one after the loop would then find too few partners)
-      if (!epilogue_all(mbar_wait(acc_full, c & 1, flag, p.wait_ns))) { ok = false; break; }
+      const int ab = (NACC == 2) ? (c & 1) : 0;
+      const uint32_t par = (NACC == 2) ? (uint32_t)((c >> 1) & 1) : (uint32_t)(c & 1);
+      const uint32_t lbase = lane_base + (uint32_t)(ab * 4 * BN);
+      if (!epilogue_all(mbar_wait(&acc_full[ab], par, flag, p.wait_ns))) { ok = false; break; }
       tc_fence_after();
       if constexpr (CH) {
         // head levels and the tail, each scaled by this chunk's 2^e_row 2^e_col (two exact
@@ -490,7 +503,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
           for (int part = 0; part < EC / 16; part++) {
             float v[16];
-            tmem_ld16(lane_base + (uint32_t)(slot * BN + part * 16), v);
+            tmem_ld16(lbase + (uint32_t)(slot * BN + part * 16), v);
 #pragma unroll
             for (int i = 0; i < 16; i++)
               dd_add(hi[part * 16 + i], lo[part * 16 + i],
@@ -503,7 +516,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
           for (int part = 0; part < EC / 16; part++) {
             float v[16];
-            tmem_ld16(lane_base + (uint32_t)(slot * BN + part * 16), v);
+            tmem_ld16(lbase + (uint32_t)(slot * BN + part * 16), v);
 #pragma unroll
             for (int i = 0; i < 16; i++) dd_add(hi[part * 16 + i], lo[part * 16 + i], v[i]);
           }
@@ -512,7 +525,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
           for (int part = 0; part < EC / 16; part++) {
             float v[16];
-            tmem_ld16(lane_base + (uint32_t)(3 * BN + part * 16), v);
+            tmem_ld16(lbase + (uint32_t)(3 * BN + part * 16), v);
 #pragma unroll
             for (int i = 0; i < 16; i++) dd_add(hi[part * 16 + i], lo[part * 16 + i], v[i]);
           }
@@ -520,7 +533,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty);
+      if (lane == 0) mbar_arrive(&acc_empty[ab]);
     }
     // All loads have landed and all MMAs have completed (the last acc_full),
     // so the operand ring is free: park (hi, lo) there, then convert and store
