@@ -427,8 +427,53 @@ __global__ void __launch_bounds__(kPbThreads) potrf_blk_kernel(const double* A, 
   }
   __syncthreads();
 
+  // Output o of sub-panel c0's trailing rank-16 update (phase (c)): o < nS indexes the lower
+  // triangle of S22 (rows and columns from c0 + 16, row by row, so the first 136 outputs are the
+  // next sub-panel's diagonal block), the rest Y_below[:, < c0 + 16] row by row.
+  auto trailing = [&](int c0, int o) {
+    const int nb_rows = NB - c0 - kPbB, cw = c0 + kPbB;
+    const int nS = nb_rows * (nb_rows + 1) / 2;
+    if (o < nS) {
+      // lower-triangle index o -> (ii, cc), cc <= ii (o < 1176: the float root is exact enough)
+      int ii = (int)((sqrtf(8.0f * (float)o + 1.0f) - 1.0f) * 0.5f);
+      while ((ii + 1) * (ii + 2) / 2 <= o) ii++;
+      while (ii * (ii + 1) / 2 > o) ii--;
+      const int cc = o - ii * (ii + 1) / 2;
+      const int i = c0 + kPbB + ii, c = c0 + kPbB + cc;
+      T acc0 = S(i, c), acc1 = AR::zero();
+#pragma unroll
+      for (int j = 0; j < kPbB; j += 2) {
+        acc0 = AR::fnma_lazy(acc0, Tm[ii * kPbB + j], S(c, c0 + j));
+        acc1 = AR::fnma_lazy(acc1, Tm[ii * kPbB + j + 1], S(c, c0 + j + 1));
+      }
+      S(i, c) = AR::add(acc0, acc1);
+    } else {
+      const int oo = o - nS;
+      const int ii = oo / cw, c = oo % cw;
+      const int i = c0 + kPbB + ii;
+      T acc0 = Y(i, c), acc1 = AR::zero();
+      const int j0 = (c > c0) ? c - c0 : 0;          // Y[c0 + j][c] = 0 for c > c0 + j
+      for (int j = j0; j < kPbB; j += 2) {
+        const T y0 = (c0 + j == c) ? AR::one() : Y(c0 + j, c);
+        acc0 = AR::fnma_lazy(acc0, Tm[ii * kPbB + j], y0);
+        if (j + 1 < kPbB) acc1 = AR::fnma_lazy(acc1, Tm[ii * kPbB + j + 1], Y(c0 + j + 1, c));
+      }
+      Y(i, c) = AR::add(acc0, acc1);
+    }
+  };
+  constexpr int kDiagOut = kPbB * (kPbB + 1) / 2;   // the next diagonal block's outputs
+  int pend = -1;                                    // sub-panel whose trailing update is unfinished
+
   for (int p = 0; p < NB / kPbB; p++) {
     const int c0 = p * kPbB;
+    // ---- the rest of the previous sub-panel's trailing update (everything but this sub-panel's
+    //      diagonal block, which the sweep below needs and which was updated first), by the 768
+    //      threads the sweep leaves idle: it touches neither the block nor the sweep's buffers
+    if (t >= kPbB * kPbB && pend >= 0) {
+      const int nr = NB - pend - kPbB;
+      const int tot = nr * (nr + 1) / 2 + nr * (pend + kPbB);
+      for (int o = kDiagOut + (t - kPbB * kPbB); o < tot; o += kPbThreads - kPbB * kPbB) trailing(pend, o);
+    }
     // ---- (a) the 16 x 16 diagonal sub-block, by the first 256 threads (8 warps, one named
     //      barrier per column): thread (r, cl) holds element (c0 + r, c0 + cl), S until column
     //      cl is published, then Y.  One element per thread keeps each step's dependent chain
@@ -526,38 +571,10 @@ __global__ void __launch_bounds__(kPbThreads) potrf_blk_kernel(const double* A, 
     __syncthreads();
     if (nb_rows == 0) break;
     // ---- (c) trailing rank-16 update of the rows below: S22 -= T21 S21^T (lower), and
-    //      Y_below[:, < c0 + 16] -= T21 Y_p
-    const int cw = c0 + kPbB;                          // Y columns touched
-    const int nS = nb_rows * (nb_rows + 1) / 2, nY = nb_rows * cw;
-    for (int o = t; o < nS + nY; o += kPbThreads) {
-      if (o < nS) {
-        // lower-triangle index o -> (ii, cc), cc <= ii (o < 1176: the float root is exact enough)
-        int ii = (int)((sqrtf(8.0f * (float)o + 1.0f) - 1.0f) * 0.5f);
-        while ((ii + 1) * (ii + 2) / 2 <= o) ii++;
-        while (ii * (ii + 1) / 2 > o) ii--;
-        const int cc = o - ii * (ii + 1) / 2;
-        const int i = c0 + kPbB + ii, c = c0 + kPbB + cc;
-        T acc0 = S(i, c), acc1 = AR::zero();
-#pragma unroll
-        for (int j = 0; j < kPbB; j += 2) {
-          acc0 = AR::fnma_lazy(acc0, Tm[ii * kPbB + j], S(c, c0 + j));
-          acc1 = AR::fnma_lazy(acc1, Tm[ii * kPbB + j + 1], S(c, c0 + j + 1));
-        }
-        S(i, c) = AR::add(acc0, acc1);
-      } else {
-        const int oo = o - nS;
-        const int ii = oo / cw, c = oo % cw;
-        const int i = c0 + kPbB + ii;
-        T acc0 = Y(i, c), acc1 = AR::zero();
-        const int j0 = (c > c0) ? c - c0 : 0;          // Y[c0 + j][c] = 0 for c > c0 + j
-        for (int j = j0; j < kPbB; j += 2) {
-          const T y0 = (c0 + j == c) ? AR::one() : Y(c0 + j, c);
-          acc0 = AR::fnma_lazy(acc0, Tm[ii * kPbB + j], y0);
-          if (j + 1 < kPbB) acc1 = AR::fnma_lazy(acc1, Tm[ii * kPbB + j + 1], Y(c0 + j + 1, c));
-        }
-        Y(i, c) = AR::add(acc0, acc1);
-      }
-    }
+    //      Y_below[:, < c0 + 16] -= T21 Y_p.  Only the next sub-panel's diagonal block now; the
+    //      rest runs beside the next sweep (above), before the next phase (b) reads it.
+    for (int o = t; o < kDiagOut; o += kPbThreads) trailing(c0, o);
+    pend = c0;
     __syncthreads();
   }
   // ---- outputs: L' = S diag(1/sqrt(d)), L'^{-1} = diag(1/sqrt(d)) Y, unscaled by D
