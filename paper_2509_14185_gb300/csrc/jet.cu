@@ -676,7 +676,19 @@ cudaError_t launch_eq(const JetArgs& a, cudaStream_t st, int64_t* warps_used) {
   constexpr int CF = (MODE == MODE_RESIDUAL) ? CR : JT<D>::CF;
   const int64_t per_warp = jet_smem_doubles(a.net, CF, CR, NF) * (int64_t)sizeof(double);
   constexpr int64_t kSmemCap = 227 * 1024;   // the opt-in maximum per block
+  // Few points (the Hilbert nodes, the wall and decay rows, the normalisation point): fewer warps
+  // per block spread them over all SMs, so each SM's FP64 pipe serves fewer of them (512 nodes in
+  // blocks of 8 warps would use 64 of the 152 SMs).  Each point is one warp's work whatever the
+  // block size, so the rows do not change.
+  static const int sms = [] {
+    int dev = 0, v = 0;
+    const bool ok = cudaGetDevice(&dev) == cudaSuccess &&
+                    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0;
+    return ok ? v : 152;
+  }();
   int wpb = 8;
+  const int64_t spread = (a.n + sms - 1) / sms;
+  if (spread < wpb) wpb = spread < 1 ? 1 : (int)spread;
   while (wpb > 1 && per_warp * wpb > kSmemCap) wpb--;
   if (per_warp > kSmemCap) return cudaErrorInvalidValue;
   const size_t smem = (size_t)per_warp * wpb;
