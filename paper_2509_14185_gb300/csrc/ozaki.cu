@@ -186,6 +186,18 @@ __device__ __forceinline__ double pow2(int e) {
 __device__ __forceinline__ float pow2f(int e) {
   return (e >= -126 && e <= 127) ? __int_as_float((e + 127) << 23) : ldexpf(1.0f, e);
 }
+// x 2^k as a double by integer operations on the bits: exact for a normal x and a normal
+// result, with no FP64 instruction (GB300's FP64 pipe retires about two per clock per SM, so
+// a conversion and a scaling multiply per element made the store loop FP64-bound); zero,
+// subnormal or non-finite x and results outside the normal range take the FP64 path.
+__device__ __forceinline__ double f2d_scaled(float x, int k) {
+  const unsigned b = __float_as_uint(x);
+  const int ex = (int)((b >> 23) & 0xff);
+  const int e = ex - 127 + k + 1023;
+  if (ex == 0 || ex == 0xff || e <= 0 || e >= 2047) return (double)x * pow2(k);
+  return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) | ((unsigned long long)e << 52) |
+                                          ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
 // (u.x, u.y) += (h, l), both double-FP32 (TwoSum, then Fast2Sum renormalisation)
 __device__ __forceinline__ void dd2_add(float2& u, float h, float l) {
   const float s = __fadd_rn(u.x, h);
@@ -591,7 +603,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           hl[q] = park[r * (BN + 1) + cc];
           if (p.mode == 3) hl[q] = make_float2(hl[q].x * pow2f(ecs[0][r] + ecs[1][cc]),
                                               hl[q].y * pow2f(ecs[0][r] + ecs[1][cc]));
-          else cv[q] = ((double)hl[q].x + (double)hl[q].y) * pow2(ecs[0][r] + ecs[1][cc]);
+          else {
+            const int e = ecs[0][r] + ecs[1][cc];
+            if constexpr (CH) {   // not reached: chunked launches accumulate into U (mode 3)
+              cv[q] = ((double)hl[q].x + (double)hl[q].y) * pow2(e);
+            } else {
+              // (hi + lo) 2^e with one FP64 addition: the two scalings are exact bit operations
+              // and rounding the sum commutes with them, so this equals (hi + lo rounded) 2^e
+              cv[q] = f2d_scaled(hl[q].x, e) + f2d_scaled(hl[q].y, e);
+            }
+          }
           rs[q] = (p.mode == 1 && p.rowscale && in[q]) ? p.rowscale[gi] : 1.0;
         }
         if (p.mode == 3) {
