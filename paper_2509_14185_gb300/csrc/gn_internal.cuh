@@ -304,9 +304,36 @@ OzOperand oz_operand_rows(const OzOperand& op, int S, int64_t row_off);
 // integer round(x 2^{8S-e}) written in balanced base-256 digits a_0 .. a_{S-1}
 // (a_0 carries the sign and the rest lie in [-128, 128)); slice q holds
 // a_q 2^{-8(q+1)}, exact in BF16.  out[q * stride] receives slice q.
+// round(x 2^n) to the nearest integer, ties to even (what llrint(ldexp(x, n)) gives), by
+// integer operations on the bits: GB300 runs the FP64 scaling and the FP64 -> int64
+// conversion on its narrow FP64 pipe, which made the slicing passes FP64-bound.  Results that
+// leave the range the split uses (|x 2^n| >= 2^62) and non-finite x take the FP64 path.
+__device__ __forceinline__ long long scaled_rint(double x, int n) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0x7ff) return llrint(ldexp(x, n));
+  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  int ee = ex;
+  if (ex != 0) m |= 1ull << 52;   // normal: the implicit bit
+  else ee = 1;                    // subnormal
+  const int sh = ee - 1075 + n;   // x 2^n = +-m 2^sh
+  unsigned long long q;
+  if (sh >= 0) {
+    if (sh > 9) return llrint(ldexp(x, n));
+    q = m << sh;
+  } else if (-sh >= 64) {
+    q = 0;                        // m < 2^53 <= 2^(-sh - 1): rounds to zero
+  } else {
+    const int r = -sh;
+    q = m >> r;
+    const unsigned long long rem = m & ((1ull << r) - 1), half = 1ull << (r - 1);
+    if (rem > half || (rem == half && (q & 1))) q++;
+  }
+  return (b >> 63) ? -(long long)q : (long long)q;
+}
 template <int S>
 __device__ __forceinline__ void oz_digits(double x, int e, __nv_bfloat16* out, int64_t stride) {
-  long long v = llrint(ldexp(x, 8 * S - e));
+  long long v = scaled_rint(x, 8 * S - e);
   int a[S];
 #pragma unroll
   for (int q = S - 1; q >= 1; q--) {

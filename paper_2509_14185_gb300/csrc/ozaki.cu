@@ -692,9 +692,14 @@ __global__ void colmax_partial(const double* __restrict__ X, int64_t ld, int64_t
   const int c = blockIdx.y;
   const int64_t per = (nrows + CM_CHUNKS - 1) / CM_CHUNKS;
   const int64_t r0 = c * per, r1 = (r0 + per < nrows) ? r0 + per : nrows;
-  double m = 0.0;
-  for (int64_t r = r0; r < r1; r++) m = fmax(m, fabs(X[r * ld + j]));
-  part[(int64_t)c * ncols + j] = m;
+  // max |x| as the largest bit pattern of |x| (the order of non-negative doubles), NaNs skipped
+  // as fmax skips them: integer operations, where fmax/fabs would run on the FP64 pipe
+  unsigned long long m = 0;
+  for (int64_t r = r0; r < r1; r++) {
+    const unsigned long long a = (unsigned long long)__double_as_longlong(X[r * ld + j]) & 0x7FFFFFFFFFFFFFFFull;
+    if (a <= 0x7FF0000000000000ull && a > m) m = a;
+  }
+  part[(int64_t)c * ncols + j] = __longlong_as_double((long long)m);
 }
 __global__ void colexp_kernel(const double* __restrict__ part, int64_t ncols, int64_t npad, int* e) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
