@@ -490,14 +490,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int i = 0; i < EC; i++) { hi[i] = 0.f; lo[i] = 0.f; }
     constexpr int nhead = S < 3 ? S : 3;        // head levels present: 2..min(S+1, 4)
     bool ok = true;
-    // Chunked exponents (the factorisation's updates): the final read-modify-write of U waits
-    // for its loads; the tile's lines are fetched into L2 while the last two chunks' MMAs run, so
-    // that wait is an L2 latency rather than a DRAM one (a tile row is BN x 8 bytes: 8 or 4 lines
-    // of 128 bytes).  Damped solve 17.34 -> 16.98 ms; the same prefetch in the single-exponent
-    // build left the Hilbert contraction unchanged and slowed the Gram by 2 %, so it is not there.
+    // Read-modify-write launches that are not the Gram (the factorisation's updates into U, the
+    // Hilbert contraction into J): the final loop waits for the tile's old values; their lines
+    // are fetched into L2 while the last two chunks' MMAs run, so that wait is an L2 latency
+    // rather than a DRAM one (a tile row is BN x 8 bytes: 8 or 4 lines of 128 bytes).  Damped
+    // solve 17.34 -> 16.98 ms, Jacobian phase 6.16 -> 6.10 ms; the symmetric single-exponent
+    // build (the Gram, which stores without reading) is compiled without it.
     const int pfc = nchunk >= 2 ? nchunk - 2 : 0;
     for (int c = 0; c < nchunk; c++) {
-      if constexpr (CH) {
+      if constexpr (CH || !SYM) {
         if (c == pfc && p.mode != 0 && !p.part) {
           constexpr int LPR = BN * 8 / 128;         // lines per tile row
           const char* Cb = reinterpret_cast<const char*>(p.C);
