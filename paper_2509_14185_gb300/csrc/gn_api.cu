@@ -764,7 +764,7 @@ int damped_solve(gn_handle* h, const double* G, const double* g, double* gamma, 
   const int64_t Pp = h->Pp;
   int retries = 0;
   for (;;) {
-    GN_TRY_CUDA(copy_add_diag(G, h->A, Pp, Pp, *gamma, h->st));
+    GN_TRY_CUDA(copy_add_diag(G, h->A, Pp, Pp, *gamma, nullptr, h->st));
     GN_TRY_CUDA(cudaMemsetAsync(h->flag + 1, 0, sizeof(int), h->st));
     if (h->precision == GN_PREC_SPLIT_ALL) {
       int rc = GN_OK;

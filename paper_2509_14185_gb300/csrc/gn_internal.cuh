@@ -258,7 +258,9 @@ cudaError_t mirror_lower(double* G, int64_t n, int64_t ld, cudaStream_t st);
 // A = G + gamma I on the lower triangle's columns [c0, c1) (gamma: device scalar)
 cudaError_t add_diag_band(const double* G, double* A, int64_t n, int64_t ld, int64_t c0, int64_t c1,
                           const double* gamma, cudaStream_t st);
-cudaError_t copy_add_diag(const double* G, double* A, int64_t n, int64_t ld, double gamma, cudaStream_t st);
+// A = G + gamma I on the lower triangle (gamma_dev, when given, is read on the device instead)
+cudaError_t copy_add_diag(const double* G, double* A, int64_t n, int64_t ld, double gamma, const double* gamma_dev,
+                          cudaStream_t st);
 cudaError_t max_abs_rows(const double* r, int64_t n, int stride_valid, double* red, cudaStream_t st);
 cudaError_t finish_max(double* red, double* out_dev, cudaStream_t st);
 // max |R_k| over the interior rows r_i = w sqrt(rho_i) R_k (rho null: 1) into *out_dev

@@ -84,20 +84,6 @@ namespace {
     if (e_ != cudaSuccess) return GN_ERR_CUDA;              \
   } while (0)
 
-// A = G + gamma I with gamma read from the state (copy_add_diag with a device scalar).
-__global__ void add_diag_state_kernel(const double* __restrict__ G, double* A, int64_t n, int64_t ld,
-                                      const StepState* s) {
-  const double gamma = s->gamma;
-  const int64_t total = n * ld;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = idx / ld, j = idx - i * ld;
-    double v = G[idx];
-    if (i == j) v += gamma;
-    A[idx] = v;
-  }
-}
-
 // Model scalars after the solve (red[256] = |r~|^2, red[257] = g.delta, red[258] =
 // delta.G.delta, delta[P] = the lambda component); decides whether the line search runs.
 __global__ void model_kernel(const double* __restrict__ red, const double* __restrict__ delta, int64_t P,
@@ -228,9 +214,7 @@ int capture_solve(gn_handle* h, double* theta, bool marks, const cudaEvent_t* ga
 
   if (mark(h, marks, 4)) return GN_ERR_CUDA;
   if (!gate) {
-    add_diag_state_kernel<<<1024, 256, 0, st>>>(h->G, h->A, Pp, Pp, ds);
-    count_launch();
-    GN_G_TRY(cudaGetLastError());
+    GN_G_TRY(copy_add_diag(h->G, h->A, Pp, Pp, 0.0, &ds->gamma, st));   // gamma from the step state
   }
   GN_G_TRY(cudaMemsetAsync(h->flag + 1, 0, sizeof(int), st));
   if (h->precision == GN_PREC_SPLIT_ALL) {

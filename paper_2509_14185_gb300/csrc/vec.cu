@@ -139,14 +139,16 @@ __global__ void mirror_lower_kernel(double* G, int64_t n, int64_t ld) {
   }
 }
 
-__global__ void copy_add_diag_kernel(const double* __restrict__ G, double* A, int64_t n, int64_t ld, double gamma) {
-  const int64_t total = n * ld;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = idx / ld, j = idx - i * ld;
-    double v = G[idx];
-    if (i == j) v += gamma;
-    A[idx] = v;
+// A = G + gamma I on the lower triangle, diagonal included: the only part the factorisations
+// read (the upper triangle of A is left as it is).  One block per row, no index division; gamma
+// from the device when gamma_dev is given (a captured step reads it from its state).
+__global__ void copy_add_diag_kernel(const double* __restrict__ G, double* A, int64_t n, int64_t ld, double gamma,
+                                     const double* __restrict__ gamma_dev) {
+  const double gm = gamma_dev ? *gamma_dev : gamma;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const double* gr = G + i * ld;
+    double* ar = A + i * ld;
+    for (int64_t j = threadIdx.x; j <= i; j += blockDim.x) ar[j] = (j == i) ? gr[j] + gm : gr[j];
   }
 }
 
@@ -286,8 +288,10 @@ cudaError_t add_diag_band(const double* G, double* A, int64_t n, int64_t ld, int
   count_launch();
   return cudaGetLastError();
 }
-cudaError_t copy_add_diag(const double* G, double* A, int64_t n, int64_t ld, double gamma, cudaStream_t st) {
-  copy_add_diag_kernel<<<1024, 256, 0, st>>>(G, A, n, ld, gamma);
+cudaError_t copy_add_diag(const double* G, double* A, int64_t n, int64_t ld, double gamma, const double* gamma_dev,
+                          cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  copy_add_diag_kernel<<<(unsigned)(n < 8192 ? n : 8192), 256, 0, st>>>(G, A, n, ld, gamma, gamma_dev);
   count_launch();
   return cudaGetLastError();
 }
