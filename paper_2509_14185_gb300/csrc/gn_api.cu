@@ -862,7 +862,6 @@ int gn_step(gn_handle* h, double* theta, double* lambda, double* damping, gn_ste
       t_gram += tm.ms(2, 3);
     }
   }
-  GN_TRY_CUDA(mirror_lower(h->G, Pp, Pp, st));
   rc = loss_of(h, h->r, 0);
   if (!rc) rc = max_res_of(h, h->r);
   if (rc) return rc;
@@ -888,7 +887,8 @@ int gn_step(gn_handle* h, double* theta, double* lambda, double* damping, gn_ste
   // 3. scalars for the model: g.delta, delta.G.delta, delta[P], h0
   GN_TRY_CUDA(dot_partial(h->g, h->delta, Pp, h->red, st));
   GN_TRY_CUDA(finish_sum(h->red, h->red + 257, st));
-  GN_TRY_CUDA(dgemv_n(h->G, Pp, Pp, Pp, h->delta, h->vtmp, 0.0, st));
+  // delta.G.delta from G's lower triangle (the step never forms the upper one)
+  GN_TRY_CUDA(quad_lower(h->G, Pp, Pp, h->delta, h->vtmp, st));
   GN_TRY_CUDA(dot_partial(h->delta, h->vtmp, Pp, h->red, st));
   GN_TRY_CUDA(finish_sum(h->red, h->red + 258, st));
   GN_TRY_CUDA(cudaMemcpyAsync(h->red + 259, h->delta + P, sizeof(double), cudaMemcpyDeviceToDevice, st));

@@ -258,6 +258,8 @@ cudaError_t mirror_lower(double* G, int64_t n, int64_t ld, cudaStream_t st);
 // A = G + gamma I on the lower triangle's columns [c0, c1) (gamma: device scalar)
 cudaError_t add_diag_band(const double* G, double* A, int64_t n, int64_t ld, int64_t c0, int64_t c1,
                           const double* gamma, cudaStream_t st);
+// y with x . y = x^T G x from G's lower triangle: y_i = G_ii x_i + 2 sum_{j<i} G_ij x_j
+cudaError_t quad_lower(const double* G, int64_t n, int64_t ld, const double* x, double* y, cudaStream_t st);
 // A = G + gamma I on the lower triangle (gamma_dev, when given, is read on the device instead)
 cudaError_t copy_add_diag(const double* G, double* A, int64_t n, int64_t ld, double gamma, const double* gamma_dev,
                           cudaStream_t st);

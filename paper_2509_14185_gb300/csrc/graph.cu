@@ -187,7 +187,6 @@ int capture_rows_gram(gn_handle* h, const double* theta, bool marks) {
     if (!rc) rc = mark(h, marks, 2);
   }
   if (rc) return rc;
-  GN_G_TRY(mirror_lower(h->G, h->Pp, h->Pp, st));
   rc = loss_of(h, h->r, 0);
   return rc ? rc : max_res_of(h, h->r);
 }
@@ -232,7 +231,7 @@ int capture_solve(gn_handle* h, double* theta, bool marks, const cudaEvent_t* ga
   if (join) GN_G_TRY(cudaStreamWaitEvent(st, join, 0));   // the model reads all of G
   GN_G_TRY(dot_partial(h->g, h->delta, Pp, h->red, st));
   GN_G_TRY(finish_sum(h->red, h->red + 257, st));
-  GN_G_TRY(dgemv_n(h->G, Pp, Pp, Pp, h->delta, h->vtmp, 0.0, st));
+  GN_G_TRY(quad_lower(h->G, Pp, Pp, h->delta, h->vtmp, st));   // delta.G.delta from the lower triangle
   GN_G_TRY(dot_partial(h->delta, h->vtmp, Pp, h->red, st));
   GN_G_TRY(finish_sum(h->red, h->red + 258, st));
   model_kernel<<<1, 1, 0, st>>>(h->red, h->delta, P, h->flag, ds, cond[0]);

@@ -139,6 +139,22 @@ __global__ void mirror_lower_kernel(double* G, int64_t n, int64_t ld) {
   }
 }
 
+// y_i = G_ii x_i + 2 sum_{j<i} G_ij x_j from the lower triangle of a symmetric G, so that
+// x . y = x^T G x (the step's model term delta^T G delta) without the upper triangle: one warp
+// per row, each row's lower part read once in a fixed order (deterministic).
+__global__ void quad_lower_kernel(const double* __restrict__ G, int64_t n, int64_t ld, const double* __restrict__ x,
+                                  double* y) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const double* gr = G + row * ld;
+  double s = 0.0;
+  for (int64_t j = lane; j < row; j += 32) s = fma(gr[j], x[j], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) y[row] = fma(gr[row], x[row], 2.0 * s);
+}
+
 // A = G + gamma I on the lower triangle, diagonal included: the only part the factorisations
 // read (the upper triangle of A is left as it is).  One block per row, no index division; gamma
 // from the device when gamma_dev is given (a captured step reads it from its state).
@@ -285,6 +301,12 @@ cudaError_t add_diag_band(const double* G, double* A, int64_t n, int64_t ld, int
   int64_t b = (total + 255) / 256;
   if (b > 2048) b = 2048;
   add_diag_band_kernel<<<(unsigned)b, 256, 0, st>>>(G, A, n, ld, c0, c1, gamma);
+  count_launch();
+  return cudaGetLastError();
+}
+cudaError_t quad_lower(const double* G, int64_t n, int64_t ld, const double* x, double* y, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  quad_lower_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, st>>>(G, n, ld, x, y);
   count_launch();
   return cudaGetLastError();
 }
