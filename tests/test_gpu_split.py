@@ -64,6 +64,31 @@ def test_split_gram_bit_exact_on_8bit_integers(nrows):
     assert np.array_equal(np.tril(G), np.tril(Gx))
 
 
+def test_split_gram_one_slice_rounds_ties_to_even():
+    """The digits are round(x 2^(8S - e)) to the nearest integer with ties to even, formed from
+    the double's bits.  With one slice and every entry an odd multiple of 1/2 below 200 (each
+    column's largest entry in [128, 256), so x 2^(8S - e) = x), every entry is a tie: the split
+    Gram must equal A^T A bit for bit with A = J rounded half to even (numpy's rule), not
+    half away from zero.  Columns rescaled by powers of two, negative ties and a zero column
+    take the same path."""
+    w = small("ccf")
+    prob = gpu_problem(w)
+    Pp = prob.P + 1
+    rng = np.random.default_rng(23)
+    nrows = 700
+    Jh = rng.integers(-200, 200, size=(nrows, Pp)).astype(np.float64) + 0.5
+    Jh[0, :] = 199.5                     # each column's maximum in [128, 256): exponent 8
+    Jh[:, 3] = 0.0
+    scale = np.ones(Pp)
+    scale[9::97] = 2.0 ** -30
+    scale[10::97] = 2.0 ** 12
+    A = np.round(Jh)                     # half to even
+    assert np.any(A != np.trunc(Jh + np.copysign(0.5, Jh)))   # the ties are really ties
+    G = host(_split_gram(prob, dev(Jh * scale), 1))
+    Gx = (A * scale).T @ (A * scale)     # exact: integers times powers of two, below 2^53
+    assert np.array_equal(np.tril(G), np.tril(Gx))
+
+
 @pytest.mark.parametrize("slices", [1, 2, 3, 4, 5, 6])
 def test_split_gram_error_bound(slices):
     w = small("ccf")
