@@ -1148,7 +1148,8 @@ def main():
                        "from pinned host memory, gn_step through the C ABI, theta out to pinned host memory "
                        "with a blocking copy; lambda, damping and the loss are host scalars of the call"}
 
-    # split precision vs FP64 at equal residual (CCF stable profile, the survey's target), and
+    # split precision vs FP64 at equal residual (CCF stable profile: the FP64 run's final validation
+    # max |R| x 1.1 with its loss x 1.1 as the target), and
     # the batched sweep of 64 uneven fits as one graph launch per step
     extras = {}
     if rank == 0 and world == 1 and not args.no_extras:
