@@ -348,14 +348,16 @@ __global__ void __launch_bounds__(NB * TPR) potrf_inv_kernel(double* A, int64_t 
 //
 // The same LDL^T elimination as potrf_inv_kernel (S: unscaled columns L_unit D; Y = L_unit^{-1}),
 // reordered into four 16-column sub-panels p so that only a 16-step chain is latency-bound:
-//  (a) one warp sweeps the 16 x 16 diagonal sub-block column by column (S and Y_pp = its
-//      unit-lower inverse share registers, as in the unblocked kernel; the pivots' reciprocals
-//      are kept);
+//  (a) 256 threads (one element each) sweep the 16 x 16 diagonal sub-block column by column
+//      (S and Y_pp = its unit-lower inverse share registers, as in the unblocked kernel; the
+//      pivots' reciprocals are kept);
 //  (b) every thread then forms, into registers: the sub-panel rows below, S21 = B21 Y_pp^T,
 //      with T21 = S21 diag(1/d); and the sub-panel's own Y rows for the earlier columns,
 //      Y_p,<c0 <- Y_pp Y_p,<c0 (the rows' share of the elimination within the sub-panel);
 //  (c) the trailing rank-16 update of the rows below: S22 -= T21 S21^T on the lower triangle,
-//      and Y_below -= T21 Y_p on the columns < c0 + 16.
+//      and Y_below -= T21 Y_p on the columns < c0 + 16.  Only the next sub-panel's diagonal
+//      block is updated before the next sweep; the rest runs on the other 768 threads beside
+//      that sweep (it touches neither the block nor the sweep's buffers).
 // Each product is the same double-float arithmetic (about 48 significant bits) as the
 // unblocked sweep; only the order of the updates changes.  1024 threads, one CTA: the
 // phases (b) and (c) give most threads one or two outputs, each a 16-term double-float dot
